@@ -1,0 +1,214 @@
+"""CPU oracle of the message-passing automaton decoder (arXiv 2506.03266).
+
+TEST INFRASTRUCTURE ONLY.  This package wraps the plain single-threaded C
+implementation in ``qca_oracle.c`` with ctypes + numpy.  Only the test-suite,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+it; the library's product path never does.  It shares no code with the CUDA
+library: neither imports nor links the other.
+
+Every function follows one definition of the paper (Sec. 3.2,
+Def. "D-dimensional message passing automaton"; Def. "synchronous automaton
+decoder"; Def. "logical failure rate and decoding time"; Sec. 7 numerics); see
+the header comment of ``qca_oracle.c`` for the readings R1-R11 of points where
+the paper is silent or garbled.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qca_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libqca_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# Defaults fixed by the paper's numerics (Sec. 7: v = 3) and by the 8-bit
+# message register (m_max = 255, reading R5).
+V_DEFAULT = 3
+M_MAX_DEFAULT = 255
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into oracle/_build (idempotent)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    hdr = os.path.join(_HERE, "qca_oracle.h")
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(hdr))):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+        i8p = np.ctypeslib.ndpointer(np.int8, flags="C_CONTIGUOUS")
+        i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+        c_int, c_i64, c_u64 = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
+        lib.qo_splitmix64.argtypes = [c_u64]
+        lib.qo_splitmix64.restype = c_u64
+        lib.qo_prob_threshold.argtypes = [ctypes.c_double]
+        lib.qo_prob_threshold.restype = c_u64
+        lib.qo_sample_errors.argtypes = [c_int, c_i64, c_i64, c_u64, c_u64, u8p]
+        lib.qo_sample_errors.restype = None
+        lib.qo_syndrome.argtypes = [c_int, u8p, i8p]
+        lib.qo_syndrome.restype = None
+        lib.qo_message_substep.argtypes = [c_int, c_int, i8p, i32p, i32p]
+        lib.qo_message_substep.restype = None
+        lib.qo_forces.argtypes = [c_int, i8p, i32p, i8p]
+        lib.qo_forces.restype = None
+        lib.qo_feedback_links.argtypes = [c_int, i8p, i8p, u8p]
+        lib.qo_feedback_links.restype = None
+        lib.qo_step.argtypes = [c_int, c_int, c_int, c_u64, c_u64, c_i64, ctypes.c_int32,
+                                i8p, i32p, u8p, ctypes.c_void_p]
+        lib.qo_step.restype = c_int
+        lib.qo_cut_parity.argtypes = [c_int, u8p, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
+        lib.qo_cut_parity.restype = None
+        lib.qo_decode_shot.argtypes = [u8p, c_int, c_int, c_int, c_int, c_u64, c_u64, c_i64,
+                                       u8p, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, c_int]
+        lib.qo_decode_shot.restype = c_int
+        lib.qo_decode_syndrome_shot.argtypes = [u8p, c_int, c_int, c_int, c_int, c_u64, c_u64,
+                                                c_i64, u8p, ctypes.POINTER(ctypes.c_int32), u8p]
+        lib.qo_decode_syndrome_shot.restype = c_int
+        lib.qo_decode_batch.argtypes = [u8p, c_int, c_i64, c_i64, c_int, c_int, c_int, c_u64,
+                                        c_u64, u8p, i32p, u8p]
+        lib.qo_decode_batch.restype = None
+        _lib = lib
+        return lib
+
+
+# ----------------------------------------------------------------- helpers --
+
+def splitmix64(z: int) -> int:
+    return int(_load().qo_splitmix64(ctypes.c_uint64(z & (2**64 - 1))))
+
+
+def prob_threshold(p: float) -> int:
+    """Integer threshold floor(p * 2^64) used by both sides for an edge flip."""
+    return int(_load().qo_prob_threshold(float(p)))
+
+
+def sample_errors(L: int, shots: int, p: float, seed: int, shot0: int = 0) -> np.ndarray:
+    """i.i.d. bit-flip noise (Sec. 7), uint8 [shots][2][L][L]."""
+    out = np.zeros((shots, 2, L, L), dtype=np.uint8)
+    _load().qo_sample_errors(L, shot0, shots, prob_threshold(p), seed, out)
+    return out
+
+
+def syndrome(edges: np.ndarray) -> np.ndarray:
+    """sigma (int8, +1/-1) of a link set uint8 [2][L][L] (Def. synch_ccqs)."""
+    edges = np.ascontiguousarray(edges, dtype=np.uint8)
+    L = edges.shape[-1]
+    sig = np.zeros((L, L), dtype=np.int8)
+    _load().qo_syndrome(L, edges, sig)
+    return sig
+
+
+def message_substep(sigma: np.ndarray, m: np.ndarray, m_max: int = M_MAX_DEFAULT) -> np.ndarray:
+    """One application of A^(D) (Def. Dd_msg_passing); m is int32 [4][L][L]."""
+    sigma = np.ascontiguousarray(sigma, dtype=np.int8)
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    L = sigma.shape[0]
+    out = np.zeros_like(m)
+    _load().qo_message_substep(L, m_max, sigma, m, out)
+    return out
+
+
+def forces(sigma: np.ndarray, m: np.ndarray) -> np.ndarray:
+    """f^a_r, int8 [2][L][L] (Eqs. blahdef / degbreak)."""
+    sigma = np.ascontiguousarray(sigma, dtype=np.int8)
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    L = sigma.shape[0]
+    f = np.zeros((2, L, L), dtype=np.int8)
+    _load().qo_forces(L, sigma, m, f)
+    return f
+
+
+def feedback_links(sigma: np.ndarray, f: np.ndarray) -> np.ndarray:
+    """Links flipped by F^(D) (Eq. ddfeedback), uint8 [2][L][L]."""
+    sigma = np.ascontiguousarray(sigma, dtype=np.int8)
+    f = np.ascontiguousarray(f, dtype=np.int8)
+    L = sigma.shape[0]
+    out = np.zeros((2, L, L), dtype=np.uint8)
+    _load().qo_feedback_links(L, sigma, f, out)
+    return out
+
+
+def step(sigma: np.ndarray, m: np.ndarray, C: np.ndarray, *, v: int = V_DEFAULT,
+         m_max: int = M_MAX_DEFAULT, move_thr: int = 0, seed: int = 0, shot: int = 0,
+         t: int = 0):
+    """One decoder step, in place on (sigma, m, C).  Returns (anyons, flips)."""
+    L = sigma.shape[0]
+    flips = np.zeros((2, L, L), dtype=np.uint8)
+    n = _load().qo_step(L, v, m_max, move_thr, seed, shot, t, sigma, m, C,
+                        flips.ctypes.data_as(ctypes.c_void_p))
+    return n, flips
+
+
+def cut_parity(R: np.ndarray):
+    R = np.ascontiguousarray(R, dtype=np.uint8)
+    L = R.shape[-1]
+    wx, wy = ctypes.c_int(), ctypes.c_int()
+    _load().qo_cut_parity(L, R, ctypes.byref(wx), ctypes.byref(wy))
+    return wx.value, wy.value
+
+
+def decode_shot(N: np.ndarray, *, v: int = V_DEFAULT, m_max: int = M_MAX_DEFAULT,
+                max_steps: int = 4096, move_thr: int = 0, seed: int = 0, shot: int = 0,
+                trace: bool = False):
+    """Decode one noise realisation N (uint8 [2][L][L]).
+
+    Returns (C, steps, flag) or, with trace=True, (C, steps, flag, anyons_per_step).
+    """
+    N = np.ascontiguousarray(N, dtype=np.uint8)
+    L = N.shape[-1]
+    C = np.zeros_like(N)
+    steps = ctypes.c_int32()
+    tr = np.zeros(max(1, max_steps), dtype=np.int32) if trace else None
+    flag = _load().qo_decode_shot(N, L, v, m_max, max_steps, move_thr, seed, shot, C,
+                                  ctypes.byref(steps),
+                                  tr.ctypes.data_as(ctypes.c_void_p) if trace else None,
+                                  len(tr) if trace else 0)
+    if trace:
+        return C, steps.value, flag, tr[: min(steps.value, len(tr))].copy()
+    return C, steps.value, flag
+
+
+def decode_syndrome_shot(anyon: np.ndarray, *, v: int = V_DEFAULT, m_max: int = M_MAX_DEFAULT,
+                         max_steps: int = 4096, move_thr: int = 0, seed: int = 0, shot: int = 0):
+    """Decode a pure syndrome (uint8 [L][L], 1 = anyon).  Returns (C, steps, flag, cut)."""
+    anyon = np.ascontiguousarray(anyon, dtype=np.uint8)
+    L = anyon.shape[-1]
+    C = np.zeros((2, L, L), dtype=np.uint8)
+    cut = np.zeros(2, dtype=np.uint8)
+    steps = ctypes.c_int32()
+    flag = _load().qo_decode_syndrome_shot(anyon, L, v, m_max, max_steps, move_thr, seed, shot,
+                                           C, ctypes.byref(steps), cut)
+    return C, steps.value, flag, cut
+
+
+def decode_batch(N: np.ndarray, *, v: int = V_DEFAULT, m_max: int = M_MAX_DEFAULT,
+                 max_steps: int = 4096, move_thr: int = 0, seed: int = 0, shot0: int = 0):
+    """Decode uint8 [shots][2][L][L].  Returns (C, steps int32[shots], flags uint8[shots])."""
+    N = np.ascontiguousarray(N, dtype=np.uint8)
+    shots, L = N.shape[0], N.shape[-1]
+    C = np.zeros_like(N)
+    steps = np.zeros(shots, dtype=np.int32)
+    flags = np.zeros(shots, dtype=np.uint8)
+    if shots:
+        _load().qo_decode_batch(N, L, shot0, shots, v, m_max, max_steps, move_thr, seed, C, steps,
+                                flags)
+    return C, steps, flags

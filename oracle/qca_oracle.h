@@ -1,0 +1,77 @@
+/*
+ * qca_oracle.h -- plain, slow, single-threaded CPU oracle of the synchronous
+ * message-passing automaton decoder for the 2D toric code (arXiv 2506.03266).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code exists to check the CUDA library.  Only
+ * the test-suite, the smoke entry point and the CPU-baseline leg of the bench
+ * may load it; the product path never does.  It shares no code, header, table
+ * or constant generator with the CUDA path.
+ *
+ * Conventions (all arrays row-major, periodic L x L torus, L >= 3):
+ *   site r = (x, y), index y*L + x.
+ *   edge bits: uint8 [2][L][L]; plane 0 holds e_x(r) = <r, r + x^>, plane 1
+ *   holds e_y(r) = <r, r + y^>.  (Qubits live on links, Sec. 2.)
+ *   sigma: int8 [L][L] with values +1 / -1 (the vertex-stabiliser eigenvalue;
+ *   -1 marks an anyon, Def. "synchronous automaton decoder", Eq. adef).
+ *   message fields m^{s a}: int32 [4][L][L], field order
+ *     k = 0: (+,x)   k = 1: (-,x)   k = 2: (+,y)   k = 3: (-,y)
+ *   with values in {0, 1, ..., m_max}; 0 means "no message" (Eq. mvals).
+ *   forces f^a: int8 [2][L][L] (a = x, y), values in {-1, 0, +1}.
+ */
+#ifndef QCA_ORACLE_H
+#define QCA_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014). */
+uint64_t qo_splitmix64(uint64_t z);
+/* floor(p * 2^64) clamped to [0, 2^64 - 1]; an edge flips iff u < threshold. */
+uint64_t qo_prob_threshold(double p);
+/* i.i.d. bit-flip noise of strength p (Sec. 7): shots [shot0, shot0+shots). */
+void qo_sample_errors(int L, int64_t shot0, int64_t shots, uint64_t thr, uint64_t seed,
+                      uint8_t* out_edges);
+/* sigma_r from the parity of the four links incident to r (Def. synch_ccqs). */
+void qo_syndrome(int L, const uint8_t* edges, int8_t* sigma);
+/* One application of the automaton rule A^(D), D = 2 (Def. Dd_msg_passing). */
+void qo_message_substep(int L, int m_max, const int8_t* sigma, const int32_t* m_in,
+                        int32_t* m_out);
+/* Forces f^a_r of Eqs. blahdef / degbreak for every anyon site (0 elsewhere). */
+void qo_forces(int L, const int8_t* sigma, const int32_t* m, int8_t* f);
+/* Links flipped by the feedback operator of Eq. ddfeedback: uint8 [2][L][L]. */
+void qo_feedback_links(int L, const int8_t* sigma, const int8_t* f, uint8_t* flips);
+/* One decoder time step in place: v message sub-steps, forces, feedback,
+ * correction update C ^= F and syndrome update sigma <- sigma * sigma_F.
+ * move_thr > 0 enables the optional random-move rule (Sec. 5, corollary on
+ * limited memory): an anyon whose draw is below move_thr moves in a random
+ * direction instead.  flips_out (may be NULL) receives the flipped links.
+ * Returns the number of anyons after the step. */
+int qo_step(int L, int v, int m_max, uint64_t move_thr, uint64_t seed, int64_t shot,
+            int32_t t, int8_t* sigma, int32_t* m, uint8_t* C, uint8_t* flips_out);
+/* Cut parities of a link set R: wx = XOR_y R.e_x((0,y)), wy = XOR_x R.e_y((x,0)). */
+void qo_cut_parity(int L, const uint8_t* R, int* wx, int* wy);
+/* Decode one shot whose noise realisation is N (Sec. 7; Def. plogandtdec).
+ * Writes the correction C, the number of feedback steps, and the failure flag
+ * (0 success, 1 nontrivial homology of N xor C, 2 step budget exhausted).
+ * anyon_trace (may be NULL) receives the anyon count after each step, at most
+ * trace_cap entries.  Returns the flag. */
+int qo_decode_shot(const uint8_t* N, int L, int v, int m_max, int max_steps,
+                   uint64_t move_thr, uint64_t seed, int64_t shot,
+                   uint8_t* C, int32_t* steps, int32_t* anyon_trace, int trace_cap);
+/* Same, from a pure syndrome (anyon indicator uint8 [L][L], 1 = anyon).
+ * Writes C, steps, and the cut parities of C alone in cut[0] (wx) / cut[1]
+ * (wy).  Returns 0 if the syndrome emptied, 2 if the budget ran out. */
+int qo_decode_syndrome_shot(const uint8_t* anyon, int L, int v, int m_max, int max_steps,
+                            uint64_t move_thr, uint64_t seed, int64_t shot,
+                            uint8_t* C, int32_t* steps, uint8_t* cut);
+/* Loop of qo_decode_shot over shots [shot0, shot0+shots); arrays are per shot. */
+void qo_decode_batch(const uint8_t* N, int L, int64_t shot0, int64_t shots, int v, int m_max,
+                     int max_steps, uint64_t move_thr, uint64_t seed,
+                     uint8_t* C, int32_t* steps, uint8_t* flags);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
