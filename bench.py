@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the message-passing automaton decoder on GB300.
+
+Workload (one "step" = one pass of the whole hot path over one batch):
+decode 100 000 shots of the plain automaton on the L = 256 toric code under
+i.i.d. bit-flip noise p = 0.05 (seed 0, v = 3, m_max = 255, budget 4096
+steps): syndrome measurement, message sweeps, feedback, early exit and the
+homology check, all inside libqca's kernels.  The noise is sampled once on the
+device before timing (inputs resident in HBM; 13.1 GB, larger than L2).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank decodes its
+own batch (weak scaling; no data-path collective) and the time is the max over
+ranks.  --impl reference times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L_DEFAULT = 256
+P_DEFAULT = 0.05
+SHOTS_DEFAULT = 100_000
+MAX_STEPS = 4096
+METRIC = "shot-decodes/s and site-updates/s at L=256,p=0.05 (plain vs net+CA, same p_log)"
+UNIT = "shot-decodes/s"
+
+# Integer-ALU roofline of the sweep (derivation in the design doc): the fused
+# v = 3 message update costs 16 min/compare lane-ops per site-update (4 fields x
+# (3 two-input mins of the width-7 cone window + 1 clamp)); the ALU pipe issues
+# 64 32-bit instructions / clk / SM (measured with a microbenchmark on GB300:
+# LOP3, IMNMX and the native 16x2 VIMNMX all issue at this rate), each carrying
+# 2 16-bit lanes; 152 SMs at the 2070 MHz maximum SM clock.
+ALU_OPS_PER_SITE_UPDATE = 16
+ALU_PEAK_LANE_OPS = 152 * 64 * 2 * 2.070e9
+
+# DRAM traffic per launch of the dominant kernel, from the ncu capture named in
+# the comment; None until captured for the current kernel version.
+TRAFFIC_BYTES_PER_LAUNCH = None
+
+
+def _oracle_worker(args):
+    """CPU-baseline worker: decode shots with the oracle (spawned process)."""
+    L, p, seed, shot, max_steps = args
+    import oracle
+    N = oracle.sample_errors(L, 1, p, seed, shot0=shot)[0]
+    t0 = time.perf_counter()
+    C, steps, flag = oracle.decode_shot(N, max_steps=max_steps)
+    return shot, steps, flag, time.perf_counter() - t0
+
+
+def cpu_oracle_rate(L, p, seed, seconds, cores, first_shot=0):
+    """Decode shots first_shot, first_shot+1, ... with the oracle on `cores`
+    processes until `seconds` of wall time pass; returns a dict of rates."""
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    done, steps_sum = 0, 0
+    t0 = time.perf_counter()
+    pool = ctx.Pool(cores)
+    try:
+        it = pool.imap_unordered(_oracle_worker,
+                                 ((L, p, seed, first_shot + i, MAX_STEPS) for i in range(10**7)))
+        while True:
+            left = seconds - (time.perf_counter() - t0)
+            if left <= 0:
+                break
+            try:
+                shot, steps, flag, dt = it.next(timeout=left)
+            except (mp.TimeoutError, StopIteration):
+                break
+            done += 1
+            steps_sum += steps
+    finally:
+        el = time.perf_counter() - t0
+        pool.terminate()
+        pool.join()
+    return {"shots": done, "elapsed": el, "shot_rate": done / el,
+            "site_update_rate": steps_sum * L * L / el}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_reference(args, rank):
+    """Reference arm: the CPU oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    per_step = max(2.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(args.L, args.p, 0, per_step / 2, cores)
+    rates, sites = [], []
+    shot = 0
+    for _ in range(args.steps):
+        r = cpu_oracle_rate(args.L, args.p, 0, per_step, cores, first_shot=shot)
+        shot += r["shots"]
+        rates.append(r["shot_rate"])
+        sites.append(r["site_update_rate"])
+    val = statistics.mean(rates)
+    sample = (f"{args.steps} samples of ~{per_step:.0f} s each: consecutive shots of the "
+              f"L={args.L}, p={args.p} workload (seed 0) decoded by the CPU oracle, "
+              f"{cores} processes")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "site_updates_per_s": statistics.mean(sites),
+        "config": workload_config(args),
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {
+        "workload": (f"plain message-passing automaton decode, L={args.L} toric code, "
+                     f"i.i.d. bit-flip p={args.p} (seed 0), {args.shots} shots per GPU, v=3, "
+                     f"m_max=255, step budget {MAX_STEPS}"),
+        "L": args.L, "p": args.p, "shots_per_gpu": args.shots, "max_steps": MAX_STEPS,
+        "l2": "inputs larger than L2 (no flush needed)",
+        "parallelism": f"shots sharded, {args.gpus} independent GPU batches (weak)",
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--L", type=int, default=L_DEFAULT)
+    ap.add_argument("--p", type=float, default=P_DEFAULT)
+    ap.add_argument("--shots", type=int, default=SHOTS_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    # CPU baseline before the first GPU call (oracle pool is spawned)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        r = cpu_oracle_rate(args.L, args.p, 0, 15.0, cores)
+        cpu = {"value": r["shot_rate"], "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": (f"{r['shots']} consecutive shots (from shot 0) of the same workload "
+                          f"decoded by the CPU oracle in {r['elapsed']:.1f} s on {cores} "
+                          f"processes; site-updates/s {r['site_update_rate']:.3e}")}
+
+    import torch
+    import paper_2506_03266_gb300 as qca
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    qca.build()
+    qca.lib()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    L, shots = args.L, args.shots
+    stream = torch.cuda.current_stream()
+    # each rank its own shots (seeded by rank), sampled on the device
+    N = qca.sample_errors(L, shots, args.p, seed=0, shot0=rank * shots)
+    C = torch.empty_like(N)
+    steps = torch.empty(shots, dtype=torch.int32, device="cuda")
+    fail = torch.empty(shots, dtype=torch.uint8, device="cuda")
+    out = (C, steps, fail)
+    path = qca.kernel_path(L)
+
+    for _ in range(args.warmup):
+        qca.decode_batch(N, MAX_STEPS, out=out)
+    barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        evs[i][0].record(stream)
+        qca.decode_batch(N, MAX_STEPS, out=out)
+        evs[i][1].record(stream)
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    kernel_ms = [a.elapsed_time(b) for a, b in evs]
+    launches = args.steps  # one sweep-kernel launch per decode call
+
+    steps_h = steps.cpu()
+    fail_h = fail.cpu()
+    site_updates = int(steps_h.to(torch.int64).sum()) * L * L
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        su = torch.tensor([site_updates], device="cuda", dtype=torch.int64)
+        dist.all_reduce(su)
+        site_updates_all = int(su.item())
+    else:
+        site_updates_all = site_updates
+    ms_per_step = total_ms / args.steps
+    value = world * shots / (ms_per_step / 1e3)
+    su_rate = site_updates_all / (ms_per_step / 1e3)
+
+    # end to end through the host-buffer C-ABI entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        Nh = N.cpu().pin_memory()
+        steps_o = torch.empty(shots, dtype=torch.int32, pin_memory=True)
+        fail_o = torch.empty(shots, dtype=torch.uint8, pin_memory=True)
+        qca.decode_batch_host(Nh, MAX_STEPS, correction=False,
+                              out=(None, steps_o, fail_o))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            qca.decode_batch_host(Nh, MAX_STEPS, correction=False, out=(None, steps_o, fail_o))
+        barrier()
+        el = (time.perf_counter() - t0) / args.steps
+        if dist is not None:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        assert torch.equal(steps_o, steps_h) and torch.equal(fail_o, fail_h)
+        e2e = {"value": world * shots / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(Nh.numel()), "d2h_bytes_per_step": shots * 5}
+        del Nh
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    kernel_s = statistics.mean(kernel_ms) / 1e3
+    achieved = ALU_OPS_PER_SITE_UPDATE * site_updates / kernel_s
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "site_updates_per_s": su_rate,
+        "config": dict(workload_config(args), kernel_path=path),
+        "decoder": {"p_log": float((fail_h > 0).float().mean()),
+                    "budget_exhausted": int((fail_h == 2).sum()),
+                    "mean_steps": float(steps_h.float().mean()),
+                    "p99_steps": float(torch.quantile(steps_h.float(), 0.99)),
+                    "max_steps_seen": int(steps_h.max())},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": ALU_PEAK_LANE_OPS / 1e9,
+                     "unit": "Glane-op/s", "frac": achieved / ALU_PEAK_LANE_OPS,
+                     "traffic": TRAFFIC_BYTES_PER_LAUNCH,
+                     "kernel_ms": statistics.mean(kernel_ms)},
+        "clocks": clk,
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,147 @@
+/*
+ * qca.h -- C ABI of libqca, a GB300 (sm_103a) implementation of the local
+ * message-passing automaton decoder of arXiv 2506.03266 ("Fast offline
+ * decoding with local message-passing automata") for the 2D toric code.
+ *
+ * The decoder (Sec. 3.2, Def. "D-dimensional message passing automaton", D = 2,
+ * run as a synchronous automaton decoder, Def. "synchronous automaton decoder"):
+ * every site of an L x L torus holds four message fields m^{+x}, m^{-x}, m^{+y},
+ * m^{-y}.  One time step applies the automaton rule v times with the syndrome
+ * held fixed (messages are emitted by anyons, propagate one site per sub-step
+ * along their direction over an infinity-norm light cone, and carry the
+ * distance travelled; smaller values overwrite larger), then moves every anyon
+ * one link toward the smallest message it holds (feedback, Eq. ddfeedback);
+ * anyons that meet annihilate.  Steps repeat until no anyon is left or the
+ * step budget is spent; the logical failure check follows (Def. plogandtdec,
+ * Sec. 7.2).
+ *
+ * Conventions shared by every entry point:
+ *   - site r = (x, y), 0 <= x, y < L, row-major index y*L + x; periodic.
+ *   - edge (qubit) arrays: uint8 [shots][2][L][L], values 0 / 1.  Plane 0 is
+ *     e_x(r) = <r, r + x^>, plane 1 is e_y(r) = <r, r + y^>.
+ *   - all array pointers are caller-owned DEVICE memory unless the entry point
+ *     name ends in _host; the library never frees them.
+ *   - "stream" arguments are cudaStream_t handles passed as void*; NULL means
+ *     the legacy default stream.  *_async calls return after enqueueing; the
+ *     others synchronise before returning.
+ *   - return value: 0 on success, or a negative QCA_ERR_* code; on error
+ *     qca_last_error() describes the cause.  No entry point aborts, traps or
+ *     prints.  Every device loop is bounded by max_steps.
+ */
+#ifndef QCA_H
+#define QCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QCA_OK 0
+#define QCA_ERR_ARG (-1)         /* bad argument: L < 3, negative count, NULL pointer ... */
+#define QCA_ERR_UNSUPPORTED (-2) /* size or option outside what the kernels support      */
+#define QCA_ERR_CUDA (-3)        /* a CUDA runtime call or kernel launch failed           */
+#define QCA_ERR_WATCHDOG (-4)    /* a bounded device wait gave up                          */
+
+#define QCA_MAX_L 1024       /* largest lattice any kernel accepts                  */
+#define QCA_MAX_STEPS (1 << 20)
+
+/* Decoder options.  Defaults (qca_default_config) are the paper's numerics
+ * (Sec. 7: v = 3, deterministic rule) with an 8-bit message register. */
+typedef struct qca_config {
+  int32_t v;             /* message sub-steps per time step (A^(v,D) = (A^(D))^v, Def.
+                            Dd_msg_passing); supported: 1..8; default 3                     */
+  int32_t m_max;         /* message cap (Eq. mvals); values above it disappear; 1..255;
+                            default 255                                                     */
+  double p_move;         /* probability that an anyon moves in a uniformly random direction
+                            instead of following its messages (the random motion of the
+                            limited-memory corollary of Sec. 5.1); default 0                 */
+  int64_t shot_offset;   /* index of this batch's first shot in the random-move stream;
+                            default 0                                                       */
+} qca_config;
+
+/* Fill *cfg with the defaults above.  Returns QCA_ERR_ARG if cfg is NULL. */
+int qca_default_config(qca_config* cfg);
+
+/* i.i.d. bit-flip noise of strength p on every link (Sec. 7 numerics, the
+ * i.i.d. case of Eq. final_channel).  Writes out_errors, device uint8
+ * [shots][2][L][L].  Link e of shot s (e = 2*(y*L+x) + plane, s counted from
+ * shot0) flips iff splitmix64(splitmix64(splitmix64(seed ^ 0x4E4F495345) ^ s) ^ e)
+ * < floor(p * 2^64), so the same (seed, shot, link) gives the same draw at any
+ * batch split, and a lower p flips a subset of a higher p's links.
+ * Errors: QCA_ERR_ARG for L < 3, L > QCA_MAX_L, shots < 0, NULL with shots > 0,
+ * p outside [0, 1]. */
+int qca_sample_errors(int L, int shots, double p, uint64_t seed, uint8_t* out_errors);
+int qca_sample_errors_async(int L, int64_t shot0, int64_t shots, double p, uint64_t seed,
+                            uint8_t* out_errors, void* stream);
+
+/* Decode a batch of noise realisations (the decoding problem of
+ * Def. plogandtdec; Sec. 7 Monte Carlo).
+ *   syndrome          device uint8 [shots][2][L][L]: the per-shot noise realisation N
+ *                     (link bits); the syndrome sigma is measured from it on the device
+ *                     (Def. synch_ccqs).  N is needed because the failure flag is a
+ *                     property of N xor C, not of sigma alone.
+ *   L                 lattice size, 3 <= L <= QCA_MAX_L
+ *   shots             number of independent shots, >= 0
+ *   max_steps         step budget per shot, 0 <= max_steps <= QCA_MAX_STEPS
+ *   rng_seed          seed of the optional random-move rule; unused with p_move = 0
+ *   out_correction    device uint8 [shots][2][L][L]: the applied correction C
+ *   out_steps         device int32 [shots]: feedback steps until no anyon is left
+ *                     (T_dec of the shot, Eq. tdecrhodef), or max_steps
+ *   out_logical_fail  device uint8 [shots]: 0 success; 1 N xor C wraps a torus cycle
+ *                     (either cycle, Sec. 7.2); 2 the budget ran out with anyons left
+ * Uses the default qca_config; synchronises.  Outputs are bit-identical to the
+ * library's CPU oracle for every input.  Errors: QCA_ERR_ARG (sizes, NULL with
+ * shots > 0), QCA_ERR_UNSUPPORTED, QCA_ERR_CUDA. */
+int qca_decode_batch(const uint8_t* syndrome, int L, int shots, int max_steps,
+                     uint64_t rng_seed, uint8_t* out_correction, int32_t* out_steps,
+                     uint8_t* out_logical_fail);
+/* As qca_decode_batch with options (cfg may be NULL for the defaults), enqueued
+ * on `stream` without synchronising. */
+int qca_decode_batch_async(const uint8_t* syndrome, int L, int64_t shots, int max_steps,
+                           uint64_t rng_seed, uint8_t* out_correction, int32_t* out_steps,
+                           uint8_t* out_logical_fail, const qca_config* cfg, void* stream);
+
+/* Decode pure syndromes: sigma is device uint8 [shots][L][L] with 1 marking an
+ * anyon (sigma_r = -1).  Writes the correction C, the steps, out_cut_parity
+ * device uint8 [shots][2] = (w_x, w_y) of C alone (w_x = XOR over y of
+ * C.e_x((0,y)), w_y = XOR over x of C.e_y((x,0))), and out_exhausted device
+ * uint8 [shots] (1 if the budget ran out; may be NULL).  Because N xor C is a
+ * cycle on success, the caller's failure flag is cut(N) xor cut(C).  An odd
+ * number of anyons cannot empty and runs to the budget. */
+int qca_decode_syndrome_batch_async(const uint8_t* sigma, int L, int64_t shots, int max_steps,
+                                    uint64_t rng_seed, uint8_t* out_correction,
+                                    int32_t* out_steps, uint8_t* out_cut_parity,
+                                    uint8_t* out_exhausted, const qca_config* cfg,
+                                    void* stream);
+
+/* End-to-end form of qca_decode_batch on HOST buffers (same layouts): copies
+ * the noise to the device in chunks, decodes, and copies the correction, steps
+ * and flags back, overlapping transfers with decoding.  Host buffers should be
+ * page-locked for full speed.  out_correction may be NULL (not copied back).
+ * Uses a device staging workspace cached by the library (qca_free_workspace
+ * releases it).  Synchronises. */
+int qca_decode_batch_host(const uint8_t* syndrome, int L, int64_t shots, int max_steps,
+                          uint64_t rng_seed, uint8_t* out_correction, int32_t* out_steps,
+                          uint8_t* out_logical_fail, const qca_config* cfg);
+
+/* Kernel path chosen for a lattice size: 1 = on-chip fast sweep, 2 = on-chip
+ * sweep on a 2-CTA cluster, 0 = generic sweep with HBM-resident state.
+ * Returns a negative code for an unsupported L. */
+int qca_kernel_path(int L, const qca_config* cfg);
+
+/* Release the device workspaces the library caches (generic-kernel state and
+ * host-path staging buffers) on the current device. */
+int qca_free_workspace(void);
+
+/* Static, thread-local description of the last error (never NULL). */
+const char* qca_last_error(void);
+
+/* ABI version: 100 * major + minor. */
+int qca_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QCA_H */

@@ -1,0 +1,214 @@
+"""Python binding of libqca, the GB300 message-passing automaton decoder.
+
+Thin ctypes marshalling over the C ABI declared in include/qca.h: every
+computation runs in the library's CUDA kernels.  PyTorch only provides device
+memory and the current CUDA stream.  There is no CPU fallback: if libqca.so is
+missing or no CUDA device is present, the compute functions raise.
+
+    import paper_2506_03266_gb300 as qca
+    N = qca.sample_errors(L=256, shots=1000, p=0.05, seed=0)      # cuda uint8
+    C, steps, fail = qca.decode_batch(N, max_steps=4096)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqca.so")
+
+QCA_OK = 0
+QCA_ERR_ARG = -1
+QCA_ERR_UNSUPPORTED = -2
+QCA_ERR_CUDA = -3
+QCA_ERR_WATCHDOG = -4
+QCA_MAX_L = 1024
+QCA_MAX_STEPS = 1 << 20
+
+_lock = threading.Lock()
+_lib = None
+
+
+class QcaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libqca error {code}: {msg}")
+        self.code = code
+
+
+class QcaConfig(ctypes.Structure):
+    """Mirror of struct qca_config (include/qca.h)."""
+    _fields_ = [("v", ctypes.c_int32), ("m_max", ctypes.c_int32), ("p_move", ctypes.c_double),
+                ("shot_offset", ctypes.c_int64)]
+
+
+def build(force: bool = False) -> str:
+    from . import builder
+    return builder.build(force=force)
+
+
+def lib():
+    """Load libqca.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libqca.so not built at {LIB_PATH}; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
+        cfgp = ctypes.POINTER(QcaConfig)
+        sig = {
+            "qca_version": ([], i32),
+            "qca_last_error": ([], ctypes.c_char_p),
+            "qca_default_config": ([cfgp], i32),
+            "qca_sample_errors": ([i32, i32, ctypes.c_double, u64, vp], i32),
+            "qca_sample_errors_async": ([i32, i64, i64, ctypes.c_double, u64, vp, vp], i32),
+            "qca_decode_batch": ([vp, i32, i32, i32, u64, vp, vp, vp], i32),
+            "qca_decode_batch_async": ([vp, i32, i64, i32, u64, vp, vp, vp, cfgp, vp], i32),
+            "qca_decode_syndrome_batch_async": ([vp, i32, i64, i32, u64, vp, vp, vp, vp, cfgp, vp],
+                                                i32),
+            "qca_decode_batch_host": ([vp, i32, i64, i32, u64, vp, vp, vp, cfgp], i32),
+            "qca_kernel_path": ([i32, cfgp], i32),
+            "qca_free_workspace": ([], i32),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != QCA_OK:
+        raise QcaError(rc, lib().qca_last_error().decode())
+
+
+def last_error() -> str:
+    return lib().qca_last_error().decode()
+
+
+def make_config(v: int = 3, m_max: int = 255, p_move: float = 0.0,
+                shot_offset: int = 0) -> QcaConfig:
+    c = QcaConfig()
+    _check(lib().qca_default_config(ctypes.byref(c)))
+    c.v, c.m_max, c.p_move, c.shot_offset = v, m_max, p_move, shot_offset
+    return c
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libqca needs a CUDA device; no CPU fallback exists")
+    return torch
+
+
+def _stream(torch, stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_u8(torch, t, shape, name):
+    if not (t.is_cuda and t.dtype == torch.uint8 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous cuda uint8 tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+def kernel_path(L: int, v: int = 3) -> int:
+    rc = lib().qca_kernel_path(L, ctypes.byref(make_config(v=v)))
+    if rc < 0:
+        _check(rc)
+    return rc
+
+
+def sample_errors(L: int, shots: int, p: float, seed: int, shot0: int = 0, out=None,
+                  stream=None):
+    """i.i.d. link flips (uint8 [shots][2][L][L] on the current cuda device)."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty((shots, 2, L, L), dtype=torch.uint8, device="cuda")
+    _dev_u8(torch, out, (shots, 2, L, L), "out")
+    _check(lib().qca_sample_errors_async(L, shot0, shots, float(p), seed & (2**64 - 1),
+                                         ctypes.c_void_p(out.data_ptr()),
+                                         _stream(torch, stream)))
+    return out
+
+
+def decode_batch(errors, max_steps: int = 4096, rng_seed: int = 0, *, v: int = 3,
+                 m_max: int = 255, p_move: float = 0.0, shot_offset: int = 0, out=None,
+                 stream=None):
+    """Decode noise realisations uint8 [shots][2][L][L] (cuda).
+
+    Returns (correction uint8 [shots][2][L][L], steps int32 [shots],
+    logical_fail uint8 [shots]); enqueued on the current stream.
+    """
+    torch = _torch()
+    shots, L = errors.shape[0], errors.shape[-1]
+    _dev_u8(torch, errors, (shots, 2, L, L), "errors")
+    if out is None:
+        C = torch.empty_like(errors)
+        steps = torch.empty(shots, dtype=torch.int32, device=errors.device)
+        fail = torch.empty(shots, dtype=torch.uint8, device=errors.device)
+    else:
+        C, steps, fail = out
+    cfg = make_config(v, m_max, p_move, shot_offset)
+    _check(lib().qca_decode_batch_async(
+        ctypes.c_void_p(errors.data_ptr()), L, shots, max_steps, rng_seed & (2**64 - 1),
+        ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(steps.data_ptr()),
+        ctypes.c_void_p(fail.data_ptr()), ctypes.byref(cfg), _stream(torch, stream)))
+    return C, steps, fail
+
+
+def decode_syndrome_batch(sigma, max_steps: int = 4096, rng_seed: int = 0, *, v: int = 3,
+                          m_max: int = 255, p_move: float = 0.0, shot_offset: int = 0,
+                          stream=None):
+    """Decode anyon indicators uint8 [shots][L][L] (cuda, 1 = anyon).
+
+    Returns (correction, steps, cut_parity uint8 [shots][2], exhausted uint8 [shots]).
+    """
+    torch = _torch()
+    shots, L = sigma.shape[0], sigma.shape[-1]
+    _dev_u8(torch, sigma, (shots, L, L), "sigma")
+    C = torch.empty((shots, 2, L, L), dtype=torch.uint8, device=sigma.device)
+    steps = torch.empty(shots, dtype=torch.int32, device=sigma.device)
+    cut = torch.empty((shots, 2), dtype=torch.uint8, device=sigma.device)
+    exh = torch.empty(shots, dtype=torch.uint8, device=sigma.device)
+    cfg = make_config(v, m_max, p_move, shot_offset)
+    _check(lib().qca_decode_syndrome_batch_async(
+        ctypes.c_void_p(sigma.data_ptr()), L, shots, max_steps, rng_seed & (2**64 - 1),
+        ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(steps.data_ptr()),
+        ctypes.c_void_p(cut.data_ptr()), ctypes.c_void_p(exh.data_ptr()), ctypes.byref(cfg),
+        _stream(torch, stream)))
+    return C, steps, cut, exh
+
+
+def decode_batch_host(errors, max_steps: int = 4096, rng_seed: int = 0, *, v: int = 3,
+                      m_max: int = 255, p_move: float = 0.0, correction: bool = True,
+                      out=None):
+    """End-to-end decode of HOST tensors (uint8 [shots][2][L][L], ideally pinned).
+
+    Returns host tensors (correction or None, steps, logical_fail).
+    """
+    torch = _torch()
+    if errors.is_cuda or errors.dtype != torch.uint8 or not errors.is_contiguous():
+        raise ValueError("errors must be a contiguous host uint8 tensor")
+    shots, L = errors.shape[0], errors.shape[-1]
+    if out is None:
+        pin = errors.is_pinned()
+        C = torch.empty_like(errors, pin_memory=pin) if correction else None
+        steps = torch.empty(shots, dtype=torch.int32, pin_memory=pin)
+        fail = torch.empty(shots, dtype=torch.uint8, pin_memory=pin)
+    else:
+        C, steps, fail = out
+    cfg = make_config(v, m_max, p_move, 0)
+    _check(lib().qca_decode_batch_host(
+        ctypes.c_void_p(errors.data_ptr()), L, shots, max_steps, rng_seed & (2**64 - 1),
+        ctypes.c_void_p(C.data_ptr()) if C is not None else None,
+        ctypes.c_void_p(steps.data_ptr()), ctypes.c_void_p(fail.data_ptr()), ctypes.byref(cfg)))
+    return C, steps, fail
+
+
+def free_workspace():
+    _check(lib().qca_free_workspace())

@@ -1,0 +1,61 @@
+// Internal declarations shared by the libqca CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qca.h"
+
+namespace qca {
+
+// Stream tags of the counter-based generator (ASCII "NOISE" and "MOVE").
+constexpr uint64_t kTagNoise = 0x4E4F495345ULL;
+constexpr uint64_t kTagMove = 0x4D4F5645ULL;
+
+// SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014): golden-gamma
+// increment, then the variant-13 mix.  Device copy of the published definition.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Everything a sweep kernel needs for one batch.
+struct DecodeArgs {
+  const uint8_t* in;       // noise N [shots][2][L][L], or sigma [shots][L][L] if from_sigma
+  int L;
+  int64_t shots;
+  int max_steps;
+  int v;                   // message sub-steps per step
+  int m_max;               // message cap (1..255)
+  uint64_t move_thr;       // random-move threshold (0 = deterministic rule)
+  uint64_t move_key;       // splitmix64(seed ^ kTagMove)
+  int64_t shot_offset;     // global index of shot 0 of this batch
+  int from_sigma;          // input is a syndrome, not a noise realisation
+  uint8_t* out_C;          // [shots][2][L][L]
+  int32_t* out_steps;      // [shots]
+  uint8_t* out_flag;       // [shots]   (noise input)
+  uint8_t* out_cut;        // [shots][2] (syndrome input)
+  uint8_t* out_exhausted;  // [shots] or null (syndrome input)
+};
+
+// Per-thread error text (set by the host layer).
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+// Random-move key chain shared by the kernels: key for (shot, step).
+__device__ __forceinline__ uint64_t move_step_key(uint64_t move_key, int64_t shot, int t) {
+  uint64_t k1 = splitmix64(move_key ^ (uint64_t)shot);
+  return splitmix64(k1 ^ (uint64_t)(uint32_t)t);
+}
+
+// Launchers (return QCA_OK or an error code; errors already recorded).
+int launch_sample_errors(int L, int64_t shot0, int64_t shots, uint64_t thr, uint64_t seed,
+                         uint8_t* out, cudaStream_t stream);
+int launch_generic(const DecodeArgs& a, cudaStream_t stream);
+int generic_workspace_release();
+int fast_path_for(int L, int v);  // 0 generic, 1 single-CTA on-chip, 2 two-CTA cluster
+int launch_fast(const DecodeArgs& a, cudaStream_t stream);
+
+}  // namespace qca

@@ -1,0 +1,104 @@
+"""CPU-side checks of the C ABI: the library loads, exports every function
+include/qca.h declares, and rejects bad arguments before touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2506_03266_gb300 as qca
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    qca.build()
+    return qca.lib()
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(qca_[a-z_0-9]+)\s*\(",
+                            text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["qca_decode_batch", "qca_decode_batch_async", "qca_sample_errors",
+                 "qca_decode_syndrome_batch_async", "qca_decode_batch_host", "qca_last_error",
+                 "qca_free_workspace", "qca_default_config"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert missing == []
+
+
+def test_version_and_defaults(lib):
+    assert lib.qca_version() >= 100
+    c = qca.QcaConfig()
+    assert lib.qca_default_config(ctypes.byref(c)) == 0
+    assert (c.v, c.m_max, c.p_move, c.shot_offset) == (3, 255, 0.0, 0)
+    assert lib.qca_default_config(None) == qca.QCA_ERR_ARG
+
+
+def test_argument_errors_need_no_gpu(lib):
+    dummy = ctypes.c_void_p(16)
+    cfg = qca.make_config()
+    # L < 3, L too large, negative shots, negative / huge budget, NULL arrays
+    assert lib.qca_decode_batch(dummy, 2, 1, 10, 0, dummy, dummy, dummy) == qca.QCA_ERR_ARG
+    assert "L = 2" in qca.last_error()
+    assert lib.qca_decode_batch(dummy, 2000, 1, 10, 0, dummy, dummy, dummy) == \
+        qca.QCA_ERR_UNSUPPORTED
+    assert lib.qca_decode_batch(dummy, 16, -1, 10, 0, dummy, dummy, dummy) == qca.QCA_ERR_ARG
+    assert lib.qca_decode_batch(dummy, 16, 1, -5, 0, dummy, dummy, dummy) == qca.QCA_ERR_ARG
+    assert lib.qca_decode_batch(dummy, 16, 1, qca.QCA_MAX_STEPS + 1, 0, dummy, dummy,
+                                dummy) == qca.QCA_ERR_ARG
+    assert lib.qca_decode_batch(None, 16, 1, 10, 0, dummy, dummy, dummy) == qca.QCA_ERR_ARG
+    assert lib.qca_decode_batch_async(dummy, 16, 1, 10, 0, None, dummy, dummy,
+                                      ctypes.byref(cfg), None) == qca.QCA_ERR_ARG
+    assert lib.qca_decode_syndrome_batch_async(dummy, 16, 1, 10, 0, dummy, dummy, None, None,
+                                               ctypes.byref(cfg), None) == qca.QCA_ERR_ARG
+    assert lib.qca_sample_errors(16, 1, 1.5, 0, dummy) == qca.QCA_ERR_ARG
+    assert lib.qca_sample_errors(16, 1, 0.1, 0, None) == qca.QCA_ERR_ARG
+    assert lib.qca_decode_batch_host(None, 16, 1, 10, 0, None, None, None, None) == \
+        qca.QCA_ERR_ARG
+    # unsupported options
+    bad = qca.make_config(v=0)
+    assert lib.qca_decode_batch_async(dummy, 16, 1, 10, 0, dummy, dummy, dummy,
+                                      ctypes.byref(bad), None) == qca.QCA_ERR_UNSUPPORTED
+    bad = qca.make_config(m_max=256)
+    assert lib.qca_decode_batch_async(dummy, 16, 1, 10, 0, dummy, dummy, dummy,
+                                      ctypes.byref(bad), None) == qca.QCA_ERR_UNSUPPORTED
+    bad = qca.make_config(p_move=-0.1)
+    assert lib.qca_decode_batch_async(dummy, 16, 1, 10, 0, dummy, dummy, dummy,
+                                      ctypes.byref(bad), None) == qca.QCA_ERR_ARG
+    # zero shots: nothing to do, NULL allowed, no device call
+    assert lib.qca_decode_batch_async(None, 16, 0, 10, 0, None, None, None, None, None) == 0
+    assert lib.qca_sample_errors_async(16, 0, 0, 0.1, 0, None, None) == 0
+
+
+def test_kernel_path_table(lib):
+    assert qca.kernel_path(16) >= 0
+    assert qca.kernel_path(256) >= 0
+    assert qca.kernel_path(1024) >= 0
+    with pytest.raises(qca.QcaError):
+        qca.kernel_path(2)
+
+
+def test_product_path_does_not_import_oracle():
+    """The CUDA path and the oracle share nothing; the package never names it."""
+    pkg = os.path.join(ROOT, "paper_2506_03266_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, fn)).read()
+                assert "import oracle" not in text and "qca_oracle" not in text, fn
