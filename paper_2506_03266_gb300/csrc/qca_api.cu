@@ -81,7 +81,7 @@ static int check_sizes(int L, int64_t shots, int max_steps) {
 
 static int dispatch(DecodeArgs& a, cudaStream_t stream) {
   if (a.shots == 0) return QCA_OK;
-  if (fast_path_for(a.L, a.v) > 0) return launch_fast(a, stream);
+  if (fast_path_for(a.L, a.v, a.m_max) > 0) return launch_fast(a, stream);
   return launch_generic(a, stream);
 }
 
@@ -199,7 +199,7 @@ int qca_kernel_path(int L, const qca_config* cfg) {
   if (rc) return rc;
   qca_config c;
   if ((rc = check_config(cfg, &c))) return rc;
-  return fast_path_for(L, c.v);
+  return fast_path_for(L, c.v, c.m_max);
 }
 
 int qca_decode_batch_host(const uint8_t* syndrome, int L, int64_t shots, int max_steps,
@@ -226,7 +226,7 @@ int qca_decode_batch_host(const uint8_t* syndrome, int L, int64_t shots, int max
   if (chunk < 1) chunk = 1;
   if (chunk > shots) chunk = shots;
   const size_t per_set = ((chunk * E + 255) & ~(size_t)255) * 2 + ((chunk * 5 + 255) & ~(size_t)255) + 512;
-  const bool concurrent = fast_path_for(L, c.v) > 0;  // the generic path shares one workspace
+  const bool concurrent = fast_path_for(L, c.v, c.m_max) > 0;  // the generic path shares one workspace
   std::lock_guard<std::mutex> lk(g_stage_mu);
   Staging& st = g_stage[dev];
   if (st.bytes < 2 * per_set) {

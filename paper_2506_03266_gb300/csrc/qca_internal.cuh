@@ -55,7 +55,7 @@ int launch_sample_errors(int L, int64_t shot0, int64_t shots, uint64_t thr, uint
                          uint8_t* out, cudaStream_t stream);
 int launch_generic(const DecodeArgs& a, cudaStream_t stream);
 int generic_workspace_release();
-int fast_path_for(int L, int v);  // 0 generic, 1 single-CTA on-chip, 2 two-CTA cluster
+int fast_path_for(int L, int v, int m_max);  // 0 generic, 1 single-CTA, 2 two-CTA cluster
 int launch_fast(const DecodeArgs& a, cudaStream_t stream);
 
 }  // namespace qca

@@ -1,18 +1,799 @@
-// On-chip sweep kernels (placeholder until the fast kernels land).
+// On-chip synchronous sweep for v = 3 and L a multiple of 4 (L <= 128, one CTA
+// per shot) or of 8 (128 < L <= 256, a two-CTA cluster per shot).
+//
+// State per shot, resident in shared memory for the whole decode:
+//   * four message planes of bytes, one per field (+x, -x, +y, -y).  Each plane
+//     is stored in its own frame so that its messages always travel along the
+//     byte (column) axis: the x fields as [y][x], the y fields as [x][y].
+//     Values use an offset encoding w = m - 1 + (255 - m_max), with 0xFF for
+//     "no message" (m = 0).  Then "min over nonzero neighbours", "+1" and
+//     "a value above m_max disappears" become a plain unsigned min and an add
+//     that saturates at 0xFF.
+//   * site bitmaps with rows padded to a power-of-two number of 32-bit words:
+//     sigma (current and next), flipped links, correction; and a compacted
+//     list of the current anyons ((y << 8) | x).
+//
+// One decoder step (Def. "synchronous automaton decoder"):
+//   1. message update, the v = 3 applications of A^(D) (Def. Dd_msg_passing)
+//      fused exactly into one pass: with sigma fixed, three sub-steps give
+//        w3(r) = min( [anyon on the cone section at distance d] ? off + d - 1
+//                     for d = 1, 2, 3,
+//                     satadd( min_{|j| <= 3} w0(r - 3 a^ + j b^), 3 ) ),
+//      i.e. a width-7 transverse window at longitudinal distance 3 (dense,
+//      in place with a rolling register window), then the anyon terms
+//      (sparse: each anyon writes its light-cone sections, largest value
+//      first).  The unsigned byte min runs on the native 16x2 integer min,
+//      each site in the high byte of a 16-bit lane.
+//   2. forces and feedback (Eqs. blahdef, degbreak, ddfeedback) for anyons
+//      only; a flipped-link bitmap implements the OR so a link crossed from
+//      both ends flips once; the flipping thread toggles the correction bit and
+//      sigma at both ends.
+//   3. early exit when sigma is empty; budget check.
+// The homology check and the byte outputs follow the last step.
+//
+// Two-CTA clusters (L > 128) split every plane by rows; each CTA keeps the full
+// sigma, writes the cone sections that fall in its rows, moves the anyons of its
+// rows, and reaches the partner's planes and bitmaps through distributed shared
+// memory.  Two cluster barriers per step.
+#include <cooperative_groups.h>
+
+#include <type_traits>
+
 #include "qca_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace qca {
 
-int fast_path_for(int L, int v) {
-  (void)L;
-  (void)v;
-  return 0;
+namespace {
+
+constexpr int kListCap = 16384;  // anyon-list entries (the whole lattice for L <= 128)
+
+struct FastGeom {
+  int L;
+  int rows_local;       // plane rows held by one CTA (L / CL)
+  int G;                // lanes per row segment (L / 4 / KW)
+  int spw;              // row segments per warp
+  int H;                // band height (rows per segment)
+  int bands;            // bands per plane per CTA
+  int segments;         // 4 * bands
+  int lws;              // log2 of the 32-bit words per bitmap row
+  int nws;              // words of one site bitmap (L << lws)
+  int off;              // 255 - m_max
+  int cap;              // anyon-list capacity
+  int ls;               // plane row stride in bytes: L + 4, so that a column of a
+                        // plane does not fall into one shared-memory bank
+  size_t plane_bytes;   // 4 * rows_local * ls
+};
+
+template <int CL>
+struct Cluster {
+  template <class T>
+  __device__ static __forceinline__ T* at(T* p, int r) {
+    if constexpr (CL == 1) {
+      return p;
+    } else {
+      return cg::this_cluster().map_shared_rank(p, (unsigned)r);
+    }
+  }
+  __device__ static __forceinline__ void sync() {
+    if constexpr (CL == 1) {
+      __syncthreads();
+    } else {
+      cg::this_cluster().sync();
+    }
+  }
+  __device__ static __forceinline__ int rank() {
+    if constexpr (CL == 1) {
+      return 0;
+    } else {
+      return (int)cg::this_cluster().block_rank();
+    }
+  }
+};
+
+__device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b) { return __vminu2(a, b); }
+
+// Rolling width-7 window over rows for one 16-bit-lane chain:
+//   p2(i) = min(a(i), a(i+1)), p4(i) = min(p2(i), p2(i+2)),
+//   t7(i) = min(p4(i-3), p4(i)) = min of a(i-3 .. i+3).
+struct Chain {
+  uint32_t a2;                  // a(i+2)
+  uint32_t q0, q1, q2;          // p2(i), p2(i+1), p2(i+2) (q2 set by step)
+  uint32_t r0, r1, r2;          // p4(i-3), p4(i-2), p4(i-1)
+  __device__ __forceinline__ void init(const uint32_t a[6]) {
+    // a[k] = a(k - 3), k = 0..5
+    const uint32_t pm3 = vmin2(a[0], a[1]), pm2 = vmin2(a[1], a[2]), pm1 = vmin2(a[2], a[3]);
+    const uint32_t p0 = vmin2(a[3], a[4]), p1 = vmin2(a[4], a[5]);
+    r0 = vmin2(pm3, pm1);
+    r1 = vmin2(pm2, p0);
+    r2 = vmin2(pm1, p1);
+    q0 = p0;
+    q1 = p1;
+    a2 = a[5];
+  }
+  // consume a(i+3); return t7(i)
+  __device__ __forceinline__ uint32_t step(uint32_t a3) {
+    q2 = vmin2(a2, a3);
+    const uint32_t p4 = vmin2(q0, q2);
+    const uint32_t t7 = vmin2(r0, p4);
+    a2 = a3;
+    q0 = q1;
+    q1 = q2;
+    r0 = r1;
+    r1 = r2;
+    r2 = p4;
+    return t7;
+  }
+};
+
+// High bytes of the 16-bit lanes carry the sites: the H chain holds bytes 1
+// and 3 of a natural word, the L chain (word << 8) holds bytes 0 and 2.
+__device__ __forceinline__ uint32_t finish_word(uint32_t tL, uint32_t tH) {
+  // satadd(.,3) on the high bytes: clamp at 0xFC, then +3 (no carry leaves a lane)
+  tL = vmin2(tL, 0xFCFFFCFFu) + 0x03000300u;
+  tH = vmin2(tH, 0xFCFFFCFFu) + 0x03000300u;
+  return __byte_perm(tL, tH, 0x7351);  // [L.b1, H.b1, L.b3, H.b3] = sites 0..3
+}
+
+__device__ __forceinline__ int wrapi(int i, int L) { return i < 0 ? i + L : (i >= L ? i - L : i); }
+
+template <int CL>
+__device__ __forceinline__ uint8_t* plane_ptr(uint8_t* planes, const FastGeom& g, int p, int R,
+                                              int c) {
+  const int owner = (CL == 1) ? 0 : (R >= g.rows_local ? 1 : 0);
+  const int lr = R - owner * g.rows_local;
+  return Cluster<CL>::at(planes, owner) + ((size_t)(p * g.rows_local + lr)) * g.ls + c;
+}
+
+// Direction from the four fields in offset encoding (0xFF = no message):
+// smallest value wins, ties to the smaller s*a, i.e. (-,y), (-,x), (+,x), (+,y);
+// then move toward the smaller of the two fields of the chosen axis (m^{+a}
+// comes from the -a side), no move if they are equal.
+// Codes: 0 none, 1 +x, 2 -x, 3 +y, 4 -y.
+__device__ __forceinline__ int choose_dir(uint32_t wpx, uint32_t wmx, uint32_t wpy, uint32_t wmy) {
+  uint32_t best = wmy;
+  int axis_y = 1;
+  if (wmx < best) { best = wmx; axis_y = 0; }
+  if (wpx < best) { best = wpx; axis_y = 0; }
+  if (wpy < best) { best = wpy; axis_y = 1; }
+  if (best == 0xFFu) return 0;
+  const uint32_t up = axis_y ? wpy : wpx, um = axis_y ? wmy : wmx;
+  if (up == um) return 0;
+  if (up < um) return axis_y ? 4 : 2;
+  return axis_y ? 3 : 1;
+}
+
+// 4 bytes that are each 0 or 1 -> 4 bits (byte k -> bit k).
+__device__ __forceinline__ uint32_t nibble_of(uint32_t w) { return (w * 0x01020408u) >> 24; }
+// 4 bytes -> 4 bits "byte is nonzero".
+__device__ __forceinline__ uint32_t nonzero_nibble(uint32_t w) {
+  const uint32_t nz = (((w & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w) & 0x80808080u;
+  return nibble_of(nz >> 7);
+}
+
+// Rebuild the anyon list from sigma; returns "any anyon" (block-uniform).
+__device__ __forceinline__ int build_list(const uint32_t* sig, const FastGeom& g, uint16_t* list,
+                                          int* count) {
+  // each thread owns a contiguous run of words: one scan and one atomic per warp
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+  const int wsm = (1 << g.lws) - 1;
+  const int per = (g.nws + nt - 1) / nt;
+  const int w0 = tid * per, w1 = min(g.nws, w0 + per);
+  int n = 0;
+  for (int w = w0; w < w1; ++w) n += __popc(sig[w]);
+  int incl = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  int wbase = 0;
+  if (lane == 31 && total) wbase = atomicAdd(count, total);
+  wbase = __shfl_sync(0xffffffffu, wbase, 31);
+  int pos = wbase + incl - n;
+  for (int w = w0; w < w1; ++w) {
+    uint32_t b = sig[w];
+    const int y = w >> g.lws, xb = (w & wsm) << 5;
+    while (b) {
+      const int k = __ffs(b) - 1;
+      b &= b - 1;
+      if (pos < g.cap) list[pos] = (uint16_t)((y << 8) | (xb + k));
+      ++pos;
+    }
+  }
+  return __syncthreads_or(n);
+}
+
+// Calls f(x, y) for every anyon of the current sigma, from the list when it
+// held them all, else straight from the bitmap.
+template <class F>
+__device__ __forceinline__ void for_each_anyon(const uint16_t* list, int count, const uint32_t* sig,
+                                               const FastGeom& g, F&& f) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (count <= g.cap) {
+    // The list is sorted by site; give the 32 lanes of a warp entries far apart
+    // (list index = lane-major transpose) so that their accesses spread over banks.
+    const int stride = (count + 31) >> 5;
+    for (int i = tid; i < 32 * stride; i += nt) {
+      const int idx = (i & 31) * stride + (i >> 5);
+      if (idx >= count) continue;
+      const int e = list[idx];
+      f(e & 0xFF, e >> 8);
+    }
+  } else {
+    const int wsm = (1 << g.lws) - 1;
+    for (int w = tid; w < g.nws; w += nt) {
+      uint32_t b = sig[w];
+      const int y = w >> g.lws, xb = (w & wsm) << 5;
+      while (b) {
+        const int k = __ffs(b) - 1;
+        b &= b - 1;
+        f(xb + k, y);
+      }
+    }
+  }
+}
+
+// n (<= 32) bits of bitmap row r starting at column c (c + n <= row width).
+__device__ __forceinline__ uint32_t row_bits(const uint32_t* bm, const FastGeom& g, int r, int c,
+                                             int n) {
+  const uint32_t* row = bm + (r << g.lws);
+  const int w = c >> 5, s = c & 31;
+  const uint32_t lo = row[w];
+  const uint32_t hi = (w + 1 < (1 << g.lws)) ? row[w + 1] : 0u;
+  const uint32_t v = __funnelshift_r(lo, hi, s);
+  return n >= 32 ? v : (v & ((1u << n) - 1u));
+}
+
+// Word wp of the padded copy of bitmap row r: bit k <-> column (k - 8) mod L,
+// for k in [0, L + 16), so that any window of columns [c - 8, c + 8) with
+// 0 <= c < L is contiguous.
+__device__ __forceinline__ uint32_t padded_word(const uint32_t* bm, const FastGeom& g, int r,
+                                                int wp) {
+  const int L = g.L, k0 = wp * 32;
+  uint32_t out = 0;
+  // (first padded bit, end, first column) of the three pieces
+  const int seg[3][3] = {{0, 8, L - 8}, {8, L + 8, 0}, {L + 8, L + 16, 0}};
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int lo = max(seg[s][0], k0), hi = min(seg[s][1], k0 + 32);
+    if (lo >= hi) continue;
+    int c = seg[s][2] + (lo - seg[s][0]);
+    int n = hi - lo, pos = lo - k0;
+    while (n > 0) {  // at most two chunks (a piece never crosses two word boundaries of the row)
+      const int take = min(n, 32 - (c & 31));
+      out |= row_bits(bm, g, r, c, take) << pos;
+      c += take;
+      pos += take;
+      n -= take;
+    }
+  }
+  return out;
+}
+
+// First decoder step with empty planes: the fused message update reduces to
+// the anyon terms, w(r) = off + d - 1 for the smallest d in {1, 2, 3} with an
+// anyon on the cone section at distance d, else 0xFF.  Each thread fills its
+// band of plane words.  The section at distance d of a site at longitudinal
+// position l is the transverse run of 2d + 1 sites at l -+ d, so with
+// V_d = OR of the sigma rows t-d .. t+d (frame orientation) the term is bit
+// l -+ d of V_d.  Uses sT (nws words) and scratch (4 * nws words) as
+// temporary storage; ends with a block barrier.
+template <int KW>
+__device__ void seed_planes(const uint32_t* sig, const uint16_t* list, int count, uint32_t* sT,
+                            uint32_t* scratch, const FastGeom& g, uint8_t* planes, int pl,
+                            int lrow0, int R0, bool plus, int cword, bool lane_on) {
+  const int tid = threadIdx.x, nt = blockDim.x, L = g.L;
+  const int wpp = (L + 16 + 31) >> 5;  // words per padded row
+  // transposed sigma: bit (row x, column y)
+  for (int i = tid; i < g.nws; i += nt) sT[i] = 0;
+  __syncthreads();
+  for_each_anyon(list, count, sig, g, [&](int x, int y) {
+    atomicOr(&sT[(x << g.lws) + (y >> 5)], 1u << (y & 31));
+  });
+  __syncthreads();
+  uint32_t* padN = scratch;            // padded rows of sigma (frame of the x planes)
+  uint32_t* padT = scratch + L * wpp;  // padded rows of its transpose (y planes)
+  for (int i = tid; i < L * wpp; i += nt) {
+    const int r = i / wpp, wp = i - r * wpp;
+    padN[i] = padded_word(sig, g, r, wp);
+    padT[i] = padded_word(sT, g, r, wp);
+  }
+  __syncthreads();
+  if (lane_on) {
+    const uint32_t* pad = (pl < 2) ? padN : padT;
+    const uint32_t off2 = (uint32_t)(g.off + 2) * 0x01010101u;
+#pragma unroll
+    for (int q = 0; q < KW; ++q) {
+      const int c = cword + q;  // plane word: sites 4c .. 4c+3 of the row
+      // window bit i <-> column 4c - 3 + i, i in [0, 10), at padded bit 4c + 5 + i
+      const int bp = 4 * c + 5, wi = bp >> 5, sh = bp & 31;
+      auto ext = [&](int i) -> uint32_t {
+        int R = R0 + i;
+        R = R < 0 ? R + L : (R >= L ? R - L : R);
+        const uint32_t* rw = pad + R * wpp;
+        const uint32_t hi = (wi + 1 < wpp) ? rw[wi + 1] : 0u;
+        return __funnelshift_r(rw[wi], hi, sh) & 0x3FFu;
+      };
+      uint32_t e0 = ext(-3), e1 = ext(-2), e2 = ext(-1), e3 = ext(0), e4 = ext(1), e5 = ext(2);
+      uint8_t* dst = planes + ((size_t)(pl * g.rows_local + lrow0)) * g.ls + 4 * c;
+      for (int i = 0; i < g.H; ++i) {
+        const uint32_t e6 = ext(i + 3);  // window rows i-3 .. i+3 = e0 .. e6
+        const uint32_t v1 = e2 | e3 | e4;
+        const uint32_t v2 = v1 | e1 | e5;
+        const uint32_t v3 = v2 | e0 | e6;
+        uint32_t a1, a2, a3;
+        if (plus) {  // term at site l comes from column l - d
+          a1 = (v1 >> 2) & 0xFu;
+          a2 = (v2 >> 1) & 0xFu;
+          a3 = v3 & 0xFu;
+        } else {     // from column l + d
+          a1 = (v1 >> 4) & 0xFu;
+          a2 = (v2 >> 5) & 0xFu;
+          a3 = (v3 >> 6) & 0xFu;
+        }
+        // bit k -> byte k (0 / 1)
+        const uint32_t b1 = (a1 * 0x00204081u) & 0x01010101u;
+        const uint32_t b12 = ((a1 | a2) * 0x00204081u) & 0x01010101u;
+        const uint32_t b123 = ((a1 | a2 | a3) * 0x00204081u) & 0x01010101u;
+        // off + d - 1 = (off + 2) - [d = 1] - [d <= 2]; 0xFF where no term
+        const uint32_t val = (off2 - b1 - b12) | ~(b123 * 0xFFu);
+        *reinterpret_cast<uint32_t*>(dst + (size_t)i * g.ls) = val;
+        e0 = e1;
+        e1 = e2;
+        e2 = e3;
+        e3 = e4;
+        e4 = e5;
+        e5 = e6;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int CL, int KW>
+__global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArgs a, FastGeom g) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int L = g.L;
+  const int LL = L * L;
+  const int rank = Cluster<CL>::rank();
+  uint8_t* planes = smem;
+  uint32_t* const bits_base = reinterpret_cast<uint32_t*>(smem + g.plane_bytes);
+  uint32_t* sig_cur = bits_base;      // the two sigma buffers swap every step
+  uint32_t* sig_nxt = bits_base + g.nws;
+  uint32_t* flip = bits_base + 2 * g.nws;  // [2][nws]: x-links, y-links (by lower end)
+  uint32_t* Cb = flip + 2 * g.nws;         // [2][nws]: this CTA's share of the correction
+  uint16_t* list = reinterpret_cast<uint16_t*>(Cb + 2 * g.nws);
+  int* misc = reinterpret_cast<int*>(list + ((g.cap + 7) & ~7));
+
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  // ---- dense-sweep role of this thread
+  const int seg = warp * g.spw + lane / g.G;
+  const int lis = lane % g.G;
+  const bool warp_on = warp * g.spw < g.segments;
+  const bool lane_on = (lane < g.spw * g.G) && (seg < g.segments);
+  const int segc = lane_on ? seg : 0;
+  const int pl = segc / g.bands;                 // plane
+  const int lrow0 = (segc % g.bands) * g.H;      // first local row of the band
+  const int R0 = rank * g.rows_local + lrow0;    // first global row
+  const bool plus = (pl % 2) == 0;
+  const int seg_base = lane - lis;
+  const int left_lane = lane_on ? seg_base + (lis + g.G - 1) % g.G : lane;
+  const int right_lane = lane_on ? seg_base + (lis + 1) % g.G : lane;
+  const int cword = lis * KW;                    // first 32-bit word of the column strip
+  const int LS = g.ls;
+  uint8_t* my_rows = planes + ((size_t)(pl * g.rows_local + lrow0)) * LS + cword * 4;
+  const int row_lo = rank * g.rows_local, row_hi = row_lo + g.rows_local;
+
+  const int nclusters = gridDim.x / CL;
+  const int cid = blockIdx.x / CL;
+  const int wpr = 1 << g.lws;  // bitmap words per row
+
+  uint32_t halo[6][KW];
+  auto snapshot = [&]() {
+    if (warp_on) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+#pragma unroll
+        for (int q = 0; q < KW; ++q) {
+          halo[k][q] = *reinterpret_cast<const uint32_t*>(
+              plane_ptr<CL>(planes, g, pl, wrapi(R0 - 3 + k, L), (cword + q) * 4));
+          int Rb = R0 + g.H + k;
+          if (Rb >= L) Rb -= L;
+          halo[3 + k][q] = *reinterpret_cast<const uint32_t*>(
+              plane_ptr<CL>(planes, g, pl, Rb, (cword + q) * 4));
+        }
+      }
+    }
+  };
+
+  for (int64_t shot = cid; shot < a.shots; shot += nclusters) {
+    const uint8_t* N = a.in + shot * (a.from_sigma ? (int64_t)LL : 2 * (int64_t)LL);
+    // ---- init: bitmaps cleared, sigma measured (every CTA of the cluster holds
+    //      the full sigma); the planes are written whole by the first step
+    {
+      sig_cur = bits_base;
+      sig_nxt = bits_base + g.nws;
+      for (int i = tid; i < 4 * g.nws; i += nt) bits_base[2 * g.nws + i] = 0;  // flip, Cb
+      if (tid == 0) misc[0] = 0;
+    }
+    // sigma, 32 sites per thread and word; Def. synch_ccqs: parity of the four
+    // links incident to r (or the given anyon indicator)
+    for (int w = tid; w < g.nws; w += nt) {
+      const int y = w >> g.lws, x0 = (w & (wpr - 1)) << 5;
+      uint32_t bits = 0;
+      if (x0 < L) {
+        const int n = min(32, L - x0);
+        if (a.from_sigma) {
+          const uint8_t* row = N + (size_t)y * L + x0;
+          for (int k = 0; k < n; k += 4)
+            bits |= nonzero_nibble(*reinterpret_cast<const uint32_t*>(row + k)) << k;
+        } else {
+          const uint8_t* ex = N + (size_t)y * L + x0;
+          const uint8_t* ey = N + LL + (size_t)y * L + x0;
+          const uint8_t* eyd = N + LL + (size_t)wrapi(y - 1, L) * L + x0;
+          uint32_t bx = 0, by = 0, byd = 0;
+          for (int k = 0; k < n; k += 4) {
+            bx |= nibble_of(*reinterpret_cast<const uint32_t*>(ex + k)) << k;
+            by |= nibble_of(*reinterpret_cast<const uint32_t*>(ey + k)) << k;
+            byd |= nibble_of(*reinterpret_cast<const uint32_t*>(eyd + k)) << k;
+          }
+          const uint32_t left = N[(size_t)y * L + wrapi(x0 - 1, L)] & 1u;  // e_x(r - x^) at x0
+          bits = bx ^ ((bx << 1) | left) ^ by ^ byd;
+          if (n < 32) bits &= (1u << n) - 1u;
+        }
+      }
+      sig_cur[w] = bits;
+    }
+    __syncthreads();
+    int any = build_list(sig_cur, g, list, &misc[0]);
+    int count = misc[0];
+
+    int t = 0, flag = 0;
+    while (any) {
+      if (t >= a.max_steps) {
+        flag = 2;
+        break;
+      }
+      if (t == 0) {
+        // ================= 1. first step: the planes start empty, so the
+        // message update reduces to the anyon terms; compute them densely
+        // for every site (32 sites per bitmap operation) instead of
+        // scattering the cone sections of the many initial anyons.
+        seed_planes<KW>(sig_cur, list, count, sig_nxt, flip, g, planes, pl, lrow0, R0, plus,
+                        cword, lane_on);
+        for (int i = tid; i < 2 * g.nws; i += nt) Cb[i] = 0;  // scratch reused above
+      } else if (warp_on) {
+        // ================= 1a. dense message update of this thread's band
+        Chain cH[KW], cL[KW];
+#pragma unroll
+        for (int q = 0; q < KW; ++q) {
+          uint32_t ah[6], al[6];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            ah[k] = halo[k][q];
+            ah[3 + k] = *reinterpret_cast<const uint32_t*>(my_rows + (size_t)k * LS + q * 4);
+          }
+#pragma unroll
+          for (int k = 0; k < 6; ++k) al[k] = ah[k] << 8;
+          cH[q].init(ah);
+          cL[q].init(al);
+        }
+        auto row = [&](int i, const uint32_t (&in)[KW]) {
+          uint32_t m[KW];
+#pragma unroll
+          for (int q = 0; q < KW; ++q) {
+            const uint32_t tH = cH[q].step(in[q]);
+            const uint32_t tL = cL[q].step(in[q] << 8);
+            m[q] = finish_word(tL, tH);
+          }
+          uint32_t out[KW];
+          if (KW == 1) {
+            if (plus) {
+              const uint32_t nb = __shfl_sync(0xffffffffu, m[0], left_lane);
+              out[0] = __funnelshift_r(nb, m[0], 8);
+            } else {
+              const uint32_t nb = __shfl_sync(0xffffffffu, m[0], right_lane);
+              out[0] = __funnelshift_r(m[0], nb, 24);
+            }
+          } else {
+            const uint32_t sendv = plus ? m[KW - 1] : m[0];
+            const uint32_t nb = __shfl_sync(0xffffffffu, sendv, plus ? left_lane : right_lane);
+            if (plus) {
+              out[0] = __funnelshift_r(nb, m[0], 8);
+#pragma unroll
+              for (int q = 1; q < KW; ++q) out[q] = __funnelshift_r(m[q - 1], m[q], 8);
+            } else {
+#pragma unroll
+              for (int q = 0; q + 1 < KW; ++q) out[q] = __funnelshift_r(m[q], m[q + 1], 24);
+              out[KW - 1] = __funnelshift_r(m[KW - 1], nb, 24);
+            }
+          }
+          if (lane_on) {
+#pragma unroll
+            for (int q = 0; q < KW; ++q)
+              *reinterpret_cast<uint32_t*>(my_rows + (size_t)i * LS + q * 4) = out[q];
+          }
+        };
+#pragma unroll 4
+        for (int i = 0; i < g.H - 3; ++i) {
+          uint32_t in[KW];
+#pragma unroll
+          for (int q = 0; q < KW; ++q)
+            in[q] = *reinterpret_cast<const uint32_t*>(my_rows + (size_t)(i + 3) * LS + q * 4);
+          row(i, in);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          uint32_t in[KW];
+#pragma unroll
+          for (int q = 0; q < KW; ++q) in[q] = halo[3 + k][q];
+          row(g.H - 3 + k, in);
+        }
+      }
+      // clear the move bitmaps and copy sigma (read only after the next sync)
+      for (int i = tid; i < g.nws; i += nt) {
+        sig_nxt[i] = sig_cur[i];
+        flip[i] = 0;
+        flip[g.nws + i] = 0;
+      }
+      __syncthreads();
+      // ================= 1b. anyon terms: light-cone sections, d = 3, 2, 1;
+      //                   each CTA writes the sections that fall in its rows
+      // (d is a compile-time constant in each pass, so the 4 * (2d + 1) stores of
+      // one anyon are independent instructions)
+      auto pass = [&](auto dconst) {
+        constexpr int d = decltype(dconst)::value;
+        const uint8_t val = (uint8_t)min(255, g.off + d - 1);
+        for_each_anyon(list, count, sig_cur, g, [&](int x0, int y0) {
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const int row0 = (p < 2) ? y0 : x0;
+            const int col0 = (p < 2) ? x0 : y0;
+            if (CL > 1) {  // skip anyons whose sections miss this CTA's rows
+              int dr = row0 - row_lo;
+              if (dr < 0) dr += L;
+              if (dr >= g.rows_local + 3 && dr < L - 3) continue;
+            }
+            const int col = wrapi((p % 2 == 0) ? col0 + d : col0 - d, L);
+            uint8_t* base = planes + (size_t)p * g.rows_local * LS + col;
+#pragma unroll
+            for (int j = -d; j <= d; ++j) {
+              const int R = wrapi(row0 + j, L);
+              if (CL > 1 && (R < row_lo || R >= row_hi)) continue;
+              base[(size_t)(R - row_lo) * LS] = val;
+            }
+          }
+        });
+        __syncthreads();
+      };
+      if (t > 0) {
+        pass(std::integral_constant<int, 3>{});
+        pass(std::integral_constant<int, 2>{});
+        pass(std::integral_constant<int, 1>{});
+      }
+      // every plane of the cluster final; sigma copies and flip maps ready
+      Cluster<CL>::sync();
+      snapshot();  // halo rows for the next step
+      // ================= 2. forces and feedback for the anyons of this CTA's rows
+      uint64_t kstep = 0;
+      if (a.move_thr) kstep = move_step_key(a.move_key, a.shot_offset + shot, t);
+      for_each_anyon(list, count, sig_cur, g, [&](int x, int y) {
+        if (CL > 1 && (y < row_lo || y >= row_hi)) return;
+        int dir = choose_dir(*plane_ptr<CL>(planes, g, 0, y, x), *plane_ptr<CL>(planes, g, 1, y, x),
+                             *plane_ptr<CL>(planes, g, 2, x, y), *plane_ptr<CL>(planes, g, 3, x, y));
+        if (a.move_thr) {
+          const uint64_t u = splitmix64(kstep ^ (uint64_t)(y * L + x));
+          if (u < a.move_thr) dir = 1 + (int)(splitmix64(u) >> 62);
+        }
+        if (!dir) return;
+        // link <lo, lo + a^> and its far end hi
+        const int ax = (dir <= 2) ? 0 : 1;
+        const int lx = (dir == 2) ? wrapi(x - 1, L) : x;
+        const int ly = (dir == 4) ? wrapi(y - 1, L) : y;
+        const int hx = ax == 0 ? wrapi(lx + 1, L) : lx;
+        const int hy = ax == 1 ? wrapi(ly + 1, L) : ly;
+        const int wlo = (ly << g.lws) + (lx >> 5), whi = (hy << g.lws) + (hx >> 5);
+        const uint32_t mlo = 1u << (lx & 31), mhi = 1u << (hx & 31);
+        const int owner = (CL == 1) ? 0 : (ly >= g.rows_local ? 1 : 0);
+        uint32_t* fw = Cluster<CL>::at(flip, owner) + ax * g.nws + wlo;
+        const uint32_t old = atomicOr(fw, mlo);
+        if (old & mlo) return;  // the other end already flipped this link (OR)
+        atomicXor(&Cb[ax * g.nws + wlo], mlo);
+#pragma unroll
+        for (int r = 0; r < CL; ++r) {
+          uint32_t* sn = Cluster<CL>::at(sig_nxt, r);
+          atomicXor(&sn[wlo], mlo);
+          atomicXor(&sn[whi], mhi);
+        }
+      });
+      Cluster<CL>::sync();
+      // ================= 3. swap sigma, new anyon list, early exit
+      {
+        uint32_t* tmp = sig_cur;
+        sig_cur = sig_nxt;
+        sig_nxt = tmp;
+      }
+      if (tid == 0) misc[0] = 0;
+      __syncthreads();
+      any = build_list(sig_cur, g, list, &misc[0]);
+      count = misc[0];
+      ++t;
+    }
+    // ================= outputs: correction bytes, homology, steps, flag
+    // the correction is the XOR of the CTAs' shares
+    uint8_t* outC = a.out_C + shot * 2 * (int64_t)LL;
+    const int gpr = L / 4;  // 4-site groups per row
+    for (int ax = 0; ax < 2; ++ax) {
+      for (int i = tid; i < g.rows_local * gpr; i += nt) {
+        const int y = row_lo + i / gpr, x = (i - (i / gpr) * gpr) * 4;
+        const int w = (y << g.lws) + (x >> 5);
+        uint32_t bits = 0;
+#pragma unroll
+        for (int r = 0; r < CL; ++r) bits ^= Cluster<CL>::at(Cb, r)[ax * g.nws + w];
+        const uint32_t nib = (bits >> (x & 31)) & 0xFu;
+        *reinterpret_cast<uint32_t*>(outC + (size_t)ax * LL + (size_t)y * L + x) =
+            (nib * 0x00204081u) & 0x01010101u;
+      }
+    }
+    if (tid == 0) misc[1] = misc[2] = 0;
+    __syncthreads();
+    if (rank == 0) {
+      int wx = 0, wy = 0;
+      for (int i = tid; i < L; i += nt) {
+        // e_x((0, i)) and e_y((i, 0))
+        uint32_t bx = 0, by = 0;
+#pragma unroll
+        for (int r = 0; r < CL; ++r) {
+          const uint32_t* c = Cluster<CL>::at(Cb, r);
+          bx ^= c[i << g.lws];
+          by ^= c[g.nws + (i >> 5)] >> (i & 31);
+        }
+        wx ^= (int)(bx & 1);
+        wy ^= (int)(by & 1);
+        if (!a.from_sigma) {
+          wx ^= N[(size_t)i * L];
+          wy ^= N[LL + i];
+        }
+      }
+      if (wx) atomicXor(&misc[1], 1);
+      if (wy) atomicXor(&misc[2], 1);
+      __syncthreads();
+      if (tid == 0) {
+        a.out_steps[shot] = t;
+        if (a.from_sigma) {
+          a.out_cut[2 * shot] = (uint8_t)misc[1];
+          a.out_cut[2 * shot + 1] = (uint8_t)misc[2];
+          if (a.out_exhausted) a.out_exhausted[shot] = (uint8_t)(flag == 2);
+        } else {
+          a.out_flag[shot] = (uint8_t)(flag == 2 ? 2 : ((misc[1] | misc[2]) ? 1 : 0));
+        }
+      }
+    }
+    // partners may still read this CTA's correction share
+    Cluster<CL>::sync();
+  }
+}
+
+// ---------------------------------------------------------------- host ----
+
+bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, size_t& smem) {
+  if (L % 4 != 0 || L < 8 || L > 256) return false;
+  if (m_max < 3) return false;  // the first-step fill assumes the d <= 3 terms fit below 0xFF
+  if (L > 128 && L % 8 != 0) return false;
+  CL = (L > 128) ? 2 : 1;
+  KW = (L / 4 > 32) ? 2 : 1;
+  g.L = L;
+  g.rows_local = L / CL;
+  g.G = L / 4 / KW;
+  if (g.G > 32) return false;
+  g.spw = 32 / g.G;
+  // band height: 32, 16, 8 or 4 rows, dividing the CTA's rows, within the
+  // thread limit; at L <= 64 few large bands (many shots per SM), above it
+  // at least 16 warps per CTA
+  const int max_warps = (CL == 1) ? 32 : 16;
+  int best_H = 0;
+  for (int H : {4, 8, 16, 32}) {
+    if (g.rows_local % H) continue;
+    const int segments = 4 * (g.rows_local / H);
+    const int warps = (segments + g.spw - 1) / g.spw;
+    if (warps > max_warps) continue;
+    if (!best_H) best_H = H;
+    if (warps >= 16 || (L <= 64 && H >= 8)) best_H = H;
+  }
+  if (!best_H) return false;
+  g.H = best_H;
+  g.bands = g.rows_local / g.H;
+  g.segments = 4 * g.bands;
+  const int warps = (g.segments + g.spw - 1) / g.spw;
+  threads = warps * 32;
+  int wpr = (L + 31) / 32, lws = 0;
+  while ((1 << lws) < wpr) ++lws;
+  g.lws = lws;
+  g.nws = L << lws;
+  g.off = 255 - m_max;
+  g.cap = L * L < kListCap ? L * L : kListCap;
+  g.ls = L + 4;
+  g.plane_bytes = (size_t)4 * g.rows_local * g.ls;
+  smem = g.plane_bytes + (size_t)6 * g.nws * 4 + (size_t)((g.cap + 7) & ~7) * 2 + 64;
+  return true;
+}
+
+template <int CL, int KW>
+int launch_t(const DecodeArgs& a, const FastGeom& g, int threads, size_t smem,
+             cudaStream_t stream) {
+  auto kern = fast_kernel<CL, KW>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "fast sweep smem attribute");
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  if (CL == 1) {
+    int resident = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, threads, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (resident < 1) {
+      set_error("fast sweep does not fit on an SM (L=%d)", a.L);
+      return QCA_ERR_UNSUPPORTED;
+    }
+    int64_t grid = (int64_t)resident * sms;
+    if (grid > a.shots) grid = a.shots;
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.numAttrs = 0;
+  } else {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)(CL * sms));
+    int clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+    if (e != cudaSuccess) return cuda_fail(e, "cluster occupancy query");
+    if (clusters < 1) {
+      set_error("fast cluster sweep does not fit (L=%d)", a.L);
+      return QCA_ERR_UNSUPPORTED;
+    }
+    int64_t grid = (int64_t)clusters;
+    if (grid > a.shots) grid = a.shots;
+    cfg.gridDim = dim3((unsigned)(grid * CL));
+  }
+  e = cudaLaunchKernelEx(&cfg, kern, a, g);
+  return cuda_fail(e, "fast sweep launch");
+}
+
+}  // namespace
+
+int fast_path_for(int L, int v, int m_max) {
+  if (v != 3) return 0;
+  int CL, KW, threads;
+  FastGeom g;
+  size_t smem;
+  if (!make_geom(L, m_max, CL, KW, g, threads, smem)) return 0;
+  return CL;
 }
 
 int launch_fast(const DecodeArgs& a, cudaStream_t stream) {
-  (void)a;
-  (void)stream;
-  set_error("no on-chip kernel for this size");
+  int CL, KW, threads;
+  FastGeom g;
+  size_t smem;
+  if (a.v != 3 || !make_geom(a.L, a.m_max, CL, KW, g, threads, smem)) {
+    set_error("no on-chip kernel for L=%d v=%d", a.L, a.v);
+    return QCA_ERR_UNSUPPORTED;
+  }
+  if (CL == 1 && KW == 1) return launch_t<1, 1>(a, g, threads, smem, stream);
+  if (CL == 2 && KW == 2) return launch_t<2, 2>(a, g, threads, smem, stream);
+  set_error("no on-chip kernel variant for L=%d", a.L);
   return QCA_ERR_UNSUPPORTED;
 }
 
