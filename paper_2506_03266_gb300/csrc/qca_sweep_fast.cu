@@ -61,6 +61,7 @@ struct FastGeom {
   int nws;              // words of one site bitmap (L << lws)
   int off;              // 255 - m_max
   int cap;              // anyon-list capacity
+  int sparse_max;       // most anyons for which the per-anyon scatter beats the dense pass
   int ls;               // plane row stride in bytes: L + 4, so that a column of a
                         // plane does not fall into one shared-memory bank
   size_t plane_bytes;   // 4 * rows_local * ls
@@ -206,6 +207,65 @@ __device__ __forceinline__ int build_list(const uint32_t* sig, const FastGeom& g
   return __syncthreads_or(n);
 }
 
+// Feedback applied densely, 32 sites per word: sigma <- sigma * sigma_F with
+// F the flipped links (bit of e_x(r) / e_y(r) at site r); a site's parity
+// toggles once per flipped incident link e_x(r), e_x(r - x^), e_y(r),
+// e_y(r - y^).  The CTA's rows of the correction take F as well.  Every CTA
+// holds the whole flipped-link map.  Then the anyon list is rebuilt from the
+// new sigma; returns "any anyon" (block-uniform).
+__device__ __forceinline__ int apply_flips(uint32_t* sig, const uint32_t* flip, uint32_t* Cb,
+                                           const FastGeom& g, uint16_t* list, int* count,
+                                           int row_lo, int row_hi) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, L = g.L;
+  const int wsm = (1 << g.lws) - 1;
+  const int per = (g.nws + nt - 1) / nt;
+  const int w0 = tid * per, w1 = min(g.nws, w0 + per);
+  const int last_w = (L - 1) >> 5, last_b = (L - 1) & 31;
+  int n = 0;
+  for (int w = w0; w < w1; ++w) {
+    const int y = w >> g.lws, j = w & wsm, x0 = j << 5;
+    if (x0 >= L) continue;  // padding word
+    const int ym = (y == 0) ? L - 1 : y - 1;
+    const uint32_t fx = flip[w], fy = flip[g.nws + w];
+    const uint32_t fyu = flip[g.nws + (ym << g.lws) + j];
+    // e_x(r - x^) for bit x: bit x - 1 of this row (wrapping to x = L - 1)
+    const uint32_t carry = (j > 0) ? (flip[w - 1] >> 31)
+                                   : ((flip[(y << g.lws) + last_w] >> last_b) & 1u);
+    const uint32_t fxl = (fx << 1) | carry;
+    const uint32_t valid = (L - x0 >= 32) ? 0xFFFFFFFFu : ((1u << (L - x0)) - 1u);
+    const uint32_t s = sig[w] ^ ((fx ^ fxl ^ fy ^ fyu) & valid);
+    sig[w] = s;
+    n += __popc(s);
+    if (y >= row_lo && y < row_hi) {
+      Cb[w] ^= fx;
+      Cb[g.nws + w] ^= fy;
+    }
+  }
+  // new anyon list (same layout as build_list)
+  int incl = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  int wbase = 0;
+  if (lane == 31 && total) wbase = atomicAdd(count, total);
+  wbase = __shfl_sync(0xffffffffu, wbase, 31);
+  int pos = wbase + incl - n;
+  for (int w = w0; w < w1; ++w) {
+    uint32_t b = sig[w];
+    const int y = w >> g.lws, xb = (w & wsm) << 5;
+    while (b) {
+      const int k = __ffs(b) - 1;
+      b &= b - 1;
+      if (pos < g.cap) list[pos] = (uint16_t)((y << 8) | (xb + k));
+      ++pos;
+    }
+  }
+  return __syncthreads_or(n);
+}
+
 // Calls f(x, y) for every anyon of the current sigma, from the list when it
 // held them all, else straight from the bitmap.
 template <class F>
@@ -236,7 +296,7 @@ __device__ __forceinline__ void for_each_anyon(const uint16_t* list, int count, 
   }
 }
 
-// n (<= 32) bits of bitmap row r starting at column c (c + n <= row width).
+// n (<= 32) bits of bitmap row r starting at column c (c + n <= L).
 __device__ __forceinline__ uint32_t row_bits(const uint32_t* bm, const FastGeom& g, int r, int c,
                                              int n) {
   const uint32_t* row = bm + (r << g.lws);
@@ -247,75 +307,50 @@ __device__ __forceinline__ uint32_t row_bits(const uint32_t* bm, const FastGeom&
   return n >= 32 ? v : (v & ((1u << n) - 1u));
 }
 
-// Word wp of the padded copy of bitmap row r: bit k <-> column (k - 8) mod L,
-// for k in [0, L + 16), so that any window of columns [c - 8, c + 8) with
-// 0 <= c < L is contiguous.
-__device__ __forceinline__ uint32_t padded_word(const uint32_t* bm, const FastGeom& g, int r,
-                                                int wp) {
-  const int L = g.L, k0 = wp * 32;
-  uint32_t out = 0;
-  // (first padded bit, end, first column) of the three pieces
-  const int seg[3][3] = {{0, 8, L - 8}, {8, L + 8, 0}, {L + 8, L + 16, 0}};
-#pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    const int lo = max(seg[s][0], k0), hi = min(seg[s][1], k0 + 32);
-    if (lo >= hi) continue;
-    int c = seg[s][2] + (lo - seg[s][0]);
-    int n = hi - lo, pos = lo - k0;
-    while (n > 0) {  // at most two chunks (a piece never crosses two word boundaries of the row)
-      const int take = min(n, 32 - (c & 31));
-      out |= row_bits(bm, g, r, c, take) << pos;
-      c += take;
-      pos += take;
-      n -= take;
-    }
-  }
-  return out;
+// Bits of columns start, start+1, ..., start+9 (mod L) of bitmap row r.
+__device__ __forceinline__ uint32_t row_window10(const uint32_t* bm, const FastGeom& g, int r,
+                                                 int start) {
+  const int L = g.L;
+  const int s = start < 0 ? start + L : start;
+  const int n1 = min(10, L - s);
+  uint32_t v = row_bits(bm, g, r, s, n1);
+  if (n1 < 10) v |= row_bits(bm, g, r, 0, 10 - n1) << n1;
+  return v;
 }
 
-// First decoder step with empty planes: the fused message update reduces to
-// the anyon terms, w(r) = off + d - 1 for the smallest d in {1, 2, 3} with an
-// anyon on the cone section at distance d, else 0xFF.  Each thread fills its
-// band of plane words.  The section at distance d of a site at longitudinal
-// position l is the transverse run of 2d + 1 sites at l -+ d, so with
-// V_d = OR of the sigma rows t-d .. t+d (frame orientation) the term is bit
-// l -+ d of V_d.  Uses sT (nws words) and scratch (4 * nws words) as
-// temporary storage; ends with a block barrier.
-template <int KW>
-__device__ void seed_planes(const uint32_t* sig, const uint16_t* list, int count, uint32_t* sT,
-                            uint32_t* scratch, const FastGeom& g, uint8_t* planes, int pl,
-                            int lrow0, int R0, bool plus, int cword, bool lane_on) {
+// Anyon terms of the fused message update computed densely for every site of
+// this thread's band: w(r) = off + d - 1 for the smallest d in {1, 2, 3} with an
+// anyon on the cone section at distance d.  The section at distance d of a site
+// at longitudinal position l is the transverse run of 2d + 1 sites at l -+ d, so
+// with V_d = OR of the sigma rows t-d .. t+d (in the plane's frame) the term is
+// bit l -+ d of V_d; 32 sites per bitmap operation.
+// MERGE = false: the planes were empty (first step), the result is stored as is.
+// MERGE = true: the planes hold the propagated values of this step, which are
+// all above any anyon term, so the term replaces the value where it exists.
+// sT (nws words) receives the transposed sigma.  Ends with a block barrier.
+template <int KW, bool MERGE>
+__device__ void dense_terms(const uint32_t* sig, const uint16_t* list, int count, uint32_t* sT,
+                            const FastGeom& g, uint8_t* planes, int pl, int lrow0, int R0,
+                            bool plus, int cword, bool lane_on) {
   const int tid = threadIdx.x, nt = blockDim.x, L = g.L;
-  const int wpp = (L + 16 + 31) >> 5;  // words per padded row
-  // transposed sigma: bit (row x, column y)
+  // transposed sigma: bit (row x, column y), the frame of the y planes
   for (int i = tid; i < g.nws; i += nt) sT[i] = 0;
   __syncthreads();
   for_each_anyon(list, count, sig, g, [&](int x, int y) {
     atomicOr(&sT[(x << g.lws) + (y >> 5)], 1u << (y & 31));
   });
   __syncthreads();
-  uint32_t* padN = scratch;            // padded rows of sigma (frame of the x planes)
-  uint32_t* padT = scratch + L * wpp;  // padded rows of its transpose (y planes)
-  for (int i = tid; i < L * wpp; i += nt) {
-    const int r = i / wpp, wp = i - r * wpp;
-    padN[i] = padded_word(sig, g, r, wp);
-    padT[i] = padded_word(sT, g, r, wp);
-  }
-  __syncthreads();
   if (lane_on) {
-    const uint32_t* pad = (pl < 2) ? padN : padT;
+    const uint32_t* bm = (pl < 2) ? sig : sT;
     const uint32_t off2 = (uint32_t)(g.off + 2) * 0x01010101u;
 #pragma unroll
     for (int q = 0; q < KW; ++q) {
       const int c = cword + q;  // plane word: sites 4c .. 4c+3 of the row
-      // window bit i <-> column 4c - 3 + i, i in [0, 10), at padded bit 4c + 5 + i
-      const int bp = 4 * c + 5, wi = bp >> 5, sh = bp & 31;
+      // window bit i <-> column 4c - 3 + i, i in [0, 10)
       auto ext = [&](int i) -> uint32_t {
         int R = R0 + i;
         R = R < 0 ? R + L : (R >= L ? R - L : R);
-        const uint32_t* rw = pad + R * wpp;
-        const uint32_t hi = (wi + 1 < wpp) ? rw[wi + 1] : 0u;
-        return __funnelshift_r(rw[wi], hi, sh) & 0x3FFu;
+        return row_window10(bm, g, R, 4 * c - 3);
       };
       uint32_t e0 = ext(-3), e1 = ext(-2), e2 = ext(-1), e3 = ext(0), e4 = ext(1), e5 = ext(2);
       uint8_t* dst = planes + ((size_t)(pl * g.rows_local + lrow0)) * g.ls + 4 * c;
@@ -337,10 +372,15 @@ __device__ void seed_planes(const uint32_t* sig, const uint16_t* list, int count
         // bit k -> byte k (0 / 1)
         const uint32_t b1 = (a1 * 0x00204081u) & 0x01010101u;
         const uint32_t b12 = ((a1 | a2) * 0x00204081u) & 0x01010101u;
-        const uint32_t b123 = ((a1 | a2 | a3) * 0x00204081u) & 0x01010101u;
-        // off + d - 1 = (off + 2) - [d = 1] - [d <= 2]; 0xFF where no term
-        const uint32_t val = (off2 - b1 - b12) | ~(b123 * 0xFFu);
-        *reinterpret_cast<uint32_t*>(dst + (size_t)i * g.ls) = val;
+        const uint32_t m = (((a1 | a2 | a3) * 0x00204081u) & 0x01010101u) * 0xFFu;
+        // off + d - 1 = (off + 2) - [d = 1] - [d <= 2]
+        uint32_t val = off2 - b1 - b12;
+        uint32_t* w = reinterpret_cast<uint32_t*>(dst + (size_t)i * g.ls);
+        if (MERGE)
+          val = (val & m) | (*w & ~m);
+        else
+          val |= ~m;
+        *w = val;
         e0 = e1;
         e1 = e2;
         e2 = e3;
@@ -361,10 +401,9 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
   const int rank = Cluster<CL>::rank();
   uint8_t* planes = smem;
   uint32_t* const bits_base = reinterpret_cast<uint32_t*>(smem + g.plane_bytes);
-  uint32_t* sig_cur = bits_base;      // the two sigma buffers swap every step
-  uint32_t* sig_nxt = bits_base + g.nws;
-  uint32_t* flip = bits_base + 2 * g.nws;  // [2][nws]: x-links, y-links (by lower end)
-  uint32_t* Cb = flip + 2 * g.nws;         // [2][nws]: this CTA's share of the correction
+  uint32_t* const sig_cur = bits_base;            // sigma (the full lattice in every CTA)
+  uint32_t* const flipb = bits_base + g.nws;      // [step parity][x-links, y-links][nws]
+  uint32_t* const Cb = flipb + 4 * g.nws;         // [2][nws]: correction, this CTA's rows
   uint16_t* list = reinterpret_cast<uint16_t*>(Cb + 2 * g.nws);
   int* misc = reinterpret_cast<int*>(list + ((g.cap + 7) & ~7));
 
@@ -415,9 +454,7 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
     // ---- init: bitmaps cleared, sigma measured (every CTA of the cluster holds
     //      the full sigma); the planes are written whole by the first step
     {
-      sig_cur = bits_base;
-      sig_nxt = bits_base + g.nws;
-      for (int i = tid; i < 4 * g.nws; i += nt) bits_base[2 * g.nws + i] = 0;  // flip, Cb
+      for (int i = tid; i < 6 * g.nws; i += nt) flipb[i] = 0;  // flip maps and Cb
       if (tid == 0) misc[0] = 0;
     }
     // sigma, 32 sites per thread and word; Def. synch_ccqs: parity of the four
@@ -458,14 +495,16 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
         flag = 2;
         break;
       }
+      // flipped-link maps alternate by step parity: a partner CTA may still read
+      // the previous step's map while this step writes the other one
+      uint32_t* const flip = flipb + (t & 1) * 2 * g.nws;
       if (t == 0) {
         // ================= 1. first step: the planes start empty, so the
         // message update reduces to the anyon terms; compute them densely
         // for every site (32 sites per bitmap operation) instead of
         // scattering the cone sections of the many initial anyons.
-        seed_planes<KW>(sig_cur, list, count, sig_nxt, flip, g, planes, pl, lrow0, R0, plus,
-                        cword, lane_on);
-        for (int i = tid; i < 2 * g.nws; i += nt) Cb[i] = 0;  // scratch reused above
+        dense_terms<KW, false>(sig_cur, list, count, flip, g, planes, pl, lrow0, R0, plus, cword,
+                               lane_on);
       } else if (warp_on) {
         // ================= 1a. dense message update of this thread's band
         Chain cH[KW], cL[KW];
@@ -534,106 +573,128 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
           row(g.H - 3 + k, in);
         }
       }
-      // clear the move bitmaps and copy sigma (read only after the next sync)
-      for (int i = tid; i < g.nws; i += nt) {
-        sig_nxt[i] = sig_cur[i];
-        flip[i] = 0;
-        flip[g.nws + i] = 0;
-      }
-      __syncthreads();
-      // ================= 1b. anyon terms: light-cone sections, d = 3, 2, 1;
-      //                   each CTA writes the sections that fall in its rows
-      // (d is a compile-time constant in each pass, so the 4 * (2d + 1) stores of
-      // one anyon are independent instructions)
-      auto pass = [&](auto dconst) {
-        constexpr int d = decltype(dconst)::value;
-        const uint8_t val = (uint8_t)min(255, g.off + d - 1);
-        for_each_anyon(list, count, sig_cur, g, [&](int x0, int y0) {
-#pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            const int row0 = (p < 2) ? y0 : x0;
-            const int col0 = (p < 2) ? x0 : y0;
-            if (CL > 1) {  // skip anyons whose sections miss this CTA's rows
-              int dr = row0 - row_lo;
-              if (dr < 0) dr += L;
-              if (dr >= g.rows_local + 3 && dr < L - 3) continue;
-            }
-            const int col = wrapi((p % 2 == 0) ? col0 + d : col0 - d, L);
-            uint8_t* base = planes + (size_t)p * g.rows_local * LS + col;
-#pragma unroll
-            for (int j = -d; j <= d; ++j) {
-              const int R = wrapi(row0 + j, L);
-              if (CL > 1 && (R < row_lo || R >= row_hi)) continue;
-              base[(size_t)(R - row_lo) * LS] = val;
-            }
-          }
-        });
-        __syncthreads();
-      };
+      // ================= 1b. anyon terms of steps after the first
       if (t > 0) {
-        pass(std::integral_constant<int, 3>{});
-        pass(std::integral_constant<int, 2>{});
-        pass(std::integral_constant<int, 1>{});
+        if (count <= g.cap && count <= g.sparse_max) {
+          // light-cone sections written per anyon, d = 3, 2, 1 (largest value
+          // first); a warp takes one anyon, lane = (plane, transverse offset), so
+          // the lanes of a store hit consecutive rows (distinct banks).  Each CTA
+          // writes the sections that fall in its rows.
+          __syncthreads();
+          auto pass = [&](auto dconst) {
+            constexpr int d = decltype(dconst)::value;
+            const uint8_t val = (uint8_t)(g.off + d - 1);
+            const int p = lane >> 3, jj = lane & 7;
+            const bool act = jj < 2 * d + 1;
+            const int nw = nt >> 5;
+            // four anyons per warp and iteration (independent loads, then stores)
+            for (int i0 = warp; i0 < count; i0 += 4 * nw) {
+              int e[4];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const int i = i0 + k * nw;
+                e[k] = (i < count) ? (int)list[i] : -1;
+              }
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const int x0 = e[k] & 0xFF, y0 = e[k] >> 8;
+                if (act && e[k] >= 0) {
+                  const int row0 = (p < 2) ? y0 : x0;
+                  const int col0 = (p < 2) ? x0 : y0;
+                  const int col = wrapi((p % 2 == 0) ? col0 + d : col0 - d, L);
+                  const int R = wrapi(row0 + jj - d, L);
+                  if (CL == 1 || (R >= row_lo && R < row_hi))
+                    planes[(size_t)(p * g.rows_local + R - row_lo) * LS + col] = val;
+                }
+              }
+            }
+            __syncthreads();
+          };
+          pass(std::integral_constant<int, 3>{});
+          pass(std::integral_constant<int, 2>{});
+          pass(std::integral_constant<int, 1>{});
+        } else {
+          __syncthreads();  // the dense update above is complete
+          dense_terms<KW, true>(sig_cur, list, count, flip, g, planes, pl, lrow0, R0, plus, cword,
+                                lane_on);
+        }
       }
-      // every plane of the cluster final; sigma copies and flip maps ready
+      // clear this step's flipped-link map (also the scratch of the dense terms)
+      __syncthreads();
+      for (int i = tid; i < 2 * g.nws; i += nt) flip[i] = 0;
+      // every plane of the cluster final; flip maps ready
       Cluster<CL>::sync();
       snapshot();  // halo rows for the next step
       // ================= 2. forces and feedback for the anyons of this CTA's rows
       uint64_t kstep = 0;
       if (a.move_thr) kstep = move_step_key(a.move_key, a.shot_offset + shot, t);
-      for_each_anyon(list, count, sig_cur, g, [&](int x, int y) {
-        if (CL > 1 && (y < row_lo || y >= row_hi)) return;
+      auto decide = [&](int x, int y) -> int {
         int dir = choose_dir(*plane_ptr<CL>(planes, g, 0, y, x), *plane_ptr<CL>(planes, g, 1, y, x),
                              *plane_ptr<CL>(planes, g, 2, x, y), *plane_ptr<CL>(planes, g, 3, x, y));
         if (a.move_thr) {
           const uint64_t u = splitmix64(kstep ^ (uint64_t)(y * L + x));
           if (u < a.move_thr) dir = 1 + (int)(splitmix64(u) >> 62);
         }
-        if (!dir) return;
-        // link <lo, lo + a^> and its far end hi
+        return dir;
+      };
+      auto apply = [&](int x, int y, int dir) {
+        // mark link <lo, lo + a^>; a link crossed from both ends is marked
+        // twice and flips once (the OR of Eq. ddfeedback)
         const int ax = (dir <= 2) ? 0 : 1;
         const int lx = (dir == 2) ? wrapi(x - 1, L) : x;
         const int ly = (dir == 4) ? wrapi(y - 1, L) : y;
-        const int hx = ax == 0 ? wrapi(lx + 1, L) : lx;
-        const int hy = ax == 1 ? wrapi(ly + 1, L) : ly;
-        const int wlo = (ly << g.lws) + (lx >> 5), whi = (hy << g.lws) + (hx >> 5);
-        const uint32_t mlo = 1u << (lx & 31), mhi = 1u << (hx & 31);
-        const int owner = (CL == 1) ? 0 : (ly >= g.rows_local ? 1 : 0);
-        uint32_t* fw = Cluster<CL>::at(flip, owner) + ax * g.nws + wlo;
-        const uint32_t old = atomicOr(fw, mlo);
-        if (old & mlo) return;  // the other end already flipped this link (OR)
-        atomicXor(&Cb[ax * g.nws + wlo], mlo);
+        const int wlo = (ly << g.lws) + (lx >> 5);
+        // every CTA keeps the whole map (fire-and-forget ORs, the remote one
+        // through distributed shared memory)
 #pragma unroll
-        for (int r = 0; r < CL; ++r) {
-          uint32_t* sn = Cluster<CL>::at(sig_nxt, r);
-          atomicXor(&sn[wlo], mlo);
-          atomicXor(&sn[whi], mhi);
+        for (int r = 0; r < CL; ++r)
+          atomicOr(Cluster<CL>::at(flip, r) + ax * g.nws + wlo, 1u << (lx & 31));
+      };
+      if (count <= g.cap) {
+        // four anyons per thread and iteration: all field loads are issued before
+        // the first atomic (latency hiding with few warps per SM)
+        const int stride = (count + 31) >> 5, span = 32 * stride;
+        for (int i0 = tid; i0 < span; i0 += 4 * nt) {
+          int ex[4], ey[4], dir[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k * nt;
+            const int idx = (i & 31) * stride + (i >> 5);
+            const bool ok = i < span && idx < count;
+            const int e = ok ? list[idx] : 0;
+            ex[k] = e & 0xFF;
+            ey[k] = e >> 8;
+            const bool mine = ok && (CL == 1 || (ey[k] >= row_lo && ey[k] < row_hi));
+            dir[k] = mine ? decide(ex[k], ey[k]) : 0;
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (dir[k]) apply(ex[k], ey[k], dir[k]);
         }
-      });
-      Cluster<CL>::sync();
-      // ================= 3. swap sigma, new anyon list, early exit
-      {
-        uint32_t* tmp = sig_cur;
-        sig_cur = sig_nxt;
-        sig_nxt = tmp;
+      } else {
+        for_each_anyon(list, count, sig_cur, g, [&](int x, int y) {
+          if (CL > 1 && (y < row_lo || y >= row_hi)) return;
+          const int dir = decide(x, y);
+          if (dir) apply(x, y, dir);
+        });
       }
-      if (tid == 0) misc[0] = 0;
-      __syncthreads();
-      any = build_list(sig_cur, g, list, &misc[0]);
+      if (tid == 0) misc[0] = 0;  // list counter (count already read by every thread)
+      Cluster<CL>::sync();
+      // ================= 3. sigma and correction from the flipped links, new
+      //                   anyon list, early exit
+      any = apply_flips(sig_cur, flip, Cb, g, list, &misc[0], row_lo, row_hi);
       count = misc[0];
       ++t;
     }
     // ================= outputs: correction bytes, homology, steps, flag
-    // the correction is the XOR of the CTAs' shares
+    // (each CTA holds the correction of its own rows)
     uint8_t* outC = a.out_C + shot * 2 * (int64_t)LL;
     const int gpr = L / 4;  // 4-site groups per row
     for (int ax = 0; ax < 2; ++ax) {
       for (int i = tid; i < g.rows_local * gpr; i += nt) {
         const int y = row_lo + i / gpr, x = (i - (i / gpr) * gpr) * 4;
         const int w = (y << g.lws) + (x >> 5);
-        uint32_t bits = 0;
-#pragma unroll
-        for (int r = 0; r < CL; ++r) bits ^= Cluster<CL>::at(Cb, r)[ax * g.nws + w];
+        const uint32_t bits = Cb[ax * g.nws + w];
         const uint32_t nib = (bits >> (x & 31)) & 0xFu;
         *reinterpret_cast<uint32_t*>(outC + (size_t)ax * LL + (size_t)y * L + x) =
             (nib * 0x00204081u) & 0x01010101u;
@@ -716,9 +777,11 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
   g.nws = L << lws;
   g.off = 255 - m_max;
   g.cap = L * L < kListCap ? L * L : kListCap;
+  g.sparse_max = L * L / 64;
   g.ls = L + 4;
   g.plane_bytes = (size_t)4 * g.rows_local * g.ls;
-  smem = g.plane_bytes + (size_t)6 * g.nws * 4 + (size_t)((g.cap + 7) & ~7) * 2 + 64;
+  // sigma, two flipped-link maps (x and y each), correction (x and y), list
+  smem = g.plane_bytes + (size_t)7 * g.nws * 4 + (size_t)((g.cap + 7) & ~7) * 2 + 64;
   return true;
 }
 
