@@ -126,6 +126,38 @@ int qca_decode_batch_host(const uint8_t* syndrome, int L, int64_t shots, int max
                           uint64_t rng_seed, uint8_t* out_correction, int32_t* out_steps,
                           uint8_t* out_logical_fail, const qca_config* cfg);
 
+/* Size of the fixed device array behind qca_decode_batch_noalloc: 16 MiB. */
+#define QCA_NOALLOC_SCRATCH_BYTES (16 << 20)
+
+/* qca_decode_batch_async for callers that must not allocate device memory.
+ * (The paper has no counterpart; this is a property of the library.)
+ *
+ * Who needs it: code that may not call cudaMalloc or any routine that
+ * allocates -- for instance a control loop that has reserved all device memory
+ * up front and must keep its latency free of allocator calls, a host that hands
+ * the whole device to its own memory pool, or a caller in the middle of work
+ * where allocation is not permitted.  This entry point allocates nothing: the
+ * caller passes the inputs and outputs (same meaning and layout as
+ * qca_decode_batch), and the decoder state lives in a fixed array of
+ * QCA_NOALLOC_SCRATCH_BYTES that the library places in device memory when it is
+ * loaded (every GPU that loads the library keeps it until the process exits).
+ * It always runs the generic sweep, so results are bit-identical to
+ * qca_decode_batch.
+ *
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - Each shot needs 14 * L * L bytes (rounded up to 256) of the array; an L
+ *    whose single shot does not fit is rejected with QCA_ERR_UNSUPPORTED.
+ *    Larger batches simply take several passes over the array.
+ *  - Every call shares the one array, which keeps the last call's contents:
+ *    calls that overlap on the GPU (for instance on two streams without an
+ *    ordering between them) race and give wrong results.  Issue them on one
+ *    stream, or order them.
+ * Errors as for qca_decode_batch_async. */
+int qca_decode_batch_noalloc(const uint8_t* syndrome, int L, int64_t shots, int max_steps,
+                             uint64_t rng_seed, uint8_t* out_correction, int32_t* out_steps,
+                             uint8_t* out_logical_fail, const qca_config* cfg, void* stream);
+
 /* Kernel path chosen for a lattice size: 1 = on-chip fast sweep, 2 = on-chip
  * sweep on a 2-CTA cluster, 0 = generic sweep with HBM-resident state.
  * Returns a negative code for an unsupported L. */

@@ -69,6 +69,7 @@ def lib():
             "qca_decode_syndrome_batch_async": ([vp, i32, i64, i32, u64, vp, vp, vp, vp, cfgp, vp],
                                                 i32),
             "qca_decode_batch_host": ([vp, i32, i64, i32, u64, vp, vp, vp, cfgp], i32),
+            "qca_decode_batch_noalloc": ([vp, i32, i64, i32, u64, vp, vp, vp, cfgp, vp], i32),
             "qca_kernel_path": ([i32, cfgp], i32),
             "qca_free_workspace": ([], i32),
         }
@@ -207,6 +208,29 @@ def decode_batch_host(errors, max_steps: int = 4096, rng_seed: int = 0, *, v: in
         ctypes.c_void_p(errors.data_ptr()), L, shots, max_steps, rng_seed & (2**64 - 1),
         ctypes.c_void_p(C.data_ptr()) if C is not None else None,
         ctypes.c_void_p(steps.data_ptr()), ctypes.c_void_p(fail.data_ptr()), ctypes.byref(cfg)))
+    return C, steps, fail
+
+
+def decode_batch_noalloc(errors, out, max_steps: int = 4096, rng_seed: int = 0, *, v: int = 3,
+                         m_max: int = 255, p_move: float = 0.0, shot_offset: int = 0,
+                         stream=None):
+    """Decode through qca_decode_batch_noalloc: the library allocates nothing.
+
+    For callers that cannot allocate device memory while decoding (see the
+    entry point's comment in include/qca.h): the caller provides the output
+    tensors ``out = (correction, steps, logical_fail)``; the decoder state uses
+    the library's fixed device array.  Calls that overlap on the GPU race on
+    that array.
+    """
+    torch = _torch()
+    shots, L = errors.shape[0], errors.shape[-1]
+    _dev_u8(torch, errors, (shots, 2, L, L), "errors")
+    C, steps, fail = out
+    cfg = make_config(v, m_max, p_move, shot_offset)
+    _check(lib().qca_decode_batch_noalloc(
+        ctypes.c_void_p(errors.data_ptr()), L, shots, max_steps, rng_seed & (2**64 - 1),
+        ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(steps.data_ptr()),
+        ctypes.c_void_p(fail.data_ptr()), ctypes.byref(cfg), _stream(torch, stream)))
     return C, steps, fail
 
 

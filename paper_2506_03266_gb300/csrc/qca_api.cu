@@ -194,6 +194,26 @@ int qca_decode_syndrome_batch_async(const uint8_t* sigma, int L, int64_t shots, 
   return dispatch(a, (cudaStream_t)stream);
 }
 
+int qca_decode_batch_noalloc(const uint8_t* syndrome, int L, int64_t shots, int max_steps,
+                             uint64_t rng_seed, uint8_t* out_correction, int32_t* out_steps,
+                             uint8_t* out_logical_fail, const qca_config* cfg, void* stream) {
+  int rc = check_sizes(L, shots, max_steps);
+  if (rc) return rc;
+  qca_config c;
+  if ((rc = check_config(cfg, &c))) return rc;
+  if (shots > 0 && (!syndrome || !out_correction || !out_steps || !out_logical_fail)) {
+    set_error("NULL array pointer");
+    return QCA_ERR_ARG;
+  }
+  DecodeArgs a;
+  fill_args(a, syndrome, L, shots, max_steps, rng_seed, c);
+  a.out_C = out_correction;
+  a.out_steps = out_steps;
+  a.out_flag = out_logical_fail;
+  if (shots == 0) return QCA_OK;
+  return launch_generic_noalloc(a, (cudaStream_t)stream);
+}
+
 int qca_kernel_path(int L, const qca_config* cfg) {
   int rc = check_sizes(L, 0, 0);
   if (rc) return rc;

@@ -57,5 +57,8 @@ int launch_generic(const DecodeArgs& a, cudaStream_t stream);
 int generic_workspace_release();
 int fast_path_for(int L, int v, int m_max);  // 0 generic, 1 single-CTA, 2 two-CTA cluster
 int launch_fast(const DecodeArgs& a, cudaStream_t stream);
+// Generic sweep on the library's fixed device array (no allocation).
+int launch_generic_noalloc(const DecodeArgs& a, cudaStream_t stream);
+size_t noalloc_slot_bytes(int L);
 
 }  // namespace qca

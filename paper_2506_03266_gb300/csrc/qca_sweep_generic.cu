@@ -260,4 +260,63 @@ int launch_generic(const DecodeArgs& a, cudaStream_t stream) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Decoding without any allocation.  The per-shot state of the generic sweep
+// lives in this fixed array instead of the cached workspace.  Every GPU that
+// loads the library holds the array until the process exits.  The sweep
+// writes all state it reads (fields, syndrome, correction, move and flip
+// bytes) at the start of each shot, so the array needs no clearing between
+// calls; it keeps whatever the last call left in it.
+static __device__ __align__(256) uint8_t g_noalloc_scratch[QCA_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+// Device address of g_noalloc_scratch, looked up once per device.
+std::mutex g_noalloc_mu;
+uint8_t* g_noalloc_ptr[64] = {};
+}  // namespace
+
+size_t noalloc_slot_bytes(int L) {
+  const size_t LL = (size_t)L * L;
+  return ((14 * LL) + 255) & ~(size_t)255;
+}
+
+int launch_generic_noalloc(const DecodeArgs& a, cudaStream_t stream) {
+  const size_t slot = noalloc_slot_bytes(a.L);
+  if (slot > (size_t)QCA_NOALLOC_SCRATCH_BYTES) {
+    set_error("L = %d needs %zu bytes of decoder state per shot, more than the %d-byte "
+              "fixed scratch of the no-allocation entry point",
+              a.L, slot, QCA_NOALLOC_SCRATCH_BYTES);
+    return QCA_ERR_UNSUPPORTED;
+  }
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) {
+    set_error("device index %d out of range", dev);
+    return QCA_ERR_UNSUPPORTED;
+  }
+  uint8_t* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      // In host code the array's name only stands in for it; the kernel needs
+      // the device address, valid on the current device.
+      e = cudaGetSymbolAddress(reinterpret_cast<void**>(&g_noalloc_ptr[dev]), g_noalloc_scratch);
+      if (e != cudaSuccess) {
+        g_noalloc_ptr[dev] = nullptr;
+        return cuda_fail(e, "cudaGetSymbolAddress of the no-allocation scratch");
+      }
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  if (a.shots == 0) return QCA_OK;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "SM count query");
+  int64_t slots = (int64_t)(QCA_NOALLOC_SCRATCH_BYTES / slot);
+  if (slots > (int64_t)sms * 4) slots = (int64_t)sms * 4;
+  if (slots > a.shots) slots = a.shots;
+  sweep_generic_kernel<<<(unsigned)slots, kThreads, 0, stream>>>(a, scratch, slot);
+  return cuda_fail(cudaGetLastError(), "no-allocation sweep launch");
+}
+
 }  // namespace qca
