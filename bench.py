@@ -50,6 +50,22 @@ ALU_PEAK_LANE_OPS = 152 * 64 * 2 * 2.070e9
 TRAFFIC_BYTES_PER_LAUNCH = None
 
 
+def shard(rank: int, shots_per_rank: int):
+    """Shot range of one rank under weak scaling: rank r decodes global shots
+    [r * n, (r + 1) * n).  Shots are independent, so no data crosses ranks."""
+    return rank * shots_per_rank, shots_per_rank
+
+
+def reduce_time_max(seconds: float, dist=None, device=None) -> float:
+    """Max over ranks of a per-rank time (the job ends when the slowest rank does)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _oracle_worker(args):
     """CPU-baseline worker: decode shots with the oracle (spawned process)."""
     L, p, seed, shot, max_steps = args
@@ -236,7 +252,8 @@ def main():
     L, shots = args.L, args.shots
     stream = torch.cuda.current_stream()
     # each rank its own shots (seeded by rank), sampled on the device
-    N = qca.sample_errors(L, shots, args.p, seed=0, shot0=rank * shots)
+    shot0, _ = shard(rank, shots)
+    N = qca.sample_errors(L, shots, args.p, seed=0, shot0=shot0)
     C = torch.empty_like(N)
     steps = torch.empty(shots, dtype=torch.int32, device="cuda")
     fail = torch.empty(shots, dtype=torch.uint8, device="cuda")
@@ -270,9 +287,7 @@ def main():
     fail_h = fail.cpu()
     site_updates = int(steps_h.to(torch.int64).sum()) * L * L
     if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = reduce_time_max(total_ms, dist, "cuda")
         su = torch.tensor([site_updates], device="cuda", dtype=torch.int64)
         dist.all_reduce(su)
         site_updates_all = int(su.item())
@@ -295,11 +310,7 @@ def main():
         for _ in range(args.steps):
             qca.decode_batch_host(Nh, MAX_STEPS, correction=False, out=(None, steps_o, fail_o))
         barrier()
-        el = (time.perf_counter() - t0) / args.steps
-        if dist is not None:
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = reduce_time_max((time.perf_counter() - t0) / args.steps, dist, "cuda")
         assert torch.equal(steps_o, steps_h) and torch.equal(fail_o, fail_h)
         e2e = {"value": world * shots / el, "unit": UNIT,
                "h2d_bytes_per_step": int(Nh.numel()), "d2h_bytes_per_step": shots * 5}
