@@ -45,9 +45,25 @@ UNIT = "shot-decodes/s"
 ALU_OPS_PER_SITE_UPDATE = 16
 ALU_PEAK_LANE_OPS = 152 * 64 * 2 * 2.070e9
 
-# DRAM traffic per launch of the dominant kernel, from the ncu capture named in
-# the comment; None until captured for the current kernel version.
-TRAFFIC_BYTES_PER_LAUNCH = None
+# DRAM traffic of the dominant kernel per decoded shot at L = 256, p = 0.05
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 4000 shots,
+# profiles/fast_kernel_L256_p005_full.md), valid only for the kernel source
+# whose SHA-256 prefix is recorded with it; reported as null otherwise.
+TRAFFIC_PER_SHOT = {"sha256_prefix": "afbd23fa2d68cab7", "L": 256, "p": 0.05,
+                    "bytes_per_shot": (525.750784e6 + 479.547904e6) / 4000}
+
+
+def traffic_per_launch(L, p, shots):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2506_03266_gb300", "csrc", "qca_sweep_fast.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    t = TRAFFIC_PER_SHOT
+    if sha != t["sha256_prefix"] or L != t["L"] or p != t["p"]:
+        return None
+    return t["bytes_per_shot"] * shots
 
 
 def shard(rank: int, shots_per_rank: int):
@@ -336,7 +352,7 @@ def main():
                     "max_steps_seen": int(steps_h.max())},
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": ALU_PEAK_LANE_OPS / 1e9,
                      "unit": "Glane-op/s", "frac": achieved / ALU_PEAK_LANE_OPS,
-                     "traffic": TRAFFIC_BYTES_PER_LAUNCH,
+                     "traffic": traffic_per_launch(L, args.p, shots),
                      "kernel_ms": statistics.mean(kernel_ms)},
         "clocks": clk,
         "gpu_launches": launches,
