@@ -62,8 +62,8 @@ struct FastGeom {
   int off;              // 255 - m_max
   int cap;              // anyon-list capacity
   int sparse_max;       // most anyons for which the per-anyon scatter beats the dense pass
-  int ls;               // plane row stride in bytes: L + 4, so that a column of a
-                        // plane does not fall into one shared-memory bank
+  int ls;               // plane row stride in bytes (L + 4 or L + 8), so that a column
+                        // of a plane does not fall into one shared-memory bank
   size_t plane_bytes;   // 4 * rows_local * ls
 };
 
@@ -307,15 +307,36 @@ __device__ __forceinline__ uint32_t row_bits(const uint32_t* bm, const FastGeom&
   return n >= 32 ? v : (v & ((1u << n) - 1u));
 }
 
-// Bits of columns start, start+1, ..., start+9 (mod L) of bitmap row r.
-__device__ __forceinline__ uint32_t row_window10(const uint32_t* bm, const FastGeom& g, int r,
-                                                 int start) {
+// Bits of columns start, start+1, ..., start+n-1 (mod L) of bitmap row r, n <= 32.
+__device__ __forceinline__ uint32_t row_window(const uint32_t* bm, const FastGeom& g, int r,
+                                               int start, int n) {
   const int L = g.L;
   const int s = start < 0 ? start + L : start;
-  const int n1 = min(10, L - s);
+  const int n1 = min(n, L - s);
   uint32_t v = row_bits(bm, g, r, s, n1);
-  if (n1 < 10) v |= row_bits(bm, g, r, 0, 10 - n1) << n1;
+  if (n1 < n) v |= row_bits(bm, g, r, 0, n - n1) << n1;
   return v;
+}
+
+// KW consecutive 32-bit words of a plane row: one 32- or 64-bit access (the
+// 64-bit form keeps a warp's row access free of bank conflicts).
+template <int KW>
+__device__ __forceinline__ void load_words(const uint8_t* p, uint32_t (&w)[KW]) {
+  if constexpr (KW == 2) {
+    const uint2 v = *reinterpret_cast<const uint2*>(p);
+    w[0] = v.x;
+    w[1] = v.y;
+  } else {
+    w[0] = *reinterpret_cast<const uint32_t*>(p);
+  }
+}
+template <int KW>
+__device__ __forceinline__ void store_words(uint8_t* p, const uint32_t (&w)[KW]) {
+  if constexpr (KW == 2) {
+    *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+  } else {
+    *reinterpret_cast<uint32_t*>(p) = w[0];
+  }
 }
 
 // Anyon terms of the fused message update computed densely for every site of
@@ -343,51 +364,51 @@ __device__ void dense_terms(const uint32_t* sig, const uint16_t* list, int count
   if (lane_on) {
     const uint32_t* bm = (pl < 2) ? sig : sT;
     const uint32_t off2 = (uint32_t)(g.off + 2) * 0x01010101u;
+    // the lane's KW plane words cover sites 4c .. 4c + 4KW - 1 of a row; window
+    // bit i <-> column 4c - 3 + i, i in [0, 4KW + 6)
+    const int c = cword;
+    constexpr int NB = 4 * KW + 6;
+    auto ext = [&](int i) -> uint32_t {
+      int R = R0 + i;
+      R = R < 0 ? R + L : (R >= L ? R - L : R);
+      return row_window(bm, g, R, 4 * c - 3, NB);
+    };
+    uint32_t e0 = ext(-3), e1 = ext(-2), e2 = ext(-1), e3 = ext(0), e4 = ext(1), e5 = ext(2);
+    uint8_t* dst = planes + ((size_t)(pl * g.rows_local + lrow0)) * g.ls + 4 * c;
+    for (int i = 0; i < g.H; ++i) {
+      const uint32_t e6 = ext(i + 3);  // window rows i-3 .. i+3 = e0 .. e6
+      const uint32_t v1 = e2 | e3 | e4;
+      const uint32_t v2 = v1 | e1 | e5;
+      const uint32_t v3 = v2 | e0 | e6;
+      uint32_t val[KW], old[KW];
+      if (MERGE) load_words<KW>(dst + (size_t)i * g.ls, old);
 #pragma unroll
-    for (int q = 0; q < KW; ++q) {
-      const int c = cword + q;  // plane word: sites 4c .. 4c+3 of the row
-      // window bit i <-> column 4c - 3 + i, i in [0, 10)
-      auto ext = [&](int i) -> uint32_t {
-        int R = R0 + i;
-        R = R < 0 ? R + L : (R >= L ? R - L : R);
-        return row_window10(bm, g, R, 4 * c - 3);
-      };
-      uint32_t e0 = ext(-3), e1 = ext(-2), e2 = ext(-1), e3 = ext(0), e4 = ext(1), e5 = ext(2);
-      uint8_t* dst = planes + ((size_t)(pl * g.rows_local + lrow0)) * g.ls + 4 * c;
-      for (int i = 0; i < g.H; ++i) {
-        const uint32_t e6 = ext(i + 3);  // window rows i-3 .. i+3 = e0 .. e6
-        const uint32_t v1 = e2 | e3 | e4;
-        const uint32_t v2 = v1 | e1 | e5;
-        const uint32_t v3 = v2 | e0 | e6;
+      for (int q = 0; q < KW; ++q) {
         uint32_t a1, a2, a3;
         if (plus) {  // term at site l comes from column l - d
-          a1 = (v1 >> 2) & 0xFu;
-          a2 = (v2 >> 1) & 0xFu;
-          a3 = v3 & 0xFu;
+          a1 = (v1 >> (2 + 4 * q)) & 0xFu;
+          a2 = (v2 >> (1 + 4 * q)) & 0xFu;
+          a3 = (v3 >> (4 * q)) & 0xFu;
         } else {     // from column l + d
-          a1 = (v1 >> 4) & 0xFu;
-          a2 = (v2 >> 5) & 0xFu;
-          a3 = (v3 >> 6) & 0xFu;
+          a1 = (v1 >> (4 + 4 * q)) & 0xFu;
+          a2 = (v2 >> (5 + 4 * q)) & 0xFu;
+          a3 = (v3 >> (6 + 4 * q)) & 0xFu;
         }
         // bit k -> byte k (0 / 1)
         const uint32_t b1 = (a1 * 0x00204081u) & 0x01010101u;
         const uint32_t b12 = ((a1 | a2) * 0x00204081u) & 0x01010101u;
         const uint32_t m = (((a1 | a2 | a3) * 0x00204081u) & 0x01010101u) * 0xFFu;
         // off + d - 1 = (off + 2) - [d = 1] - [d <= 2]
-        uint32_t val = off2 - b1 - b12;
-        uint32_t* w = reinterpret_cast<uint32_t*>(dst + (size_t)i * g.ls);
-        if (MERGE)
-          val = (val & m) | (*w & ~m);
-        else
-          val |= ~m;
-        *w = val;
-        e0 = e1;
-        e1 = e2;
-        e2 = e3;
-        e3 = e4;
-        e4 = e5;
-        e5 = e6;
+        val[q] = off2 - b1 - b12;
+        val[q] = MERGE ? ((val[q] & m) | (old[q] & ~m)) : (val[q] | ~m);
       }
+      store_words<KW>(dst + (size_t)i * g.ls, val);
+      e0 = e1;
+      e1 = e2;
+      e2 = e3;
+      e3 = e4;
+      e4 = e5;
+      e5 = e6;
     }
   }
   __syncthreads();
@@ -436,15 +457,10 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
     if (warp_on) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-#pragma unroll
-        for (int q = 0; q < KW; ++q) {
-          halo[k][q] = *reinterpret_cast<const uint32_t*>(
-              plane_ptr<CL>(planes, g, pl, wrapi(R0 - 3 + k, L), (cword + q) * 4));
-          int Rb = R0 + g.H + k;
-          if (Rb >= L) Rb -= L;
-          halo[3 + k][q] = *reinterpret_cast<const uint32_t*>(
-              plane_ptr<CL>(planes, g, pl, Rb, (cword + q) * 4));
-        }
+        load_words<KW>(plane_ptr<CL>(planes, g, pl, wrapi(R0 - 3 + k, L), cword * 4), halo[k]);
+        int Rb = R0 + g.H + k;
+        if (Rb >= L) Rb -= L;
+        load_words<KW>(plane_ptr<CL>(planes, g, pl, Rb, cword * 4), halo[3 + k]);
       }
     }
   };
@@ -508,13 +524,16 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
       } else if (warp_on) {
         // ================= 1a. dense message update of this thread's band
         Chain cH[KW], cL[KW];
+        uint32_t first[3][KW];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) load_words<KW>(my_rows + (size_t)k * LS, first[k]);
 #pragma unroll
         for (int q = 0; q < KW; ++q) {
           uint32_t ah[6], al[6];
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
             ah[k] = halo[k][q];
-            ah[3 + k] = *reinterpret_cast<const uint32_t*>(my_rows + (size_t)k * LS + q * 4);
+            ah[3 + k] = first[k][q];
           }
 #pragma unroll
           for (int k = 0; k < 6; ++k) al[k] = ah[k] << 8;
@@ -551,18 +570,12 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
               out[KW - 1] = __funnelshift_r(m[KW - 1], nb, 24);
             }
           }
-          if (lane_on) {
-#pragma unroll
-            for (int q = 0; q < KW; ++q)
-              *reinterpret_cast<uint32_t*>(my_rows + (size_t)i * LS + q * 4) = out[q];
-          }
+          if (lane_on) store_words<KW>(my_rows + (size_t)i * LS, out);
         };
 #pragma unroll 4
         for (int i = 0; i < g.H - 3; ++i) {
           uint32_t in[KW];
-#pragma unroll
-          for (int q = 0; q < KW; ++q)
-            in[q] = *reinterpret_cast<const uint32_t*>(my_rows + (size_t)(i + 3) * LS + q * 4);
+          load_words<KW>(my_rows + (size_t)(i + 3) * LS, in);
           row(i, in);
         }
 #pragma unroll
@@ -778,7 +791,9 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
   g.off = 255 - m_max;
   g.cap = L * L < kListCap ? L * L : kListCap;
   g.sparse_max = L * L / 64;
-  g.ls = L + 4;
+  // row pitch: L + 4 bytes (one extra bank per row); L + 8 keeps the 8-byte
+  // alignment of the 64-bit accesses used with two words per lane
+  g.ls = L + (KW == 2 ? 8 : 4);
   g.plane_bytes = (size_t)4 * g.rows_local * g.ls;
   // sigma, two flipped-link maps (x and y each), correction (x and y), list
   smem = g.plane_bytes + (size_t)7 * g.nws * 4 + (size_t)((g.cap + 7) & ~7) * 2 + 64;
