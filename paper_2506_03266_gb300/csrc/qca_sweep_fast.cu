@@ -221,8 +221,16 @@ __device__ __forceinline__ int apply_flips(uint32_t* sig, const uint32_t* flip, 
   const int per = (g.nws + nt - 1) / nt;
   const int w0 = tid * per, w1 = min(g.nws, w0 + per);
   const int last_w = (L - 1) >> 5, last_b = (L - 1) & 31;
+  // the words of a thread are handled as independent chains (unrolled for up
+  // to kMaxPer words, the most any configuration gives a thread)
+  constexpr int kMaxPer = 4;
+  uint32_t snew[kMaxPer];
   int n = 0;
-  for (int w = w0; w < w1; ++w) {
+#pragma unroll
+  for (int k = 0; k < kMaxPer; ++k) {
+    const int w = w0 + k;
+    snew[k] = 0;
+    if (w >= w1) continue;
     const int y = w >> g.lws, j = w & wsm, x0 = j << 5;
     if (x0 >= L) continue;  // padding word
     const int ym = (y == 0) ? L - 1 : y - 1;
@@ -235,6 +243,7 @@ __device__ __forceinline__ int apply_flips(uint32_t* sig, const uint32_t* flip, 
     const uint32_t valid = (L - x0 >= 32) ? 0xFFFFFFFFu : ((1u << (L - x0)) - 1u);
     const uint32_t s = sig[w] ^ ((fx ^ fxl ^ fy ^ fyu) & valid);
     sig[w] = s;
+    snew[k] = s;
     n += __popc(s);
     if (y >= row_lo && y < row_hi) {
       Cb[w] ^= fx;
@@ -253,13 +262,15 @@ __device__ __forceinline__ int apply_flips(uint32_t* sig, const uint32_t* flip, 
   if (lane == 31 && total) wbase = atomicAdd(count, total);
   wbase = __shfl_sync(0xffffffffu, wbase, 31);
   int pos = wbase + incl - n;
-  for (int w = w0; w < w1; ++w) {
-    uint32_t b = sig[w];
+#pragma unroll
+  for (int k = 0; k < kMaxPer; ++k) {
+    const int w = w0 + k;
+    uint32_t b = snew[k];
     const int y = w >> g.lws, xb = (w & wsm) << 5;
     while (b) {
-      const int k = __ffs(b) - 1;
+      const int q = __ffs(b) - 1;
       b &= b - 1;
-      if (pos < g.cap) list[pos] = (uint16_t)((y << 8) | (xb + k));
+      if (pos < g.cap) list[pos] = (uint16_t)((y << 8) | (xb + q));
       ++pos;
     }
   }
@@ -788,6 +799,7 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
   while ((1 << lws) < wpr) ++lws;
   g.lws = lws;
   g.nws = L << lws;
+  if ((g.nws + threads - 1) / threads > 4) return false;  // apply_flips handles <= 4 words/thread
   g.off = 255 - m_max;
   g.cap = L * L < kListCap ? L * L : kListCap;
   g.sparse_max = L * L / 64;
