@@ -158,6 +158,51 @@ int qca_decode_batch_noalloc(const uint8_t* syndrome, int L, int64_t shots, int 
                              uint64_t rng_seed, uint8_t* out_correction, int32_t* out_steps,
                              uint8_t* out_logical_fail, const qca_config* cfg, void* stream);
 
+/* ---- Uneven batches: shots of different lattice sizes in one decode ------
+ * The Monte-Carlo sweeps of Sec. 7 cover several L; these entry points decode a
+ * mix of sizes together.  Shots are packed back to back: shot s occupies the
+ * uint8 [2][L_s][L_s] block at byte offset off_s = sum_{t<s} 2 L_t^2 of the
+ * input (and of the correction output); steps and flags are indexed by s. */
+
+/* Per-shot L and noise threshold of the mixed synthetic workload (host only):
+ * L_s in {24, 48, 64, 96, 128, 192} with probabilities 30/25/20/12/8/5 %,
+ * drawn as splitmix64(splitmix64(seed ^ 0x4C53495A45) ^ s) against cumulative
+ * cut points floor(c/100 * 2^64); the flip threshold is
+ * floor(0.01 * 2^64) + ((v * floor(0.06 * 2^64)) >> 64) with
+ * v = splitmix64(splitmix64(seed ^ 0x5052415445) ^ s), i.e. p ~ U[0.01, 0.07).
+ * Writes out_L[shots] and out_thr[shots] (host arrays). */
+int qca_uneven_draw(int64_t shots, uint64_t seed, int32_t* out_L, uint64_t* out_thr);
+
+typedef struct qca_uneven_plan_s* qca_uneven_plan_t;
+
+/* Group the shots (host array L_host[shots]) by size and place the shot lists,
+ * the block offsets and the work counters in device memory owned by the plan.
+ * offsets_host (may be NULL) receives off_s; total_bytes (may be NULL) the size
+ * of the packed input.  Not for use under stream capture (it allocates). */
+int qca_uneven_plan_create(const int32_t* L_host, int64_t shots, int64_t* offsets_host,
+                           int64_t* total_bytes, qca_uneven_plan_t* out_plan);
+int qca_uneven_plan_destroy(qca_uneven_plan_t plan);
+/* Device array of the plan's block offsets (int64 [shots]), owned by the plan. */
+int qca_uneven_plan_offsets_device(qca_uneven_plan_t plan, const int64_t** offsets_device);
+
+/* i.i.d. noise for a packed uneven batch: shot s gets the L_s x L_s torus at
+ * offsets_dev[s] with flip threshold thr_dev[s] (all device arrays); the link
+ * draws are those of qca_sample_errors for shot index s. */
+int qca_sample_errors_uneven_async(const int32_t* L_dev, const int64_t* offsets_dev,
+                                   const uint64_t* thr_dev, int64_t shots, uint64_t seed,
+                                   uint8_t* out_errors, void* stream);
+
+/* Decode a packed uneven batch: for every size present, one persistent kernel
+ * whose CTAs take shots from that size's work counter (work stealing; every
+ * shot retires after its own number of steps), all sizes running concurrently
+ * on streams forked from and joined to `stream`.  Only kernel launches, memset
+ * and event operations are enqueued, so the call can be captured in a CUDA graph
+ * once one uncaptured call has sized the library's workspaces.  Outputs are
+ * bit-identical to decoding each shot with qca_decode_batch. */
+int qca_decode_uneven_async(qca_uneven_plan_t plan, const uint8_t* errors, int max_steps,
+                            uint64_t rng_seed, uint8_t* out_correction, int32_t* out_steps,
+                            uint8_t* out_logical_fail, const qca_config* cfg, void* stream);
+
 /* Kernel path chosen for a lattice size: 1 = on-chip fast sweep, 2 = on-chip
  * sweep on a 2-CTA cluster, 0 = generic sweep with HBM-resident state.
  * Returns a negative code for an unsupported L. */

@@ -64,6 +64,9 @@ def _load():
         lib.qo_prob_threshold.restype = c_u64
         lib.qo_sample_errors.argtypes = [c_int, c_i64, c_i64, c_u64, c_u64, u8p]
         lib.qo_sample_errors.restype = None
+        lib.qo_uneven_draw.argtypes = [c_i64, c_u64, i32p,
+                                       np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")]
+        lib.qo_uneven_draw.restype = None
         lib.qo_syndrome.argtypes = [c_int, u8p, i8p]
         lib.qo_syndrome.restype = None
         lib.qo_message_substep.argtypes = [c_int, c_int, i8p, i32p, i32p]
@@ -101,11 +104,23 @@ def prob_threshold(p: float) -> int:
     return int(_load().qo_prob_threshold(float(p)))
 
 
-def sample_errors(L: int, shots: int, p: float, seed: int, shot0: int = 0) -> np.ndarray:
-    """i.i.d. bit-flip noise (Sec. 7), uint8 [shots][2][L][L]."""
+def sample_errors(L: int, shots: int, p: float, seed: int, shot0: int = 0,
+                  thr: int = None) -> np.ndarray:
+    """i.i.d. bit-flip noise (Sec. 7), uint8 [shots][2][L][L]; `thr` (the integer
+    flip threshold) overrides p."""
     out = np.zeros((shots, 2, L, L), dtype=np.uint8)
-    _load().qo_sample_errors(L, shot0, shots, prob_threshold(p), seed, out)
+    t = prob_threshold(p) if thr is None else int(thr)
+    _load().qo_sample_errors(L, shot0, shots, t, seed, out)
     return out
+
+
+def uneven_draw(shots: int, seed: int):
+    """Per-shot (L, flip threshold) of the mixed-size workload."""
+    L = np.zeros(shots, dtype=np.int32)
+    thr = np.zeros(shots, dtype=np.uint64)
+    if shots:
+        _load().qo_uneven_draw(shots, seed, L, thr)
+    return L, thr
 
 
 def syndrome(edges: np.ndarray) -> np.ndarray:

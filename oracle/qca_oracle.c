@@ -73,6 +73,33 @@ void qo_sample_errors(int L, int64_t shot0, int64_t shots, uint64_t thr, uint64_
   }
 }
 
+/* Mixed-size workload of the Monte Carlo sweeps: per-shot L in
+ * {24, 48, 64, 96, 128, 192} with probabilities 30/25/20/12/8/5 per cent and
+ * a flip probability uniform in [0.01, 0.07), both from counter draws. */
+#define QO_TAG_SIZE 0x4C53495A45ULL
+#define QO_TAG_RATE 0x5052415445ULL
+
+void qo_uneven_draw(int64_t shots, uint64_t seed, int32_t* out_L, uint64_t* out_thr) {
+  static const int sizes[6] = {24, 48, 64, 96, 128, 192};
+  static const int percent_upto[6] = {30, 55, 75, 87, 95, 100};
+  const uint64_t klsize = qo_splitmix64(seed ^ QO_TAG_SIZE);
+  const uint64_t krate = qo_splitmix64(seed ^ QO_TAG_RATE);
+  const uint64_t t_lo = qo_prob_threshold(0.01), t_span = qo_prob_threshold(0.06);
+  for (int64_t s = 0; s < shots; ++s) {
+    uint64_t u = qo_splitmix64(klsize ^ (uint64_t)s);
+    /* class k is chosen when u < floor(percent_upto[k] / 100 * 2^64) */
+    int k;
+    for (k = 0; k < 5; ++k) {
+      unsigned __int128 cut = ((unsigned __int128)percent_upto[k] << 64) / 100;
+      if ((unsigned __int128)u < cut) break;
+    }
+    out_L[s] = sizes[k];
+    uint64_t v = qo_splitmix64(krate ^ (uint64_t)s);
+    unsigned __int128 scaled = (unsigned __int128)v * t_span;
+    out_thr[s] = t_lo + (uint64_t)(scaled >> 64);
+  }
+}
+
 /* ------------------------------------------------------------ lattice ---- */
 
 static int wrap(int i, int L) {

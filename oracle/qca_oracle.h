@@ -33,6 +33,8 @@ uint64_t qo_prob_threshold(double p);
 /* i.i.d. bit-flip noise of strength p (Sec. 7): shots [shot0, shot0+shots). */
 void qo_sample_errors(int L, int64_t shot0, int64_t shots, uint64_t thr, uint64_t seed,
                       uint8_t* out_edges);
+/* Per-shot L and flip threshold of the mixed-size workload (see the .c file). */
+void qo_uneven_draw(int64_t shots, uint64_t seed, int32_t* out_L, uint64_t* out_thr);
 /* sigma_r from the parity of the four links incident to r (Def. synch_ccqs). */
 void qo_syndrome(int L, const uint8_t* edges, int8_t* sigma);
 /* One application of the automaton rule A^(D), D = 2 (Def. Dd_msg_passing). */

@@ -70,6 +70,12 @@ def lib():
                                                 i32),
             "qca_decode_batch_host": ([vp, i32, i64, i32, u64, vp, vp, vp, cfgp], i32),
             "qca_decode_batch_noalloc": ([vp, i32, i64, i32, u64, vp, vp, vp, cfgp, vp], i32),
+            "qca_uneven_draw": ([i64, u64, vp, vp], i32),
+            "qca_uneven_plan_create": ([vp, i64, vp, vp, ctypes.POINTER(vp)], i32),
+            "qca_uneven_plan_destroy": ([vp], i32),
+            "qca_uneven_plan_offsets_device": ([vp, ctypes.POINTER(vp)], i32),
+            "qca_sample_errors_uneven_async": ([vp, vp, vp, i64, u64, vp, vp], i32),
+            "qca_decode_uneven_async": ([vp, vp, i32, u64, vp, vp, vp, cfgp, vp], i32),
             "qca_kernel_path": ([i32, cfgp], i32),
             "qca_free_workspace": ([], i32),
         }
@@ -232,6 +238,83 @@ def decode_batch_noalloc(errors, out, max_steps: int = 4096, rng_seed: int = 0, 
         ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(steps.data_ptr()),
         ctypes.c_void_p(fail.data_ptr()), ctypes.byref(cfg), _stream(torch, stream)))
     return C, steps, fail
+
+
+def uneven_draw(shots: int, seed: int):
+    """Per-shot L (int32) and flip threshold (uint64) of the mixed-size workload
+    (host computation, numpy arrays)."""
+    import numpy as np
+    L = np.zeros(shots, dtype=np.int32)
+    thr = np.zeros(shots, dtype=np.uint64)
+    if shots:
+        _check(lib().qca_uneven_draw(shots, seed & (2**64 - 1), L.ctypes.data_as(ctypes.c_void_p),
+                                     thr.ctypes.data_as(ctypes.c_void_p)))
+    return L, thr
+
+
+class UnevenPlan:
+    """Shots of mixed lattice sizes packed back to back (qca_uneven_plan_*)."""
+
+    def __init__(self, L_host):
+        import numpy as np
+        self.L = np.ascontiguousarray(L_host, dtype=np.int32)
+        self.shots = len(self.L)
+        self.offsets = np.zeros(self.shots, dtype=np.int64)
+        total = ctypes.c_int64()
+        h = ctypes.c_void_p()
+        _check(lib().qca_uneven_plan_create(self.L.ctypes.data_as(ctypes.c_void_p), self.shots,
+                                            self.offsets.ctypes.data_as(ctypes.c_void_p),
+                                            ctypes.byref(total), ctypes.byref(h)))
+        self.handle = h
+        self.total_bytes = total.value
+
+    def close(self):
+        if self.handle:
+            lib().qca_uneven_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def offsets_device_ptr(self) -> int:
+        p = ctypes.c_void_p()
+        _check(lib().qca_uneven_plan_offsets_device(self.handle, ctypes.byref(p)))
+        return p.value
+
+    def sample(self, thr_host, seed: int, out=None, stream=None):
+        """Packed noise on the device (uint8 [total_bytes])."""
+        torch = _torch()
+        import numpy as np
+        if out is None:
+            out = torch.empty(self.total_bytes, dtype=torch.uint8, device="cuda")
+        Ld = torch.from_numpy(self.L).cuda()
+        td = torch.from_numpy(np.ascontiguousarray(thr_host, dtype=np.uint64).view(np.int64)).cuda()
+        _check(lib().qca_sample_errors_uneven_async(
+            ctypes.c_void_p(Ld.data_ptr()), ctypes.c_void_p(self.offsets_device_ptr()),
+            ctypes.c_void_p(td.data_ptr()), self.shots, seed & (2**64 - 1),
+            ctypes.c_void_p(out.data_ptr()), _stream(torch, stream)))
+        torch.cuda.current_stream().synchronize()
+        return out
+
+    def decode(self, errors, max_steps: int = 4096, rng_seed: int = 0, out=None, v: int = 3,
+               m_max: int = 255, p_move: float = 0.0, stream=None):
+        """Decode packed noise; returns (correction packed uint8, steps, logical_fail)."""
+        torch = _torch()
+        if out is None:
+            C = torch.empty_like(errors)
+            steps = torch.empty(self.shots, dtype=torch.int32, device=errors.device)
+            fail = torch.empty(self.shots, dtype=torch.uint8, device=errors.device)
+        else:
+            C, steps, fail = out
+        cfg = make_config(v, m_max, p_move, 0)
+        _check(lib().qca_decode_uneven_async(
+            self.handle, ctypes.c_void_p(errors.data_ptr()), max_steps, rng_seed & (2**64 - 1),
+            ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(steps.data_ptr()),
+            ctypes.c_void_p(fail.data_ptr()), ctypes.byref(cfg), _stream(torch, stream)))
+        return C, steps, fail
 
 
 def free_workspace():

@@ -100,6 +100,15 @@ static int fill_args(DecodeArgs& a, const uint8_t* in, int L, int64_t shots, int
   return QCA_OK;
 }
 
+int fill_decode_args(DecodeArgs& a, const uint8_t* in, int L, int64_t shots, int max_steps,
+                     uint64_t seed, const qca_config* cfg) {
+  int rc = check_sizes(L, shots, max_steps);
+  if (rc) return rc;
+  qca_config c;
+  if ((rc = check_config(cfg, &c))) return rc;
+  return fill_args(a, in, L, shots, max_steps, seed, c);
+}
+
 }  // namespace qca
 
 using namespace qca;

@@ -38,7 +38,26 @@ struct DecodeArgs {
   uint8_t* out_flag;       // [shots]   (noise input)
   uint8_t* out_cut;        // [shots][2] (syndrome input)
   uint8_t* out_exhausted;  // [shots] or null (syndrome input)
+  // Uneven batches (optional): this launch decodes the shots shot_list[0 ..
+  // shots); a shot's input and correction blocks start at byte offsets[shot];
+  // CTAs take work from the counter *queue (work stealing) when it is set.
+  const int32_t* shot_list;
+  const int64_t* offsets;
+  unsigned int* queue;
 };
+
+// Byte offset of shot `shot`'s input block: [2][L][L] noise, or [L][L] sigma.
+__host__ __device__ __forceinline__ int64_t shot_offset_of(const DecodeArgs& a, int64_t shot) {
+  if (a.offsets) return a.offsets[shot];
+  const int64_t LL = (int64_t)a.L * a.L;
+  return shot * (a.from_sigma ? LL : 2 * LL);
+}
+// Byte offset of shot `shot`'s correction block ([2][L][L] for either input).
+__host__ __device__ __forceinline__ int64_t correction_offset_of(const DecodeArgs& a,
+                                                                 int64_t shot) {
+  if (a.offsets) return a.offsets[shot];
+  return shot * 2 * (int64_t)a.L * a.L;
+}
 
 // Per-thread error text (set by the host layer).
 void set_error(const char* fmt, ...);
@@ -49,6 +68,10 @@ __device__ __forceinline__ uint64_t move_step_key(uint64_t move_key, int64_t sho
   uint64_t k1 = splitmix64(move_key ^ (uint64_t)shot);
   return splitmix64(k1 ^ (uint64_t)(uint32_t)t);
 }
+
+// Validate sizes and options and fill the common fields of a DecodeArgs.
+int fill_decode_args(DecodeArgs& a, const uint8_t* in, int L, int64_t shots, int max_steps,
+                     uint64_t seed, const qca_config* cfg);
 
 // Launchers (return QCA_OK or an error code; errors already recorded).
 int launch_sample_errors(int L, int64_t shot0, int64_t shots, uint64_t thr, uint64_t seed,

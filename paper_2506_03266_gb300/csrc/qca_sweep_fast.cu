@@ -37,7 +37,9 @@
 // memory.  Two cluster barriers per step.
 #include <cooperative_groups.h>
 
+#include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "qca_internal.cuh"
 
@@ -476,8 +478,22 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
     }
   };
 
-  for (int64_t shot = cid; shot < a.shots; shot += nclusters) {
-    const uint8_t* N = a.in + shot * (a.from_sigma ? (int64_t)LL : 2 * (int64_t)LL);
+  // Work: static (cluster c takes c, c + nclusters, ...) or, with a queue,
+  // dynamic (rank 0 of the cluster takes the next index and shares it).
+  auto next_work = [&](int64_t prev) -> int64_t {
+    if (!a.queue) return prev < 0 ? (int64_t)cid : prev + nclusters;
+    if (rank == 0 && tid == 0) misc[4] = (int)atomicAdd(a.queue, 1u);
+    Cluster<CL>::sync();
+    const int64_t k = (int64_t)*Cluster<CL>::at(&misc[4], 0);
+    // rank 0 must neither overwrite the index nor exit (its shared memory goes
+    // away) before every CTA of the cluster has read it
+    if (CL > 1) Cluster<CL>::sync();
+    return k;
+  };
+  for (int64_t k = next_work(-1); k < a.shots; k = next_work(k)) {
+    const int64_t shot = a.shot_list ? (int64_t)a.shot_list[k] : k;
+    const int64_t base = shot_offset_of(a, shot);
+    const uint8_t* N = a.in + base;
     // ---- init: bitmaps cleared, sigma measured (every CTA of the cluster holds
     //      the full sigma); the planes are written whole by the first step
     {
@@ -712,7 +728,7 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
     }
     // ================= outputs: correction bytes, homology, steps, flag
     // (each CTA holds the correction of its own rows)
-    uint8_t* outC = a.out_C + shot * 2 * (int64_t)LL;
+    uint8_t* outC = a.out_C + correction_offset_of(a, shot);
     const int gpr = L / 4;  // 4-site groups per row
     for (int ax = 0; ax < 2; ++ax) {
       for (int i = tid; i < g.rows_local * gpr; i += nt) {
@@ -761,6 +777,8 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
     // partners may still read this CTA's correction share
     Cluster<CL>::sync();
   }
+  // no CTA of a cluster leaves while a partner could still reach its shared memory
+  if (CL > 1) Cluster<CL>::sync();
 }
 
 // ---------------------------------------------------------------- host ----
@@ -812,52 +830,76 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
   return true;
 }
 
+// Launch shape of one kernel variant for one (threads, shared memory) pair on
+// one device: found once with the occupancy calculator and cached, so that a
+// later call (for instance under CUDA-graph capture) only enqueues the launch.
+struct LaunchShape {
+  int dev, cl, kw, threads;
+  size_t smem;
+  int units;  // resident CTAs (CL = 1) or clusters (CL = 2) on the whole GPU
+};
+std::mutex g_shape_mu;
+std::vector<LaunchShape> g_shapes;
+
 template <int CL, int KW>
 int launch_t(const DecodeArgs& a, const FastGeom& g, int threads, size_t smem,
              cudaStream_t stream) {
   auto kern = fast_kernel<CL, KW>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return cuda_fail(e, "fast sweep smem attribute");
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
-  if (CL == 1) {
-    int resident = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, threads, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-    if (resident < 1) {
-      set_error("fast sweep does not fit on an SM (L=%d)", a.L);
-      return QCA_ERR_UNSUPPORTED;
-    }
-    int64_t grid = (int64_t)resident * sms;
-    if (grid > a.shots) grid = a.shots;
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.numAttrs = 0;
-  } else {
+  if (CL > 1) {
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = CL;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cfg.gridDim = dim3((unsigned)(CL * sms));
-    int clusters = 0;
-    e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
-    if (e != cudaSuccess) return cuda_fail(e, "cluster occupancy query");
-    if (clusters < 1) {
-      set_error("fast cluster sweep does not fit (L=%d)", a.L);
+  }
+  int units = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    for (const LaunchShape& s : g_shapes)
+      if (s.dev == dev && s.cl == CL && s.kw == KW && s.threads == threads && s.smem == smem)
+        units = s.units;
+  }
+  if (units < 0) {
+    // first use of this shape: allow the largest dynamic shared memory any
+    // configuration asks for, then ask the occupancy calculator
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "fast sweep smem attribute");
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (CL == 1) {
+      int resident = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, threads, smem);
+      if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+      units = resident * sms;
+    } else {
+      cfg.gridDim = dim3((unsigned)(CL * sms));
+      e = cudaOccupancyMaxActiveClusters(&units, kern, &cfg);
+      if (e != cudaSuccess) return cuda_fail(e, "cluster occupancy query");
+    }
+    if (units < 1) {
+      set_error("fast sweep does not fit on an SM (L=%d)", a.L);
       return QCA_ERR_UNSUPPORTED;
     }
-    int64_t grid = (int64_t)clusters;
-    if (grid > a.shots) grid = a.shots;
-    cfg.gridDim = dim3((unsigned)(grid * CL));
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_shapes.push_back({dev, CL, KW, threads, smem, units});
+  } else {
+    // the attribute is per function; a shape with less shared memory than a
+    // previous one still launches within the larger allowance
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "fast sweep smem attribute");
   }
+  int64_t grid = units;
+  if (grid > a.shots) grid = a.shots;
+  cfg.gridDim = dim3((unsigned)(grid * CL));
   e = cudaLaunchKernelEx(&cfg, kern, a, g);
   return cuda_fail(e, "fast sweep launch");
 }

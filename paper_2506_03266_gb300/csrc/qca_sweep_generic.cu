@@ -62,8 +62,19 @@ __global__ void __launch_bounds__(kThreads) sweep_generic_kernel(DecodeArgs a, u
   uint8_t* fl = dir + LL;            // [L][L] bit0: e_x flipped, bit1: e_y flipped
   __shared__ int s_red[2];
 
-  for (int64_t shot = blockIdx.x; shot < a.shots; shot += gridDim.x) {
-    const uint8_t* in = a.in + shot * (a.from_sigma ? (int64_t)LL : 2 * (int64_t)LL);
+  __shared__ int64_t s_next;
+  // static work (CTA b takes b, b + gridDim.x, ...) or a dynamic queue
+  auto next_work = [&](int64_t prev) -> int64_t {
+    if (!a.queue) return prev < 0 ? (int64_t)blockIdx.x : prev + gridDim.x;
+    __syncthreads();
+    if (threadIdx.x == 0) s_next = (int64_t)atomicAdd(a.queue, 1u);
+    __syncthreads();
+    return s_next;
+  };
+  for (int64_t k = next_work(-1); k < a.shots; k = next_work(k)) {
+    const int64_t shot = a.shot_list ? (int64_t)a.shot_list[k] : k;
+    const int64_t base = shot_offset_of(a, shot);
+    const uint8_t* in = a.in + base;
     int any = 0;
     for (int i = threadIdx.x; i < LL; i += blockDim.x) {
       const int x = i % L, y = i / L;
@@ -155,7 +166,7 @@ __global__ void __launch_bounds__(kThreads) sweep_generic_kernel(DecodeArgs a, u
       ++t;
     }
     // ---- outputs and homology (cut parities of N xor C, or of C alone)
-    uint8_t* outC = a.out_C + shot * 2 * (int64_t)LL;
+    uint8_t* outC = a.out_C + correction_offset_of(a, shot);
     int wx = 0, wy = 0;
     for (int i = threadIdx.x; i < 2 * LL; i += blockDim.x) outC[i] = Cc[i];
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
