@@ -203,6 +203,22 @@ int qca_decode_uneven_async(qca_uneven_plan_t plan, const uint8_t* errors, int m
                             uint64_t rng_seed, uint8_t* out_correction, int32_t* out_steps,
                             uint8_t* out_logical_fail, const qca_config* cfg, void* stream);
 
+/* ---- Tuning of the on-chip sweep (per lattice size, process-wide) --------
+ * band_height: rows of one plane a warp segment sweeps (4, 8, 16 or 32; it sets
+ * the threads per CTA and so the CTAs per SM); 0 = built-in heuristic.
+ * sparse_divisor: steps with at most L^2 / sparse_divisor anyons write the
+ * anyon terms per anyon, busier steps compute them densely; 0 = 64.
+ * An override that does not fit a size is ignored. */
+int qca_set_tuning(int L, int band_height, int sparse_divisor);
+/* Current effective values and the resulting threads per CTA (QCA_ERR_UNSUPPORTED
+ * if L has no on-chip kernel). */
+int qca_get_tuning(int L, int* band_height, int* sparse_divisor, int* threads_per_cta);
+/* Time every valid (band_height, sparse_divisor) on `shots` shots of i.i.d.
+ * noise p (seed) and keep the fastest as the setting for L.  Allocates
+ * temporary device memory; synchronises. */
+int qca_autotune(int L, int64_t shots, double p, uint64_t seed, int max_steps,
+                 int* best_band_height, int* best_sparse_divisor, float* best_ms);
+
 /* Kernel path chosen for a lattice size: 1 = on-chip fast sweep, 2 = on-chip
  * sweep on a 2-CTA cluster, 0 = generic sweep with HBM-resident state.
  * Returns a negative code for an unsupported L. */

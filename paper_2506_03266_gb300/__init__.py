@@ -71,6 +71,9 @@ def lib():
             "qca_decode_batch_host": ([vp, i32, i64, i32, u64, vp, vp, vp, cfgp], i32),
             "qca_decode_batch_noalloc": ([vp, i32, i64, i32, u64, vp, vp, vp, cfgp, vp], i32),
             "qca_uneven_draw": ([i64, u64, vp, vp], i32),
+            "qca_set_tuning": ([i32, i32, i32], i32),
+            "qca_get_tuning": ([i32, vp, vp, vp], i32),
+            "qca_autotune": ([i32, i64, ctypes.c_double, u64, i32, vp, vp, vp], i32),
             "qca_uneven_plan_create": ([vp, i64, vp, vp, ctypes.POINTER(vp)], i32),
             "qca_uneven_plan_destroy": ([vp], i32),
             "qca_uneven_plan_offsets_device": ([vp, ctypes.POINTER(vp)], i32),
@@ -238,6 +241,27 @@ def decode_batch_noalloc(errors, out, max_steps: int = 4096, rng_seed: int = 0, 
         ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(steps.data_ptr()),
         ctypes.c_void_p(fail.data_ptr()), ctypes.byref(cfg), _stream(torch, stream)))
     return C, steps, fail
+
+
+def set_tuning(L: int, band_height: int = 0, sparse_divisor: int = 0):
+    _check(lib().qca_set_tuning(L, band_height, sparse_divisor))
+
+
+def get_tuning(L: int):
+    """(band_height, sparse_divisor, threads_per_cta) in effect for L."""
+    h, d, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().qca_get_tuning(L, ctypes.byref(h), ctypes.byref(d), ctypes.byref(t)))
+    return h.value, d.value, t.value
+
+
+def autotune(L: int, shots: int, p: float, seed: int = 1, max_steps: int = 4096):
+    """Time the valid tunings for L and keep the fastest; returns
+    (band_height, sparse_divisor, ms per decode of `shots` shots)."""
+    _torch()
+    h, d, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(lib().qca_autotune(L, shots, float(p), seed & (2**64 - 1), max_steps, ctypes.byref(h),
+                              ctypes.byref(d), ctypes.byref(ms)))
+    return h.value, d.value, ms.value
 
 
 def uneven_draw(shots: int, seed: int):

@@ -37,6 +37,7 @@
 // memory.  Two cluster barriers per step.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -783,6 +784,12 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
 
 // ---------------------------------------------------------------- host ----
 
+// Tuning overrides per lattice size, set by qca_set_tuning / qca_autotune:
+// band height (0 = heuristic) and the anyon count below which the anyon terms
+// are scattered per anyon, as a divisor of L^2 (0 = 64).
+int g_tune_H[QCA_MAX_L + 1];
+int g_tune_div[QCA_MAX_L + 1];
+
 bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, size_t& smem) {
   if (L % 4 != 0 || L < 8 || L > 256) return false;
   if (m_max < 3) return false;  // the first-step fill assumes the d <= 3 terms fit below 0xFF
@@ -806,6 +813,10 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
     if (warps > max_warps) continue;
     if (!best_H) best_H = H;
     if (warps >= 16 || (L <= 64 && H >= 8)) best_H = H;
+    if (g_tune_H[L] == H) {  // a valid override wins
+      best_H = H;
+      break;
+    }
   }
   if (!best_H) return false;
   g.H = best_H;
@@ -820,7 +831,7 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
   if ((g.nws + threads - 1) / threads > 4) return false;  // apply_flips handles <= 4 words/thread
   g.off = 255 - m_max;
   g.cap = L * L < kListCap ? L * L : kListCap;
-  g.sparse_max = L * L / 64;
+  g.sparse_max = L * L / (g_tune_div[L] > 0 ? g_tune_div[L] : 64);
   // row pitch: L + 4 bytes (one extra bank per row); L + 8 keeps the 8-byte
   // alignment of the 64-bit accesses used with two words per lane
   g.ls = L + (KW == 2 ? 8 : 4);
@@ -930,3 +941,114 @@ int launch_fast(const DecodeArgs& a, cudaStream_t stream) {
 }
 
 }  // namespace qca
+
+using namespace qca;
+
+extern "C" {
+
+int qca_set_tuning(int L, int band_height, int sparse_divisor) {
+  if (L < 3 || L > QCA_MAX_L || band_height < 0 || sparse_divisor < 0) {
+    set_error("qca_set_tuning: bad arguments");
+    return QCA_ERR_ARG;
+  }
+  g_tune_H[L] = band_height;
+  g_tune_div[L] = sparse_divisor;
+  return QCA_OK;
+}
+
+int qca_get_tuning(int L, int* band_height, int* sparse_divisor, int* threads_per_cta) {
+  if (L < 3 || L > QCA_MAX_L) {
+    set_error("qca_get_tuning: bad L");
+    return QCA_ERR_ARG;
+  }
+  int CL, KW, threads = 0;
+  FastGeom g;
+  size_t smem;
+  const bool fast = make_geom(L, 255, CL, KW, g, threads, smem);
+  if (band_height) *band_height = fast ? g.H : 0;
+  if (sparse_divisor) *sparse_divisor = g_tune_div[L] > 0 ? g_tune_div[L] : 64;
+  if (threads_per_cta) *threads_per_cta = fast ? threads : 0;
+  return fast ? QCA_OK : QCA_ERR_UNSUPPORTED;
+}
+
+int qca_autotune(int L, int64_t shots, double p, uint64_t seed, int max_steps,
+                 int* best_band_height, int* best_sparse_divisor, float* best_ms) {
+  if (L < 3 || L > QCA_MAX_L || shots <= 0 || !(p >= 0.0 && p <= 1.0)) {
+    set_error("qca_autotune: bad arguments");
+    return QCA_ERR_ARG;
+  }
+  int CL, KW, threads;
+  FastGeom g;
+  size_t smem;
+  if (!make_geom(L, 255, CL, KW, g, threads, smem)) {
+    set_error("qca_autotune: L = %d has no on-chip kernel to tune", L);
+    return QCA_ERR_UNSUPPORTED;
+  }
+  const size_t E = 2 * (size_t)L * L;
+  uint8_t *N = nullptr, *C = nullptr, *F = nullptr;
+  int32_t* S = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&N, E * shots);
+  if (e == cudaSuccess) e = cudaMalloc(&C, E * shots);
+  if (e == cudaSuccess) e = cudaMalloc(&F, shots);
+  if (e == cudaSuccess) e = cudaMalloc(&S, 4 * shots);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  int rc = cuda_fail(e, "qca_autotune setup");
+  if (rc == QCA_OK) rc = qca_sample_errors_async(L, 0, shots, p, seed, N, st);
+  const int saved_H = g_tune_H[L], saved_div = g_tune_div[L];
+  int bH = 0, bD = 0;
+  float bms = 1e30f;
+  for (int H : {4, 8, 16, 32}) {
+    if (rc != QCA_OK) break;
+    g_tune_H[L] = H;
+    int CL2, KW2, th2;
+    FastGeom g2;
+    size_t sm2;
+    if (!make_geom(L, 255, CL2, KW2, g2, th2, sm2) || g2.H != H) continue;  // invalid here
+    for (int div : {128, 64, 32}) {
+      g_tune_div[L] = div;
+      // one untimed run, then the median of three timed runs
+      rc = qca_decode_batch_async(N, L, shots, max_steps, 0, C, S, F, nullptr, st);
+      float t[3];
+      for (int r = 0; r < 3 && rc == QCA_OK; ++r) {
+        cudaEventRecord(e0, st);
+        rc = qca_decode_batch_async(N, L, shots, max_steps, 0, C, S, F, nullptr, st);
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) rc = cuda_fail(e, "qca_autotune timing");
+        if (rc == QCA_OK) cudaEventElapsedTime(&t[r], e0, e1);
+      }
+      if (rc != QCA_OK) break;
+      std::sort(t, t + 3);
+      if (t[1] < bms) {
+        bms = t[1];
+        bH = H;
+        bD = div;
+      }
+    }
+  }
+  if (rc == QCA_OK && bH) {
+    g_tune_H[L] = bH;
+    g_tune_div[L] = bD;
+  } else {
+    g_tune_H[L] = saved_H;
+    g_tune_div[L] = saved_div;
+  }
+  if (best_band_height) *best_band_height = bH;
+  if (best_sparse_divisor) *best_sparse_divisor = bD;
+  if (best_ms) *best_ms = bms;
+  if (st) cudaStreamSynchronize(st);
+  cudaFree(N);
+  cudaFree(C);
+  cudaFree(F);
+  cudaFree(S);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  return rc;
+}
+
+}  // extern "C"
