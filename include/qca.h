@@ -219,6 +219,95 @@ int qca_get_tuning(int L, int* band_height, int* sparse_divisor, int* threads_pe
 int qca_autotune(int L, int64_t shots, double p, uint64_t seed, int max_steps,
                  int* best_band_height, int* best_sparse_divisor, float* best_ms);
 
+/* ---------------------------------------------------------------------------
+ * Learned pre-decoder in front of the automaton.  The paper has no learned
+ * component; this stage is an addition whose only job is to pair off nearby
+ * anyons before the automaton (the paper's decoder, unchanged) finishes every
+ * shot, so the automaton stays both the fallback and the judge.
+ *
+ * The net: four 3x3 convolutions with circular (periodic) padding,
+ * 2 -> 32 -> 32 -> 32 -> 4 channels, ReLU between layers.  Input channel 0 is
+ * the anyon indicator (sigma_r = -1), channel 1 is constant 1.  Output channel
+ * k is the logit of a move in direction k: 0 = +x, 1 = -x, 2 = +y, 3 = -y
+ * (the fifth class "no move" has logit 0).  Parameters: fp32, flat, per layer
+ * W[c_out][c_in][3][3] (tap (ky, kx) reads site (x + kx - 1, y + ky - 1))
+ * followed by b[c_out]; qca_net_param_count() floats in all.
+ *
+ * Inference rounds the weights and each layer's input to bfloat16 (round to
+ * nearest even) and accumulates in fp32 (tensor cores for layers 2-4); logits
+ * are fp32.  Pairing: an anyon proposes direction argmax_k z_k if that logit
+ * is > 0 (first index on ties), else nothing; the link <r, r + a^> joins the
+ * pre-decoder correction C0 iff r proposes +a and r + a^ proposes -a.
+ *
+ * Labels (training targets) come from the automaton's own first step: with all
+ * fields empty, v = 3 sub-steps and the forces of Eqs. blahdef / degbreak give
+ * each anyon a move direction (or none); an anyon is labelled with its
+ * direction when the anyon next to it in that direction moves back toward it
+ * (the pair annihilates in that step), else 4 ("no move"); non-anyon sites
+ * are 255 (ignored).
+ *
+ * A qca_net_t handle belongs to the device that was current when it was
+ * created; calls on one handle must not overlap (no internal locking).
+ * ------------------------------------------------------------------------- */
+typedef struct qca_net_s* qca_net_t;
+
+/* Number of fp32 parameters of the net. */
+int64_t qca_net_param_count(void);
+
+/* Create a net with He-normal weights drawn from splitmix64(seed ...) and zero
+ * biases; *out receives the handle.  Allocates a few hundred KB of device
+ * memory on the current device. */
+int qca_net_create(uint64_t seed, qca_net_t* out);
+
+/* Free the handle and its device memory (NULL is accepted). */
+int qca_net_destroy(qca_net_t net);
+
+/* Copy the fp32 parameters to / from HOST memory; count must equal
+ * qca_net_param_count().  Synchronous. */
+int qca_net_get_params(qca_net_t net, float* host_params, int64_t count);
+int qca_net_set_params(qca_net_t net, const float* host_params, int64_t count);
+
+/* Train on freshly drawn syndromes: `iterations` Adam steps (betas 0.9 /
+ * 0.999, epsilon 1e-8, learning rate lr), each on `batch` L x L tori whose
+ * links flip i.i.d. with a per-torus probability drawn uniformly from
+ * [p_lo, p_hi) (splitmix64 counter stream of `seed`; the stream position
+ * advances across calls on the same handle).  Loss: mean softmax
+ * cross-entropy over the anyon sites against the first-step labels above,
+ * smoothed by 0.1 (that mass spread evenly over the five classes).
+ * Forward and backward run in fp32 on the device.  out_losses (HOST, may be
+ * NULL) receives one loss per iteration.  4 <= L <= 128, batch * L * L <=
+ * 2^24.  Allocates its buffers for the duration of the call; synchronous. */
+int qca_net_train(qca_net_t net, int L, int64_t iterations, int batch, double p_lo, double p_hi,
+                  uint64_t seed, float lr, float* out_losses);
+
+/* First-step labels of noise realisations: noise uint8 [shots][2][L][L],
+ * out_labels uint8 [shots][L][L] (values as above), scratch >= 2 * shots * L^2
+ * bytes of device memory.  4 <= L <= QCA_MAX_L. */
+int qca_net_labels_async(const uint8_t* noise, int L, int64_t shots, uint8_t* out_labels,
+                         uint8_t* scratch, void* stream);
+
+/* Logits of the net: out_logits fp32 [shots][4][L][L].  The handle keeps an
+ * inference workspace (about 130 bytes per site of up to 4 GiB worth of
+ * shots) that grows on demand; growth synchronises the device, so make one
+ * call of the largest size before capturing a stream. */
+int qca_net_logits_async(qca_net_t net, const uint8_t* noise, int L, int64_t shots,
+                         float* out_logits, void* stream);
+
+/* Pre-decode: out_residual uint8 [shots][2][L][L] = N xor C0 and, if out_c0
+ * is not NULL, out_c0 = C0 (same layout). */
+int qca_net_predecode_async(qca_net_t net, const uint8_t* noise, int L, int64_t shots,
+                            uint8_t* out_residual, uint8_t* out_c0, void* stream);
+
+/* Net + automaton: pre-decode, run qca_decode_batch_async on the residual
+ * N xor C0 (arguments as there), then out_correction = C0 xor C_automaton.
+ * out_steps counts the automaton's steps; out_logical_fail is the failure
+ * flag of N xor C (the automaton's flag on the residual).  residual_scratch
+ * is caller-owned device memory of 2 * shots * L^2 bytes. */
+int qca_net_decode_batch_async(qca_net_t net, const uint8_t* noise, int L, int64_t shots,
+                               int max_steps, uint64_t rng_seed, uint8_t* out_correction,
+                               int32_t* out_steps, uint8_t* out_logical_fail,
+                               const qca_config* cfg, uint8_t* residual_scratch, void* stream);
+
 /* Kernel path chosen for a lattice size: 1 = on-chip fast sweep, 2 = on-chip
  * sweep on a 2-CTA cluster, 0 = generic sweep with HBM-resident state.
  * Returns a negative code for an unsupported L. */

@@ -1,0 +1,129 @@
+"""CPU reference of the learned pre-decoder (TEST INFRASTRUCTURE ONLY).
+
+The pre-decoder is not part of the paper: it is a small convolutional net that
+proposes, for every anyon, a move toward an adjacent anyon; links whose two end
+anyons propose each other are flipped before the paper's automaton finishes
+the shot.  Its labels come from the automaton itself: the direction an anyon
+takes in the automaton's first step (Def. "D-dimensional message passing
+automaton", Eqs. blahdef, degbreak, ddfeedback, readings R1-R4), kept when the
+anyon it moves toward moves back, i.e. when the first step annihilates the pair.
+
+Only the tests may import this module.  It uses numpy in float64; the
+quantisation points of the GPU kernels (bf16 weights; bf16 activations at layer
+boundaries) are applied explicitly so that the two sides compute the same
+arithmetic up to accumulation order and precision.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+# layer shapes (c_out, c_in) of the 3x3 circular convolutions
+LAYERS = [(32, 2), (32, 32), (32, 32), (4, 32)]
+# logit channel k <-> move direction (code k + 1): +x, -x, +y, -y
+DIRS = [(1, 0), (-1, 0), (0, 1), (0, -1)]
+
+
+def param_count() -> int:
+    return sum(co * ci * 9 + co for co, ci in LAYERS)
+
+
+def unpack(params: np.ndarray):
+    """Flat float32 parameters -> [(W[co][ci][3][3], b[co]), ...]."""
+    out, o = [], 0
+    for co, ci in LAYERS:
+        W = params[o:o + co * ci * 9].reshape(co, ci, 3, 3)
+        o += co * ci * 9
+        b = params[o:o + co]
+        o += co
+        out.append((W.astype(np.float64), b.astype(np.float64)))
+    assert o == len(params)
+    return out
+
+
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """Round to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = ((u + 0x7FFF + lsb) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def conv3x3_circular(x: np.ndarray, W: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """x [ci][L][L], W [co][ci][3][3] (tap (ky, kx) <-> offset (ky-1, kx-1)):
+    out[co][y][x] = b[co] + sum W[co][ci][ky][kx] x[ci][y+ky-1][x+kx-1] (periodic)."""
+    co = W.shape[0]
+    L = x.shape[-1]
+    out = np.zeros((co, L, L), dtype=np.float64)
+    for ky in range(3):
+        for kx in range(3):
+            # shifted[ci][y][x] = x[ci][y + ky - 1][x + kx - 1]
+            shifted = np.roll(x, shift=(1 - ky, 1 - kx), axis=(1, 2))
+            out += np.einsum("oc,cyx->oyx", W[:, :, ky, kx], shifted)
+    return out + b[:, None, None]
+
+
+def forward(anyon: np.ndarray, params: np.ndarray, quantize: bool = True) -> np.ndarray:
+    """Logits [4][L][L] of one syndrome (anyon indicator [L][L])."""
+    layers = unpack(params)
+    x = np.stack([anyon.astype(np.float64), np.ones_like(anyon, dtype=np.float64)])
+    for i, (W, b) in enumerate(layers):
+        if quantize:
+            W = bf16_round(W)
+            x = bf16_round(x)
+        x = conv3x3_circular(x, W, b)
+        if i < len(layers) - 1:
+            x = np.maximum(x, 0.0)
+    return x
+
+
+def first_step_labels(anyon: np.ndarray) -> np.ndarray:
+    """Per site: 255 (no anyon), 4 (anyon not in a first-step annihilating
+    adjacent pair) or k in 0..3 (direction DIRS[k] toward its partner)."""
+    L = anyon.shape[0]
+    sigma = np.where(anyon, -1, 1).astype(np.int8)
+    m = np.zeros((4, L, L), np.int32)
+    for _ in range(3):
+        m = oracle.message_substep(sigma, m)
+    f = oracle.forces(sigma, m)
+    # direction code per anyon: f^x = -1 -> +x, +1 -> -x; same for y
+    d = np.full((L, L), -1, np.int32)
+    d[f[0] == -1] = 0
+    d[f[0] == 1] = 1
+    d[f[1] == -1] = 2
+    d[f[1] == 1] = 3
+    lab = np.full((L, L), 255, np.uint8)
+    for y in range(L):
+        for x in range(L):
+            if not anyon[y, x]:
+                continue
+            k = d[y, x]
+            lab[y, x] = 4
+            if k < 0:
+                continue
+            dx, dy = DIRS[k]
+            xn, yn = (x + dx) % L, (y + dy) % L
+            back = {0: 1, 1: 0, 2: 3, 3: 2}[k]
+            if anyon[yn, xn] and d[yn, xn] == back:
+                lab[y, x] = k
+    return lab
+
+
+def proposals(anyon: np.ndarray, logits: np.ndarray) -> np.ndarray:
+    """Per anyon: argmax of the four logits if positive, else 4 (no proposal)."""
+    k = np.argmax(logits, axis=0)
+    best = np.max(logits, axis=0)
+    prop = np.where(best > 0.0, k, 4).astype(np.int32)
+    return np.where(anyon.astype(bool), prop, 4)
+
+
+def pairing_links(anyon: np.ndarray, prop: np.ndarray) -> np.ndarray:
+    """Links [2][L][L] flipped by the pre-decoder: e_x(r) iff r proposes +x and
+    r + x^ proposes -x; e_y(r) likewise with +y / -y."""
+    L = anyon.shape[0]
+    C0 = np.zeros((2, L, L), np.uint8)
+    C0[0] = ((prop == 0) & (np.roll(prop, -1, axis=1) == 1)).astype(np.uint8)
+    C0[1] = ((prop == 2) & (np.roll(prop, -1, axis=0) == 3)).astype(np.uint8)
+    return C0

@@ -80,6 +80,18 @@ def lib():
             "qca_sample_errors_uneven_async": ([vp, vp, vp, i64, u64, vp, vp], i32),
             "qca_decode_uneven_async": ([vp, vp, i32, u64, vp, vp, vp, cfgp, vp], i32),
             "qca_kernel_path": ([i32, cfgp], i32),
+            "qca_net_param_count": ([], i64),
+            "qca_net_create": ([u64, ctypes.POINTER(vp)], i32),
+            "qca_net_destroy": ([vp], i32),
+            "qca_net_get_params": ([vp, vp, i64], i32),
+            "qca_net_set_params": ([vp, vp, i64], i32),
+            "qca_net_train": ([vp, i32, i64, i32, ctypes.c_double, ctypes.c_double, u64,
+                               ctypes.c_float, vp], i32),
+            "qca_net_labels_async": ([vp, i32, i64, vp, vp, vp], i32),
+            "qca_net_logits_async": ([vp, vp, i32, i64, vp, vp], i32),
+            "qca_net_predecode_async": ([vp, vp, i32, i64, vp, vp, vp], i32),
+            "qca_net_decode_batch_async": ([vp, vp, i32, i64, i32, u64, vp, vp, vp, cfgp, vp,
+                                            vp], i32),
             "qca_free_workspace": ([], i32),
         }
         for name, (args, res) in sig.items():
@@ -338,6 +350,115 @@ class UnevenPlan:
             self.handle, ctypes.c_void_p(errors.data_ptr()), max_steps, rng_seed & (2**64 - 1),
             ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(steps.data_ptr()),
             ctypes.c_void_p(fail.data_ptr()), ctypes.byref(cfg), _stream(torch, stream)))
+        return C, steps, fail
+
+
+def net_labels(errors, stream=None):
+    """First-step labels (uint8 [shots][L][L]: 0..3 direction, 4 none, 255 no anyon)."""
+    torch = _torch()
+    shots, L = errors.shape[0], errors.shape[-1]
+    _dev_u8(torch, errors, (shots, 2, L, L), "errors")
+    out = torch.empty((shots, L, L), dtype=torch.uint8, device=errors.device)
+    scratch = torch.empty(2 * shots * L * L, dtype=torch.uint8, device=errors.device)
+    _check(lib().qca_net_labels_async(ctypes.c_void_p(errors.data_ptr()), L, shots,
+                                      ctypes.c_void_p(out.data_ptr()),
+                                      ctypes.c_void_p(scratch.data_ptr()), _stream(torch, stream)))
+    torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    return out
+
+
+class Net:
+    """Learned pre-decoder handle (qca_net_*): 3x3 circular conv net
+    2 -> 32 -> 32 -> 32 -> 4 proposing moves that pair adjacent anyons."""
+
+    def __init__(self, seed: int = 0):
+        _torch()
+        h = ctypes.c_void_p()
+        _check(lib().qca_net_create(seed & (2**64 - 1), ctypes.byref(h)))
+        self.handle = h
+
+    @staticmethod
+    def param_count() -> int:
+        return int(lib().qca_net_param_count())
+
+    def close(self):
+        if self.handle:
+            lib().qca_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        import numpy as np
+        out = np.zeros(self.param_count(), dtype=np.float32)
+        _check(lib().qca_net_get_params(self.handle, out.ctypes.data_as(ctypes.c_void_p),
+                                        out.size))
+        return out
+
+    def set_params(self, params):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().qca_net_set_params(self.handle, a.ctypes.data_as(ctypes.c_void_p), a.size))
+
+    def train(self, L: int, iterations: int, batch: int, p_lo: float, p_hi: float,
+              seed: int = 1, lr: float = 1e-3):
+        """Adam steps on fresh automaton-labelled syndromes; returns the losses."""
+        import numpy as np
+        losses = np.zeros(max(iterations, 1), dtype=np.float32)
+        _check(lib().qca_net_train(self.handle, L, iterations, batch, float(p_lo), float(p_hi),
+                                   seed & (2**64 - 1), float(lr),
+                                   losses.ctypes.data_as(ctypes.c_void_p)))
+        return losses[:iterations]
+
+    def logits(self, errors, stream=None):
+        """fp32 [shots][4][L][L] logits of the noise realisations' syndromes."""
+        torch = _torch()
+        shots, L = errors.shape[0], errors.shape[-1]
+        _dev_u8(torch, errors, (shots, 2, L, L), "errors")
+        out = torch.empty((shots, 4, L, L), dtype=torch.float32, device=errors.device)
+        _check(lib().qca_net_logits_async(self.handle, ctypes.c_void_p(errors.data_ptr()), L,
+                                          shots, ctypes.c_void_p(out.data_ptr()),
+                                          _stream(torch, stream)))
+        return out
+
+    def predecode(self, errors, stream=None):
+        """(residual N xor C0, C0), both uint8 [shots][2][L][L]."""
+        torch = _torch()
+        shots, L = errors.shape[0], errors.shape[-1]
+        _dev_u8(torch, errors, (shots, 2, L, L), "errors")
+        R = torch.empty_like(errors)
+        C0 = torch.empty_like(errors)
+        _check(lib().qca_net_predecode_async(self.handle, ctypes.c_void_p(errors.data_ptr()), L,
+                                             shots, ctypes.c_void_p(R.data_ptr()),
+                                             ctypes.c_void_p(C0.data_ptr()),
+                                             _stream(torch, stream)))
+        return R, C0
+
+    def decode_batch(self, errors, max_steps: int = 4096, rng_seed: int = 0, *, v: int = 3,
+                     m_max: int = 255, p_move: float = 0.0, shot_offset: int = 0, out=None,
+                     scratch=None, stream=None):
+        """Net + automaton: (correction, automaton steps, logical_fail)."""
+        torch = _torch()
+        shots, L = errors.shape[0], errors.shape[-1]
+        _dev_u8(torch, errors, (shots, 2, L, L), "errors")
+        if out is None:
+            C = torch.empty_like(errors)
+            steps = torch.empty(shots, dtype=torch.int32, device=errors.device)
+            fail = torch.empty(shots, dtype=torch.uint8, device=errors.device)
+        else:
+            C, steps, fail = out
+        if scratch is None:
+            scratch = torch.empty_like(errors)
+        cfg = make_config(v, m_max, p_move, shot_offset)
+        _check(lib().qca_net_decode_batch_async(
+            self.handle, ctypes.c_void_p(errors.data_ptr()), L, shots, max_steps,
+            rng_seed & (2**64 - 1), ctypes.c_void_p(C.data_ptr()),
+            ctypes.c_void_p(steps.data_ptr()), ctypes.c_void_p(fail.data_ptr()),
+            ctypes.byref(cfg), ctypes.c_void_p(scratch.data_ptr()), _stream(torch, stream)))
         return C, steps, fail
 
 

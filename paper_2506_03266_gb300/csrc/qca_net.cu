@@ -1,0 +1,945 @@
+// Learned local pre-decoder (not part of the paper) in front of the exact
+// automaton.  A 4-layer 3x3 convolutional net with circular padding
+// (2 -> 32 -> 32 -> 32 -> 4 channels, ReLU between layers) reads the anyon
+// indicator and a constant channel and gives every site four logits, one per
+// move direction (+x, -x, +y, -y).  An anyon proposes the direction of its
+// largest logit when that logit is positive; a link whose two end anyons
+// propose each other is flipped (the pair annihilates).  The automaton then
+// decodes the residual N xor C0; the final correction is C0 xor C_automaton and
+// the failure flag is the automaton's on the residual (N xor C0 xor C_automaton
+// = N xor C).
+//
+// Training labels come from the automaton itself: the direction an anyon moves
+// in the automaton's first step (all fields empty before it, so the fields are
+// the cone distances <= 3), kept when its neighbour in that direction moves
+// back (the pair annihilates in that step); other anyons get label 4 (none).
+//
+// Inference: layer 1 on CUDA cores (2 input channels), layers 2-4 as
+// implicit-GEMM convolutions on the tensor cores (mma.sync m16n8k16, bf16
+// operands, fp32 accumulation), activations bf16 in NHWC layout.
+// Training: fp32 kernels on the CUDA cores (forward, softmax cross-entropy,
+// backward data/weights, Adam).
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "qca_internal.cuh"
+
+namespace qca {
+
+namespace {
+
+// ---- parameter layout: per layer W[co][ci][3][3] then b[co], fp32
+constexpr int kLayers = 4;
+constexpr int kCo[kLayers] = {32, 32, 32, 4};
+constexpr int kCi[kLayers] = {2, 32, 32, 32};
+constexpr int kW0 = 0, kB0 = kW0 + 32 * 2 * 9;
+constexpr int kW1 = kB0 + 32, kB1 = kW1 + 32 * 32 * 9;
+constexpr int kW2 = kB1 + 32, kB2 = kW2 + 32 * 32 * 9;
+constexpr int kW3 = kB2 + 32, kB3 = kW3 + 4 * 32 * 9;
+constexpr int kParams = kB3 + 4;
+constexpr int kWoff[kLayers] = {kW0, kW1, kW2, kW3};
+
+constexpr uint64_t kTagTrain = 0x545241494EULL;  // "TRAIN"
+
+__device__ __forceinline__ int wrapL(int i, int L) { return i < 0 ? i + L : (i >= L ? i - L : i); }
+
+// ---------------------------------------------------------------- labels --
+
+// sigma (1 = anyon) from noise [2][L][L] for every shot, byte per site
+__global__ void syndrome_kernel(const uint8_t* __restrict__ N, int L, int64_t shots,
+                                uint8_t* __restrict__ sig) {
+  const int64_t LL = (int64_t)L * L;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < shots * LL;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / LL;
+    const int r = (int)(i - s * LL), x = r % L, y = r / L;
+    const uint8_t* n = N + s * 2 * LL;
+    sig[i] = n[r] ^ n[y * L + wrapL(x - 1, L)] ^ n[LL + r] ^ n[LL + wrapL(y - 1, L) * L + x];
+  }
+}
+
+// First-step direction of every anyon (0 +x, 1 -x, 2 +y, 3 -y, 4 none; 255 no
+// anyon).  With empty fields, three applications of A^(D) leave in m^{s a}_r
+// the smallest d <= 3 with an anyon on {r - s d a^ + j b^, |j| <= d}; the
+// forces follow readings R1-R4 (smallest field, ties (-,y) < (-,x) < (+,x) <
+// (+,y), no move on a balanced axis).
+__global__ void first_dir_kernel(const uint8_t* __restrict__ sig, int L, int64_t shots,
+                                 uint8_t* __restrict__ dir) {
+  const int64_t LL = (int64_t)L * L;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < shots * LL;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / LL;
+    const int r = (int)(i - s * LL), x = r % L, y = r / L;
+    const uint8_t* g = sig + s * LL;
+    if (!g[r]) {
+      dir[i] = 255;
+      continue;
+    }
+    int m[4];  // (+,x) (-,x) (+,y) (-,y); 0 = none
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const int sgn = (f % 2 == 0) ? 1 : -1;
+      const bool ax = f < 2;
+      int best = 0;
+      for (int d = 1; d <= 3 && !best; ++d) {
+        for (int j = -d; j <= d; ++j) {
+          const int xx = ax ? wrapL(x - sgn * d, L) : wrapL(x + j, L);
+          const int yy = ax ? wrapL(y + j, L) : wrapL(y - sgn * d, L);
+          if (g[yy * L + xx]) {
+            best = d;
+            break;
+          }
+        }
+      }
+      m[f] = best;
+    }
+    const int val[4] = {m[3], m[1], m[0], m[2]};  // preference order (-,y) (-,x) (+,x) (+,y)
+    int bi = -1, bv = 0;
+    for (int k = 0; k < 4; ++k)
+      if (val[k] > 0 && (bi < 0 || val[k] < bv)) {
+        bi = k;
+        bv = val[k];
+      }
+    int code = 4;
+    if (bi >= 0) {
+      const bool yaxis = (bi == 0 || bi == 3);
+      const int mp = yaxis ? m[2] : m[0], mm = yaxis ? m[3] : m[1];
+      const unsigned up = mp ? (unsigned)mp : 0xFFu, um = mm ? (unsigned)mm : 0xFFu;
+      if (up != um) code = (up < um) ? (yaxis ? 3 : 1) : (yaxis ? 2 : 0);
+    }
+    dir[i] = (uint8_t)code;
+  }
+}
+
+// label = direction if the neighbour in that direction moves back, else 4
+__global__ void mutual_label_kernel(const uint8_t* __restrict__ dir, int L, int64_t shots,
+                                    uint8_t* __restrict__ lab) {
+  const int64_t LL = (int64_t)L * L;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < shots * LL;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / LL;
+    const int r = (int)(i - s * LL), x = r % L, y = r / L;
+    const int d = dir[i];
+    if (d == 255) {
+      lab[i] = 255;
+      continue;
+    }
+    int out = 4;
+    if (d < 4) {
+      const int dx = (d == 0) ? 1 : (d == 1 ? -1 : 0), dy = (d == 2) ? 1 : (d == 3 ? -1 : 0);
+      const int nb = wrapL(y + dy, L) * L + wrapL(x + dx, L);
+      const int back = d ^ 1;
+      if (dir[s * LL + nb] == back) out = d;
+    }
+    lab[i] = (uint8_t)out;
+  }
+}
+
+// ------------------------------------------------------- training (fp32) --
+
+// Random training syndromes: shot b of batch `it` uses global index
+// it * B + b; p ~ U[p_lo, p_hi) per shot; links drawn like qca_sample_errors.
+__global__ void train_sample_kernel(int L, int B, int64_t it, uint64_t seed, uint64_t t_lo,
+                                    uint64_t t_span, uint8_t* __restrict__ sig) {
+  const int LL = L * L;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B * LL; i += gridDim.x * blockDim.x) {
+    const int b = i / LL, r = i - b * LL, x = r % L, y = r / L;
+    const uint64_t shot = (uint64_t)it * B + b;
+    const uint64_t ks = splitmix64(splitmix64(seed ^ kTagTrain) ^ shot);
+    const uint64_t thr = t_lo + (uint64_t)(((unsigned __int128)splitmix64(ks ^ 0x5052ULL) * t_span) >> 64);
+    auto link = [&](int xx, int yy, int dirb) -> uint8_t {
+      const uint64_t e = 2 * ((uint64_t)yy * L + xx) + dirb;
+      return splitmix64(ks ^ e) < thr ? 1 : 0;
+    };
+    sig[i] = link(x, y, 0) ^ link(wrapL(x - 1, L), y, 0) ^ link(x, y, 1) ^ link(x, wrapL(y - 1, L), 1);
+  }
+}
+
+// input layer activations: channel 0 = anyon, channel 1 = 1 (fp32 NCHW)
+__global__ void input_f32_kernel(const uint8_t* __restrict__ sig, int L, int B,
+                                 float* __restrict__ x) {
+  const int LL = L * L;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B * LL; i += gridDim.x * blockDim.x) {
+    const int b = i / LL, r = i - b * LL;
+    x[(size_t)b * 2 * LL + r] = sig[i] ? 1.f : 0.f;
+    x[(size_t)b * 2 * LL + LL + r] = 1.f;
+  }
+}
+
+// out[b][co][y][x] = bias[co] + sum W[co][ci][ky][kx] in[b][ci][y+ky-1][x+kx-1]
+template <int CI, int CO, bool RELU>
+__global__ void conv_fwd_f32(const float* __restrict__ in, const float* __restrict__ W,
+                             const float* __restrict__ bias, int L, int B,
+                             float* __restrict__ out) {
+  __shared__ float sW[CO * CI * 9];
+  __shared__ float sb[CO];
+  for (int i = threadIdx.x; i < CO * CI * 9; i += blockDim.x) sW[i] = W[i];
+  for (int i = threadIdx.x; i < CO; i += blockDim.x) sb[i] = bias[i];
+  __syncthreads();
+  const int LL = L * L;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B * LL; i += gridDim.x * blockDim.x) {
+    const int b = i / LL, r = i - b * LL, x = r % L, y = r / L;
+    float acc[CO];
+#pragma unroll
+    for (int co = 0; co < CO; ++co) acc[co] = sb[co];
+    const float* ib = in + (size_t)b * CI * LL;
+    for (int ky = 0; ky < 3; ++ky)
+      for (int kx = 0; kx < 3; ++kx) {
+        const int nb = wrapL(y + ky - 1, L) * L + wrapL(x + kx - 1, L);
+        for (int ci = 0; ci < CI; ++ci) {
+          const float v = ib[(size_t)ci * LL + nb];
+#pragma unroll
+          for (int co = 0; co < CO; ++co) acc[co] += sW[((co * CI + ci) * 3 + ky) * 3 + kx] * v;
+        }
+      }
+    float* ob = out + (size_t)b * CO * LL;
+#pragma unroll
+    for (int co = 0; co < CO; ++co) ob[(size_t)co * LL + r] = RELU ? fmaxf(acc[co], 0.f) : acc[co];
+  }
+}
+
+__global__ void count_labelled_kernel(const uint8_t* __restrict__ lab, int n,
+                                      unsigned int* __restrict__ count) {
+  unsigned int c = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    c += lab[i] != 255;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+// Label smoothing of the training target: eps spread evenly over the five
+// classes.  It bounds the logits the loss drives toward (target margin
+// log((1 - eps + eps/5) / (eps/5)), about 3.8 at eps = 0.1), which keeps the
+// activations, and so the size of one bf16 rounding step in them, small.
+constexpr float kLabelSmoothing = 0.1f;
+
+// Softmax over (z0..z3, 0) at labelled sites, the fifth class ("no move")
+// with its logit fixed at 0; target q = smoothed one-hot of the label;
+// dz = (p - q) / n_labelled, loss = mean cross-entropy -sum q log p.
+__global__ void loss_grad_kernel(const float* __restrict__ z, const uint8_t* __restrict__ lab,
+                                 int L, int B, const unsigned int* __restrict__ count,
+                                 float* __restrict__ dz, float* __restrict__ loss) {
+  const int LL = L * L;
+  const float inv_n = 1.f / (float)(*count > 0 ? *count : 1u);
+  const float q_off = kLabelSmoothing / 5.f, q_on = 1.f - kLabelSmoothing + q_off;
+  float local = 0.f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B * LL; i += gridDim.x * blockDim.x) {
+    const int b = i / LL, r = i - b * LL;
+    const float* zb = z + (size_t)b * 4 * LL;
+    float* db = dz + (size_t)b * 4 * LL;
+    const int t = lab[i];
+    if (t == 255) {
+      for (int k = 0; k < 4; ++k) db[(size_t)k * LL + r] = 0.f;
+      continue;
+    }
+    float v[5] = {zb[r], zb[LL + r], zb[2 * LL + r], zb[3 * LL + r], 0.f};
+    float mx = v[0];
+    for (int k = 1; k < 5; ++k) mx = fmaxf(mx, v[k]);
+    float sum = 0.f;
+    for (int k = 0; k < 5; ++k) sum += expf(v[k] - mx);
+    const float lse = mx + logf(sum);
+    for (int k = 0; k < 5; ++k) {
+      const float q = (t == k) ? q_on : q_off;
+      const float pk = expf(v[k] - lse);
+      if (k < 4) db[(size_t)k * LL + r] = (pk - q) * inv_n;
+      local += q * (lse - v[k]);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xFFFFFFFFu, local, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, local * inv_n);
+}
+
+// din[b][ci][y][x] = sum W[co][ci][ky][kx] dout[b][co][y-ky+1][x-kx+1], times the
+// ReLU mask of the forward input (act > 0) when MASK
+template <int CI, int CO, bool MASK>
+__global__ void conv_bwd_data_f32(const float* __restrict__ dout, const float* __restrict__ W,
+                                  const float* __restrict__ act, int L, int B,
+                                  float* __restrict__ din) {
+  __shared__ float sW[CO * CI * 9];
+  for (int i = threadIdx.x; i < CO * CI * 9; i += blockDim.x) sW[i] = W[i];
+  __syncthreads();
+  const int LL = L * L;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B * LL; i += gridDim.x * blockDim.x) {
+    const int b = i / LL, r = i - b * LL, x = r % L, y = r / L;
+    float acc[CI];
+#pragma unroll
+    for (int ci = 0; ci < CI; ++ci) acc[ci] = 0.f;
+    const float* db = dout + (size_t)b * CO * LL;
+    for (int ky = 0; ky < 3; ++ky)
+      for (int kx = 0; kx < 3; ++kx) {
+        const int nb = wrapL(y - ky + 1, L) * L + wrapL(x - kx + 1, L);
+        for (int co = 0; co < CO; ++co) {
+          const float g = db[(size_t)co * LL + nb];
+#pragma unroll
+          for (int ci = 0; ci < CI; ++ci) acc[ci] += sW[((co * CI + ci) * 3 + ky) * 3 + kx] * g;
+        }
+      }
+    float* ob = din + (size_t)b * CI * LL;
+    const float* ab = act + (size_t)b * CI * LL;
+#pragma unroll
+    for (int ci = 0; ci < CI; ++ci)
+      ob[(size_t)ci * LL + r] = (MASK && ab[(size_t)ci * LL + r] <= 0.f) ? 0.f : acc[ci];
+  }
+}
+
+// dW[co][ci][ky][kx] += sum_sites dout[co][s] in[ci][s + (ky-1, kx-1)], db[co] += sum dout
+// One CTA per chunk of sites; thread t owns entries t, t + blockDim, ...
+template <int CI, int CO>
+__global__ void conv_bwd_weight_f32(const float* __restrict__ in, const float* __restrict__ dout,
+                                    int L, int B, int chunk, float* __restrict__ dW,
+                                    float* __restrict__ dbias) {
+  constexpr int NE = CO * CI * 9;
+  constexpr int T = 32;  // sites staged per round (rows padded to T + 1 words)
+  __shared__ float sin[9][CI][T + 1];
+  __shared__ float sd[CO][T + 1];
+  const int LL = L * L, total = B * LL;
+  const int s0 = blockIdx.x * chunk, s1 = min(total, s0 + chunk);
+  constexpr int PER = (NE + 255) / 256;
+  float acc[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) acc[k] = 0.f;
+  float accb = 0.f;
+  for (int base = s0; base < s1; base += T) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < T * (CO + 9 * CI); idx += blockDim.x) {
+      const int t = idx % T, q = idx / T;
+      const int s = base + t;
+      float v = 0.f;
+      if (s < s1) {
+        const int b = s / LL, r = s - b * LL, x = r % L, y = r / L;
+        if (q < CO) {
+          v = dout[((size_t)b * CO + q) * LL + r];
+        } else {
+          const int qq = q - CO, tap = qq / CI, ci = qq - tap * CI;
+          const int nb = wrapL(y + tap / 3 - 1, L) * L + wrapL(x + tap % 3 - 1, L);
+          v = in[((size_t)b * CI + ci) * LL + nb];
+        }
+      }
+      if (q < CO)
+        sd[q][t] = v;
+      else
+        sin[(q - CO) / CI][(q - CO) % CI][t] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int e = threadIdx.x + k * 256;
+      if (e >= NE) break;
+      const int co = e / (CI * 9), rem = e - co * CI * 9, ci = rem / 9, tap = rem - ci * 9;
+      float a = 0.f;
+#pragma unroll 8
+      for (int t = 0; t < T; ++t) a += sd[co][t] * sin[tap][ci][t];
+      acc[k] += a;
+    }
+    if (threadIdx.x < CO)
+      for (int t = 0; t < T; ++t) accb += sd[threadIdx.x][t];
+  }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int e = threadIdx.x + k * 256;
+    if (e < NE) atomicAdd(&dW[e], acc[k]);
+  }
+  if (threadIdx.x < CO) atomicAdd(&dbias[threadIdx.x], accb);
+}
+
+// Adam (Kingma & Ba, ICLR 2015) with bias corrections c1 = 1 / (1 - b1^t),
+// c2 = 1 / (1 - b2^t) computed on the host; epsilon 1e-8.
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g,
+                            float* __restrict__ m1, float* __restrict__ m2, int n, float lr,
+                            float b1, float b2, float c1, float c2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float a = b1 * m1[i] + (1.f - b1) * gi;
+    const float b = b2 * m2[i] + (1.f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = b;
+    p[i] -= lr * (a * c1) / (sqrtf(b * c2) + 1e-8f);
+  }
+}
+
+// ---------------------------------------------------- inference (bf16) ----
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// bf16 weights of layers 2..4 as [tap][co][ci] (co padded to 8 for layer 4),
+// layer 1 fp32 [co][ci][tap], biases fp32; built from the fp32 parameters.
+__global__ void prepare_weights_kernel(const float* __restrict__ P, __nv_bfloat16* __restrict__ Wb,
+                                       float* __restrict__ W1) {
+  const int n23 = 9 * 32 * 32, n4 = 9 * 8 * 32;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n23 + n4 + 32 * 2 * 9;
+       i += gridDim.x * blockDim.x) {
+    if (i < 2 * n23) {
+      const int l = i / n23, j = i - l * n23;  // layers 2, 3
+      const int tap = j / (32 * 32), co = (j / 32) % 32, ci = j % 32;
+      const int off = (l == 0) ? kW1 : kW2;
+      Wb[i] = __float2bfloat16_rn(P[off + (co * 32 + ci) * 9 + tap]);
+    } else if (i < 2 * n23 + n4) {
+      const int j = i - 2 * n23, tap = j / (8 * 32), co = (j / 32) % 8, ci = j % 32;
+      Wb[i] = __float2bfloat16_rn(co < 4 ? P[kW3 + (co * 32 + ci) * 9 + tap] : 0.f);
+    } else {
+      const int j = i - 2 * n23 - n4;  // layer 1, rounded to bf16 like the others
+      W1[j] = __bfloat162float(__float2bfloat16_rn(P[kW0 + j]));
+    }
+  }
+}
+
+// layer 1 (2 -> 32, CUDA cores).  The inputs (anyon, 1) are exact in bf16;
+// the constant channel's nine taps are folded into the bias once per CTA, and
+// each anyon tap adds its weight column.
+__global__ void layer1_kernel(const uint8_t* __restrict__ sig, int L, int64_t shots,
+                              const float* __restrict__ W1, const float* __restrict__ P,
+                              __nv_bfloat16* __restrict__ out) {
+  __shared__ float sW[9][32];  // anyon-channel weights by tap
+  __shared__ float sb[32];     // bias + constant-channel taps
+  for (int i = threadIdx.x; i < 32 * 9; i += blockDim.x) sW[i % 9][i / 9] = W1[(i / 9) * 18 + i % 9];
+  for (int co = threadIdx.x; co < 32; co += blockDim.x) {
+    float b = P[kB0 + co];
+    for (int tap = 0; tap < 9; ++tap) b += W1[co * 18 + 9 + tap];
+    sb[co] = b;
+  }
+  __syncthreads();
+  const int64_t LL = (int64_t)L * L;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < shots * LL;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / LL;
+    const int r = (int)(i - s * LL), x = r % L, y = r / L;
+    const uint8_t* g = sig + s * LL;
+    float acc[32];
+#pragma unroll
+    for (int co = 0; co < 32; ++co) acc[co] = sb[co];
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+      const int nb = wrapL(y + tap / 3 - 1, L) * L + wrapL(x + tap % 3 - 1, L);
+      if (g[nb]) {
+#pragma unroll
+        for (int co = 0; co < 32; ++co) acc[co] += sW[tap][co];
+      }
+    }
+    uint4* o = reinterpret_cast<uint4*>(out + i * 32);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      uint4 w;
+      w.x = pack_bf16(fmaxf(acc[8 * c + 0], 0.f), fmaxf(acc[8 * c + 1], 0.f));
+      w.y = pack_bf16(fmaxf(acc[8 * c + 2], 0.f), fmaxf(acc[8 * c + 3], 0.f));
+      w.z = pack_bf16(fmaxf(acc[8 * c + 4], 0.f), fmaxf(acc[8 * c + 5], 0.f));
+      w.w = pack_bf16(fmaxf(acc[8 * c + 6], 0.f), fmaxf(acc[8 * c + 7], 0.f));
+      o[c] = w;
+    }
+  }
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Implicit-GEMM 3x3 circular convolution, 32 input channels (bf16 NHWC, 64
+// bytes per site), NT n-tiles of 8 output channels.  A warp computes 16
+// consecutive sites (GEMM rows, possibly spanning shots) x 8*NT channels;
+// K = 9 taps x 32 channels in k-steps of 16.  Weights sit in shared memory as
+// [tap][co][ci pair] words with a row pitch of 20 words (conflict-free B
+// fragment reads).  Epilogue by MODE:
+//   kActs:      bias + ReLU, bf16 NHWC activations to `out`;
+//   kLogits:    fp32 logits [shot][4][L][L] (channels < 4) to `logits`;
+//   kProposals: per anyon (sig != 0) the channel of the largest logit if it is
+//               positive, else 4; non-anyons 4; one byte per site to `prop`.
+enum ConvMode { kActs = 0, kLogits = 1, kProposals = 2 };
+constexpr int kWPitch = 20;
+
+template <int NT, int MODE>
+__global__ void __launch_bounds__(128) conv_mma_kernel(
+    const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Wg,
+    const float* __restrict__ bias, int L, int64_t shots, __nv_bfloat16* __restrict__ out,
+    float* __restrict__ logits, const uint8_t* __restrict__ sig, uint8_t* __restrict__ prop) {
+  constexpr int CO = 8 * NT;
+  __shared__ uint32_t sW[9 * CO * kWPitch];
+  __shared__ float sb[CO];
+  for (int i = threadIdx.x; i < 9 * CO * 16; i += blockDim.x)
+    sW[(i / 16) * kWPitch + (i % 16)] = reinterpret_cast<const uint32_t*>(Wg)[i];
+  for (int i = threadIdx.x; i < CO; i += blockDim.x) sb[i] = (MODE == kActs || i < 4) ? bias[i] : 0.f;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int64_t LL = (int64_t)L * L, S = shots * LL;
+  const int64_t tiles = (S + 15) / 16;
+  const uint32_t* inw = reinterpret_cast<const uint32_t*>(in);  // 16 words per site
+  for (int64_t tile = blockIdx.x * 4 + warp; tile < tiles; tile += (int64_t)gridDim.x * 4) {
+    const int64_t s0 = tile * 16;
+    // the two sites this lane feeds (rows g and g + 8 of the tile)
+    int64_t site[2], shot[2];
+    int xs[2], ys[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      site[h] = s0 + g + 8 * h;
+      const int64_t sc = site[h] < S ? site[h] : S - 1;
+      shot[h] = sc / LL;
+      const int r = (int)(sc - shot[h] * LL);
+      xs[h] = r % L;
+      ys[h] = r / L;
+    }
+    float acc[NT][4];
+#pragma unroll
+    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+      int64_t nbw[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        nbw[h] = (shot[h] * LL + wrapL(ys[h] + dy, L) * L + wrapL(xs[h] + dx, L)) * 16;
+#pragma unroll
+      for (int kh = 0; kh < 2; ++kh) {  // input channels 16 kh .. 16 kh + 15
+        uint32_t a[4];
+        a[0] = __ldg(inw + nbw[0] + kh * 8 + t);      // row g,     k = 2t, 2t+1
+        a[1] = __ldg(inw + nbw[1] + kh * 8 + t);      // row g + 8
+        a[2] = __ldg(inw + nbw[0] + kh * 8 + 4 + t);  // row g,     k = 2t+8, 2t+9
+        a[3] = __ldg(inw + nbw[1] + kh * 8 + 4 + t);  // row g + 8
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+          const uint32_t* wr = sW + (tap * CO + n * 8 + g) * kWPitch + kh * 8 + t;
+          mma_bf16(acc[n], a, wr[0], wr[4]);
+        }
+      }
+    }
+    // epilogue: rows g and g + 8, columns 2t and 2t + 1 of every n-tile
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const bool valid = site[h] < S;
+      const int r = ys[h] * L + xs[h];
+      if (MODE == kProposals) {
+        // channels 0,1 sit in lane t = 0, channels 2,3 in lane t = 1 of the group
+        const float v0 = acc[0][2 * h] + sb[2 * t], v1 = acc[0][2 * h + 1] + sb[2 * t + 1];
+        const float w0 = __shfl_down_sync(0xFFFFFFFFu, v0, 1);
+        const float w1 = __shfl_down_sync(0xFFFFFFFFu, v1, 1);
+        if (t == 0 && valid) {
+          const float z[4] = {v0, v1, w0, w1};
+          float best = z[0];
+          int bk = 0;
+#pragma unroll
+          for (int q = 1; q < 4; ++q)
+            if (z[q] > best) {
+              best = z[q];
+              bk = q;
+            }
+          prop[site[h]] = (sig[site[h]] && best > 0.f) ? (uint8_t)bk : (uint8_t)4;
+        }
+        continue;
+      }
+      if (!valid) continue;
+#pragma unroll
+      for (int n = 0; n < NT; ++n) {
+        const int c0 = n * 8 + 2 * t;
+        const float v0 = acc[n][2 * h] + sb[c0], v1 = acc[n][2 * h + 1] + sb[c0 + 1];
+        if (MODE == kLogits) {
+          float* lb = logits + shot[h] * 4 * LL + r;
+          if (c0 < 4) lb[(int64_t)c0 * LL] = v0;
+          if (c0 + 1 < 4) lb[(int64_t)(c0 + 1) * LL] = v1;
+        } else {
+          reinterpret_cast<uint32_t*>(out)[site[h] * 16 + c0 / 2] =
+              pack_bf16(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
+        }
+      }
+    }
+  }
+}
+
+// Links whose two end anyons propose each other: e_x(r) iff prop(r) = +x and
+// prop(r + x^) = -x; e_y likewise.  residual = N xor C0; C0 written if given.
+__global__ void pairing_kernel(const uint8_t* __restrict__ N, const uint8_t* __restrict__ prop,
+                               int L, int64_t shots, uint8_t* __restrict__ resid,
+                               uint8_t* __restrict__ c0) {
+  const int64_t LL = (int64_t)L * L;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < shots * LL;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / LL;
+    const int r = (int)(i - s * LL), x = r % L, y = r / L;
+    const uint8_t* ps = prop + s * LL;
+    const uint8_t fx = (ps[r] == 0 && ps[y * L + wrapL(x + 1, L)] == 1) ? 1 : 0;
+    const uint8_t fy = (ps[r] == 2 && ps[wrapL(y + 1, L) * L + x] == 3) ? 1 : 0;
+    const int64_t e = s * 2 * LL + r;
+    if (c0) {
+      c0[e] = fx;
+      c0[e + LL] = fy;
+    }
+    resid[e] = N[e] ^ fx;
+    resid[e + LL] = N[e + LL] ^ fy;
+  }
+}
+
+// C ^= N ^ R (C0 = N xor R recovered from the noise and the residual)
+__global__ void combine_kernel(uint8_t* __restrict__ C, const uint8_t* __restrict__ N,
+                               const uint8_t* __restrict__ R, int64_t n) {
+  const int64_t n16 = n / 16;
+  const uint4* N4 = reinterpret_cast<const uint4*>(N);
+  const uint4* R4 = reinterpret_cast<const uint4*>(R);
+  uint4* C4 = reinterpret_cast<uint4*>(C);
+  const bool vec = ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(N) |
+                     reinterpret_cast<uintptr_t>(R)) & 15) == 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (vec) {
+    for (int64_t i = i0; i < n16; i += stride) {
+      uint4 c = C4[i];
+      const uint4 a = N4[i], b = R4[i];
+      c.x ^= a.x ^ b.x;
+      c.y ^= a.y ^ b.y;
+      c.z ^= a.z ^ b.z;
+      c.w ^= a.w ^ b.w;
+      C4[i] = c;
+    }
+    i0 += n16 * 16;
+  }
+  for (int64_t i = i0; i < n; i += stride) C[i] ^= N[i] ^ R[i];
+}
+
+int grid_for(int64_t items, int threads) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t b = (items + threads - 1) / threads;
+  const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 32;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+}  // namespace qca
+
+using namespace qca;
+
+struct qca_net_s {
+  int device = 0;
+  float* params = nullptr;         // fp32 [kParams]
+  float* grads = nullptr;          // fp32 [kParams]
+  float* m1 = nullptr;             // Adam first moments [kParams]
+  float* m2 = nullptr;             // Adam second moments [kParams]
+  int64_t adam_t = 0;              // optimiser steps taken
+  int64_t train_shots = 0;         // training syndromes drawn so far
+  __nv_bfloat16* wb = nullptr;     // bf16 weights of layers 2-4, [tap][co][ci]
+  float* w1 = nullptr;             // layer 1 fp32 (bf16-rounded) [co][ci][tap]
+  bool prepared = false;
+  // inference workspace
+  uint8_t* ws = nullptr;
+  size_t ws_bytes = 0;
+};
+
+extern "C" {
+
+int64_t qca_net_param_count(void) { return kParams; }
+
+int qca_net_create(uint64_t seed, qca_net_t* out) {
+  if (!out) {
+    set_error("qca_net_create: NULL output");
+    return QCA_ERR_ARG;
+  }
+  *out = nullptr;
+  // He-normal-like init from the counter generator (Box-Muller), biases 0
+  std::vector<float> h(kParams, 0.f);
+  uint64_t k = splitmix64(seed ^ 0x494E4954ULL);  // "INIT"
+  for (int l = 0; l < kLayers; ++l) {
+    const float sd = sqrtf(2.f / (kCi[l] * 9.f));
+    for (int i = 0; i < kCo[l] * kCi[l] * 9; ++i) {
+      const double u1 = ((splitmix64(k ^ (2 * (uint64_t)i)) >> 11) + 1) * (1.0 / 9007199254740993.0);
+      const double u2 = (splitmix64(k ^ (2 * (uint64_t)i + 1)) >> 11) * (1.0 / 9007199254740992.0);
+      h[kWoff[l] + i] = (float)(sd * sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
+    }
+    k = splitmix64(k);
+  }
+  qca_net_s* n = new qca_net_s();
+  cudaGetDevice(&n->device);
+  cudaError_t e = cudaMalloc(&n->params, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = cudaMalloc(&n->grads, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = cudaMalloc(&n->m1, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = cudaMalloc(&n->m2, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = cudaMalloc(&n->wb, sizeof(__nv_bfloat16) * (2 * 9 * 32 * 32 + 9 * 8 * 32));
+  if (e == cudaSuccess) e = cudaMalloc(&n->w1, sizeof(float) * 32 * 2 * 9);
+  if (e == cudaSuccess) e = cudaMemcpy(n->params, h.data(), sizeof(float) * kParams, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(n->m1, 0, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = cudaMemset(n->m2, 0, sizeof(float) * kParams);
+  if (e != cudaSuccess) {
+    qca_net_destroy(n);
+    return cuda_fail(e, "qca_net_create");
+  }
+  *out = n;
+  return QCA_OK;
+}
+
+int qca_net_destroy(qca_net_t n) {
+  if (!n) return QCA_OK;
+  cudaFree(n->params);
+  cudaFree(n->grads);
+  cudaFree(n->m1);
+  cudaFree(n->m2);
+  cudaFree(n->wb);
+  cudaFree(n->w1);
+  cudaFree(n->ws);
+  delete n;
+  return QCA_OK;
+}
+
+int qca_net_get_params(qca_net_t n, float* host, int64_t count) {
+  if (!n || !host || count != kParams) {
+    set_error("qca_net_get_params: bad arguments (count must be %d)", kParams);
+    return QCA_ERR_ARG;
+  }
+  return cuda_fail(cudaMemcpy(host, n->params, sizeof(float) * kParams, cudaMemcpyDeviceToHost),
+                   "qca_net_get_params");
+}
+
+int qca_net_set_params(qca_net_t n, const float* host, int64_t count) {
+  if (!n || !host || count != kParams) {
+    set_error("qca_net_set_params: bad arguments (count must be %d)", kParams);
+    return QCA_ERR_ARG;
+  }
+  n->prepared = false;
+  return cuda_fail(cudaMemcpy(n->params, host, sizeof(float) * kParams, cudaMemcpyHostToDevice),
+                   "qca_net_set_params");
+}
+
+int qca_net_train(qca_net_t n, int L, int64_t iterations, int batch, double p_lo, double p_hi,
+                  uint64_t seed, float lr, float* out_losses) {
+  if (!n || L < 4 || L > 128 || iterations < 0 || iterations > (1 << 24) || batch < 1 ||
+      (int64_t)batch * L * L > (1 << 24) || !(p_lo >= 0 && p_hi <= 1 && p_lo <= p_hi) ||
+      !(lr > 0.f)) {
+    set_error("qca_net_train: bad arguments");
+    return QCA_ERR_ARG;
+  }
+  if (iterations == 0) return QCA_OK;
+  const int64_t S = (int64_t)batch * L * L;
+  // bytes: sig, dir, lab; floats: x0 (2), a1, a2, a3 (32), z, dz (4), ga, gb (32); per-iteration
+  // loss and labelled-site count
+  uint8_t* bytes = nullptr;
+  float* fl = nullptr;
+  float* losses = nullptr;
+  unsigned int* counts = nullptr;
+  cudaError_t e = cudaMalloc(&bytes, 3 * S);
+  if (e == cudaSuccess) e = cudaMalloc(&fl, sizeof(float) * S * (2 + 32 * 3 + 4 + 4 + 32 * 2));
+  if (e == cudaSuccess) e = cudaMalloc(&losses, sizeof(float) * iterations);
+  if (e == cudaSuccess) e = cudaMalloc(&counts, sizeof(unsigned int) * iterations);
+  if (e == cudaSuccess) e = cudaMemset(losses, 0, sizeof(float) * iterations);
+  if (e == cudaSuccess) e = cudaMemset(counts, 0, sizeof(unsigned int) * iterations);
+  if (e != cudaSuccess) {
+    cudaFree(bytes);
+    cudaFree(fl);
+    cudaFree(losses);
+    cudaFree(counts);
+    return cuda_fail(e, "qca_net_train allocation");
+  }
+  uint8_t *sig = bytes, *dir = bytes + S, *lab = bytes + 2 * S;
+  float* x0 = fl;
+  float* a1 = x0 + 2 * S;
+  float* a2 = a1 + 32 * S;
+  float* a3 = a2 + 32 * S;
+  float* z = a3 + 32 * S;
+  float* dz = z + 4 * S;
+  float* ga = dz + 4 * S;
+  float* gb = ga + 32 * S;
+  auto thr_of = [](double p) -> uint64_t {
+    const double v = ldexp(p, 64);
+    return v >= 18446744073709549568.0 ? ~0ull : (uint64_t)v;
+  };
+  const uint64_t t_lo = thr_of(p_lo), t_span = thr_of(p_hi - p_lo);
+  const int gS = grid_for(S, 256);
+  // weight-gradient CTAs: about two per SM, each over a contiguous run of sites
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t chunk64 = (S + 2 * (int64_t)(sms > 0 ? sms : 1) - 1) / (2 * (int64_t)(sms > 0 ? sms : 1));
+  chunk64 = ((chunk64 + 31) / 32) * 32;
+  const int chunk = (int)(chunk64 < 256 ? 256 : chunk64);
+  const int gW = (int)((S + chunk - 1) / chunk);
+  const float b1 = 0.9f, b2 = 0.999f;
+  int rc = QCA_OK;
+  for (int64_t it = 0; it < iterations; ++it) {
+    train_sample_kernel<<<gS, 256>>>(L, batch, n->train_shots, seed, t_lo, t_span, sig);
+    first_dir_kernel<<<gS, 256>>>(sig, L, batch, dir);
+    mutual_label_kernel<<<gS, 256>>>(dir, L, batch, lab);
+    count_labelled_kernel<<<gS, 256>>>(lab, (int)S, counts + it);
+    input_f32_kernel<<<gS, 256>>>(sig, L, batch, x0);
+    conv_fwd_f32<2, 32, true><<<gS, 256>>>(x0, n->params + kW0, n->params + kB0, L, batch, a1);
+    conv_fwd_f32<32, 32, true><<<gS, 256>>>(a1, n->params + kW1, n->params + kB1, L, batch, a2);
+    conv_fwd_f32<32, 32, true><<<gS, 256>>>(a2, n->params + kW2, n->params + kB2, L, batch, a3);
+    conv_fwd_f32<32, 4, false><<<gS, 256>>>(a3, n->params + kW3, n->params + kB3, L, batch, z);
+    cudaMemsetAsync(n->grads, 0, sizeof(float) * kParams);
+    loss_grad_kernel<<<gS, 256>>>(z, lab, L, batch, counts + it, dz, losses + it);
+    conv_bwd_weight_f32<32, 4><<<gW, 256>>>(a3, dz, L, batch, chunk, n->grads + kW3, n->grads + kB3);
+    conv_bwd_data_f32<32, 4, true><<<gS, 256>>>(dz, n->params + kW3, a3, L, batch, ga);
+    conv_bwd_weight_f32<32, 32><<<gW, 256>>>(a2, ga, L, batch, chunk, n->grads + kW2, n->grads + kB2);
+    conv_bwd_data_f32<32, 32, true><<<gS, 256>>>(ga, n->params + kW2, a2, L, batch, gb);
+    conv_bwd_weight_f32<32, 32><<<gW, 256>>>(a1, gb, L, batch, chunk, n->grads + kW1, n->grads + kB1);
+    conv_bwd_data_f32<32, 32, true><<<gS, 256>>>(gb, n->params + kW1, a1, L, batch, ga);
+    conv_bwd_weight_f32<2, 32><<<gW, 256>>>(x0, ga, L, batch, chunk, n->grads + kW0, n->grads + kB0);
+    n->adam_t += 1;
+    const float c1 = 1.f / (1.f - powf(b1, (float)n->adam_t));
+    const float c2 = 1.f / (1.f - powf(b2, (float)n->adam_t));
+    adam_kernel<<<grid_for(kParams, 256), 256>>>(n->params, n->grads, n->m1, n->m2, kParams, lr, b1,
+                                                b2, c1, c2);
+    n->train_shots += batch;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "training kernels");
+      break;
+    }
+  }
+  if (rc == QCA_OK) rc = cuda_fail(cudaDeviceSynchronize(), "qca_net_train");
+  if (rc == QCA_OK && out_losses)
+    rc = cuda_fail(cudaMemcpy(out_losses, losses, sizeof(float) * iterations, cudaMemcpyDeviceToHost),
+                   "training loss copy");
+  cudaFree(bytes);
+  cudaFree(fl);
+  cudaFree(losses);
+  cudaFree(counts);
+  n->prepared = false;
+  return rc;
+}
+
+int qca_net_labels_async(const uint8_t* noise, int L, int64_t shots, uint8_t* out_labels,
+                         uint8_t* scratch, void* stream) {
+  if (L < 4 || L > QCA_MAX_L || shots < 0 || (shots > 0 && (!noise || !out_labels || !scratch))) {
+    set_error("qca_net_labels_async: bad arguments");
+    return QCA_ERR_ARG;
+  }
+  if (shots == 0) return QCA_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = shots * (int64_t)L * L;
+  uint8_t* sig = scratch;
+  uint8_t* dir = scratch + n;
+  syndrome_kernel<<<grid_for(n, 256), 256, 0, st>>>(noise, L, shots, sig);
+  first_dir_kernel<<<grid_for(n, 256), 256, 0, st>>>(sig, L, shots, dir);
+  mutual_label_kernel<<<grid_for(n, 256), 256, 0, st>>>(dir, L, shots, out_labels);
+  return cuda_fail(cudaGetLastError(), "label kernels");
+}
+
+}  // extern "C"
+
+namespace {
+
+// Bytes of inference workspace per site: sig, prop, two bf16 activation maps
+constexpr int64_t kWsPerSite = 2 + 2 * 64;
+
+int64_t net_chunk(int L) {
+  const int64_t per = (int64_t)L * L * kWsPerSite;
+  const int64_t c = ((int64_t)4 << 30) / per;  // about 4 GiB of workspace
+  return c < 1 ? 1 : c;
+}
+
+int net_workspace(qca_net_s* n, int64_t sites) {
+  const size_t need = (size_t)sites * kWsPerSite + 512;
+  if (n->ws_bytes >= need) return QCA_OK;
+  if (n->ws) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "net workspace sync");
+    cudaFree(n->ws);
+    n->ws = nullptr;
+    n->ws_bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&n->ws, need);
+  if (e != cudaSuccess) return cuda_fail(e, "net workspace");
+  n->ws_bytes = need;
+  return QCA_OK;
+}
+
+// Net inference over `shots` noise realisations in chunks: logits (fp32
+// [shots][4][L][L]) when `logits` is set, else proposals and the pairing
+// (residual, optional C0).
+int net_run(qca_net_s* n, const uint8_t* noise, int L, int64_t shots, float* logits,
+            uint8_t* resid, uint8_t* c0, cudaStream_t st) {
+  if (!n->prepared) {
+    prepare_weights_kernel<<<64, 256, 0, st>>>(n->params, n->wb, n->w1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "prepare weights");
+    n->prepared = true;
+  }
+  const int64_t LL = (int64_t)L * L;
+  const int64_t chunk = net_chunk(L);
+  int rc = net_workspace(n, (shots < chunk ? shots : chunk) * LL);
+  if (rc) return rc;
+  for (int64_t c0s = 0; c0s < shots; c0s += chunk) {
+    const int64_t m = (shots - c0s < chunk) ? shots - c0s : chunk;
+    const int64_t S = m * LL;
+    uint8_t* sig = n->ws;
+    uint8_t* prop = sig + S;
+    __nv_bfloat16* actA =
+        reinterpret_cast<__nv_bfloat16*>(n->ws + ((2 * S + 255) & ~(int64_t)255));
+    __nv_bfloat16* actB = actA + S * 32;
+    const uint8_t* Nc = noise + c0s * 2 * LL;
+    syndrome_kernel<<<grid_for(S, 256), 256, 0, st>>>(Nc, L, m, sig);
+    layer1_kernel<<<grid_for(S, 256), 256, 0, st>>>(sig, L, m, n->w1, n->params, actA);
+    const int64_t tiles = (S + 15) / 16;
+    const int gm = grid_for(tiles * 32, 128);
+    conv_mma_kernel<4, kActs><<<gm, 128, 0, st>>>(actA, n->wb, n->params + kB1, L, m, actB,
+                                                  nullptr, nullptr, nullptr);
+    conv_mma_kernel<4, kActs><<<gm, 128, 0, st>>>(actB, n->wb + 9 * 32 * 32, n->params + kB2, L, m,
+                                                  actA, nullptr, nullptr, nullptr);
+    if (logits) {
+      conv_mma_kernel<1, kLogits><<<gm, 128, 0, st>>>(actA, n->wb + 2 * 9 * 32 * 32,
+                                                      n->params + kB3, L, m, nullptr,
+                                                      logits + c0s * 4 * LL, nullptr, nullptr);
+    } else {
+      conv_mma_kernel<1, kProposals><<<gm, 128, 0, st>>>(actA, n->wb + 2 * 9 * 32 * 32,
+                                                         n->params + kB3, L, m, nullptr, nullptr,
+                                                         sig, prop);
+      pairing_kernel<<<grid_for(S, 256), 256, 0, st>>>(Nc, prop, L, m, resid + c0s * 2 * LL,
+                                                       c0 ? c0 + c0s * 2 * LL : nullptr);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "net inference kernels");
+  }
+  return QCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qca_net_logits_async(qca_net_t n, const uint8_t* noise, int L, int64_t shots,
+                         float* out_logits, void* stream) {
+  if (!n || L < 4 || L > QCA_MAX_L || shots < 0 || (shots > 0 && (!noise || !out_logits))) {
+    set_error("qca_net_logits_async: bad arguments");
+    return QCA_ERR_ARG;
+  }
+  if (shots == 0) return QCA_OK;
+  return net_run(n, noise, L, shots, out_logits, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+int qca_net_predecode_async(qca_net_t n, const uint8_t* noise, int L, int64_t shots,
+                            uint8_t* out_residual, uint8_t* out_c0, void* stream) {
+  if (!n || L < 4 || L > QCA_MAX_L || shots < 0 || (shots > 0 && (!noise || !out_residual))) {
+    set_error("qca_net_predecode_async: bad arguments");
+    return QCA_ERR_ARG;
+  }
+  if (shots == 0) return QCA_OK;
+  return net_run(n, noise, L, shots, nullptr, out_residual, out_c0, (cudaStream_t)stream);
+}
+
+int qca_net_decode_batch_async(qca_net_t n, const uint8_t* noise, int L, int64_t shots,
+                               int max_steps, uint64_t rng_seed, uint8_t* out_correction,
+                               int32_t* out_steps, uint8_t* out_logical_fail,
+                               const qca_config* cfg, uint8_t* residual_scratch, void* stream) {
+  if (!n || (shots > 0 && !residual_scratch)) {
+    set_error("qca_net_decode_batch_async: NULL net or residual scratch");
+    return QCA_ERR_ARG;
+  }
+  int rc = qca_net_predecode_async(n, noise, L, shots, residual_scratch, nullptr, stream);
+  if (rc) return rc;
+  rc = qca_decode_batch_async(residual_scratch, L, shots, max_steps, rng_seed, out_correction,
+                              out_steps, out_logical_fail, cfg, stream);
+  if (rc || shots == 0) return rc;
+  const int64_t E = shots * 2 * (int64_t)L * L;
+  combine_kernel<<<grid_for(E / 16 + 1, 256), 256, 0, (cudaStream_t)stream>>>(
+      out_correction, noise, residual_scratch, E);
+  return cuda_fail(cudaGetLastError(), "combine kernel");
+}
+
+}  // extern "C"

@@ -1,0 +1,209 @@
+"""GPU checks of the learned pre-decoder through the C ABI.
+
+- labels (integer work): bit-exact against the CPU reference of the
+  automaton's first step;
+- logits: within 1e-2 of the FP64 CPU forward that applies the same bf16
+  rounding points;
+- proposals and pairing: bit-exact against the reference rule applied to the
+  GPU's own fp32 logits (the float decision is taken in the kernel's
+  precision on both sides);
+- net + automaton: the automaton part is bit-exact against the oracle run on
+  the GPU's residual, and the combined correction clears the syndrome;
+- training lowers the loss and the trained net reproduces most labels;
+- the logical failure rate of net + automaton is within 2 sigma of the plain
+  automaton's below threshold.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import oracle.net as onet  # noqa: E402
+import paper_2506_03266_gb300 as qca  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    qca.build()
+    oracle.build()
+    qca.lib()
+    yield
+    torch.cuda.synchronize()
+
+
+@pytest.fixture(scope="module")
+def trained():
+    """A net trained on L = 32 crops, p ~ U[0.02, 0.07)."""
+    net = qca.Net(seed=1)
+    losses = net.train(L=32, iterations=1500, batch=64, p_lo=0.02, p_hi=0.07, seed=1, lr=2e-3)
+    yield net, losses
+    net.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def anyon_maps(N):
+    return np.stack([(oracle.syndrome(n) == -1).astype(np.uint8) for n in N])
+
+
+# ------------------------------------------------------------------- labels
+
+@pytest.mark.parametrize("L,p,shots", [(4, 0.2, 8), (7, 0.08, 10), (16, 0.05, 12),
+                                       (33, 0.03, 6), (256, 0.05, 2)])
+def test_labels_bit_exact(L, p, shots):
+    N = oracle.sample_errors(L, shots, p, seed=3)
+    got = qca.net_labels(dev(N)).cpu().numpy()
+    for s in range(shots):
+        want = onet.first_step_labels(anyon_maps(N[s:s + 1])[0])
+        np.testing.assert_array_equal(got[s], want, err_msg=f"shot {s}")
+
+
+# ------------------------------------------------------------------- logits
+
+def _check_logits(net, L, shots, p, seed):
+    N = oracle.sample_errors(L, shots, p, seed=seed)
+    z = net.logits(dev(N))
+    torch.cuda.synchronize()
+    z = z.cpu().numpy()
+    params = net.get_params()
+    A = anyon_maps(N)
+    worst = 0.0
+    for s in range(shots):
+        want = onet.forward(A[s], params, quantize=True)
+        worst = max(worst, float(np.max(np.abs(z[s] - want))))
+    assert worst <= 1e-2, f"max |logit - fp64 forward| = {worst}"
+    return worst
+
+
+@pytest.mark.parametrize("L,shots", [(16, 3), (21, 3), (5, 7)])
+def test_logits_initial_net(L, shots):
+    net = qca.Net(seed=7)
+    try:
+        _check_logits(net, L, shots, 0.08, seed=L)
+    finally:
+        net.close()
+
+
+def test_logits_trained_net(trained):
+    net, _ = trained
+    _check_logits(net, 24, 4, 0.05, seed=9)
+    _check_logits(net, 19, 2, 0.07, seed=10)
+
+
+def test_set_get_params_roundtrip():
+    net = qca.Net(seed=2)
+    try:
+        p = net.get_params()
+        assert p.shape == (onet.param_count(),) and np.isfinite(p).all()
+        q = (np.random.default_rng(0).standard_normal(p.size) * 0.05).astype(np.float32)
+        net.set_params(q)
+        np.testing.assert_array_equal(net.get_params(), q)
+        _check_logits(net, 12, 2, 0.1, seed=4)  # the prepared bf16 weights follow set_params
+    finally:
+        net.close()
+
+
+# ------------------------------------------------------- pairing / residual
+
+@pytest.mark.parametrize("L,shots,p", [(16, 20, 0.05), (21, 5, 0.08)])
+def test_predecode_pairing_bit_exact(trained, L, shots, p):
+    net, _ = trained
+    N = oracle.sample_errors(L, shots, p, seed=21)
+    Nd = dev(N)
+    z = net.logits(Nd).cpu().numpy()          # fp32, the kernel's own values
+    R, C0 = net.predecode(Nd)
+    torch.cuda.synchronize()
+    R, C0 = R.cpu().numpy(), C0.cpu().numpy()
+    A = anyon_maps(N)
+    paired = 0
+    for s in range(shots):
+        prop = onet.proposals(A[s], z[s])     # float32 comparisons, same as the kernel
+        want = onet.pairing_links(A[s], prop)
+        np.testing.assert_array_equal(C0[s], want, err_msg=f"shot {s}")
+        paired += int(want.sum())
+    np.testing.assert_array_equal(R, N ^ C0)
+    assert paired > 0
+
+
+def test_net_decode_matches_oracle_on_residual(trained):
+    net, _ = trained
+    L, shots = 16, 60
+    N = oracle.sample_errors(L, shots, 0.06, seed=31)
+    Nd = dev(N)
+    C, steps, fail = net.decode_batch(Nd, max_steps=4096)
+    R, C0 = net.predecode(Nd)
+    torch.cuda.synchronize()
+    C, steps, fail, R, C0 = (t.cpu().numpy() for t in (C, steps, fail, R, C0))
+    for s in range(shots):
+        Co, so, fo = oracle.decode_shot(R[s], max_steps=4096)
+        np.testing.assert_array_equal(C[s], Co ^ C0[s], err_msg=f"shot {s}")
+        assert (steps[s], fail[s]) == (so, fo), f"shot {s}"
+
+
+def test_net_decode_full_size_properties(trained):
+    # L = 128, the learned-stage workload's size: every shot that ends within
+    # the budget leaves N xor C with an empty syndrome (checked with torch ops)
+    net, _ = trained
+    L, shots = 128, 400
+    N = qca.sample_errors(L, shots, 0.04, seed=0)
+    C, steps, fail = net.decode_batch(N, max_steps=4096)
+    E = (N ^ C).to(torch.int32)
+    ex, ey = E[:, 0], E[:, 1]
+    sig = ex ^ torch.roll(ex, 1, dims=2) ^ ey ^ torch.roll(ey, 1, dims=1)
+    done = fail != 2
+    assert int(done.sum()) == shots
+    assert int(sig[done].sum()) == 0
+    assert int(steps.min()) >= 0
+
+
+# ----------------------------------------------------------------- training
+
+def test_training_lowers_loss_and_learns_labels(trained):
+    net, losses = trained
+    assert np.isfinite(losses).all()
+    assert losses[-50:].mean() < 0.5 * losses[:5].mean(), (losses[:5], losses[-50:].mean())
+    L, shots = 32, 64
+    N = oracle.sample_errors(L, shots, 0.05, seed=77)
+    Nd = dev(N)
+    lab = qca.net_labels(Nd).cpu().numpy()
+    z = net.logits(Nd).cpu().numpy()
+    A = anyon_maps(N)
+    prop = np.stack([onet.proposals(A[s], z[s]) for s in range(shots)])
+    m = lab != 255
+    acc = float((prop[m] == lab[m]).mean())
+    assert acc > 0.9, acc
+
+
+def test_training_argument_errors():
+    net = qca.Net(seed=0)
+    try:
+        with pytest.raises(qca.QcaError):
+            net.train(L=200, iterations=1, batch=1, p_lo=0.01, p_hi=0.05)
+        with pytest.raises(qca.QcaError):
+            net.train(L=16, iterations=1, batch=1, p_lo=0.05, p_hi=0.01)
+        assert net.train(L=16, iterations=0, batch=1, p_lo=0.01, p_hi=0.05).size == 0
+    finally:
+        net.close()
+
+
+# ------------------------------------------------------- statistical target
+
+def test_net_plus_automaton_plog_within_2sigma(trained):
+    # below threshold (p = 0.058, about 0.8 of the paper's 7.3 %), L = 32:
+    # failure counts of plain and net + automaton on the same noise agree
+    # within two standard deviations of their difference
+    net, _ = trained
+    L, shots = 32, 40000
+    N = qca.sample_errors(L, shots, 0.058, seed=0)
+    _, _, f_plain = qca.decode_batch(N, max_steps=4096)
+    _, _, f_net = net.decode_batch(N, max_steps=4096)
+    a = (f_plain == 1).double().mean().item()
+    b = (f_net == 1).double().mean().item()
+    sigma = np.sqrt((a * (1 - a) + b * (1 - b)) / shots)
+    assert a > 0.0 and abs(a - b) <= 2 * sigma + 1e-12, (a, b, sigma)
