@@ -282,6 +282,180 @@ def run_uneven(args, rank, world, local):
     plan.close()
 
 
+# Algorithmic FLOPs of the pre-decoder per site: 2 x 9 taps x (2*32 + 32*32 +
+# 32*32 + 32*4) multiply-adds over the four 3x3 convolutions.
+NET_FLOP_PER_SITE = 2 * 9 * (2 * 32 + 32 * 32 + 32 * 32 + 32 * 4)
+
+
+def measured_peak(key, fallback):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key]), "measured"
+    except (OSError, KeyError, ValueError):
+        return fallback, "fallback"
+
+
+def run_net(args, rank, world, local):
+    """Learned pre-decoder + automaton at L = 128, p = 0.04 (100 000 shots):
+    the net is trained first (untimed) on 10^6 automaton-labelled syndromes
+    (L = 32 tori, p ~ U[0.02, 0.07), training seed 1); one step is one
+    net + automaton decode of the whole batch (evaluation seed 0).  The plain
+    automaton is timed on the same noise for the comparison."""
+    import numpy as np
+    import torch
+
+    import paper_2506_03266_gb300 as qca
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    qca.build()
+    qca.lib()
+    L = args.L if args.L != L_DEFAULT else 128
+    p = args.p if args.p != P_DEFAULT else 0.04
+    shots = args.shots
+    train_batch, train_L = 256, 32
+    train_iters = (1_000_000 + train_batch - 1) // train_batch
+    net = qca.Net(seed=1)
+    t0 = time.perf_counter()
+    losses = net.train(L=train_L, iterations=train_iters, batch=train_batch, p_lo=0.02,
+                       p_hi=0.07, seed=1, lr=2e-3)
+    train_s = time.perf_counter() - t0
+
+    shot0, _ = shard(rank, shots)
+    N = qca.sample_errors(L, shots, p, seed=0, shot0=shot0)
+    out = (torch.empty_like(N), torch.empty(shots, dtype=torch.int32, device="cuda"),
+           torch.empty(shots, dtype=torch.uint8, device="cuda"))
+    plain = (torch.empty_like(N), torch.empty(shots, dtype=torch.int32, device="cuda"),
+             torch.empty(shots, dtype=torch.uint8, device="cuda"))
+    scratch = torch.empty_like(N)
+    R, C0 = torch.empty_like(N), torch.empty_like(N)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        net.decode_batch(N, MAX_STEPS, out=out, scratch=scratch)
+        qca.decode_batch(N, MAX_STEPS, out=plain)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        net.decode_batch(N, MAX_STEPS, out=out, scratch=scratch)
+        ev[i + 1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = ev[0].elapsed_time(ev[-1])
+    # the stages, each timed on its own: net (pre-decode) and plain automaton
+    stage = {}
+    for name, fn in [("predecode", lambda: qca.lib().qca_net_predecode_async(
+                          net.handle, ctypes_ptr(N), L, shots, ctypes_ptr(R), None,
+                          ctypes_stream(stream))),
+                     ("plain", lambda: qca.decode_batch(N, MAX_STEPS, out=plain))]:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            rc = fn()
+            if isinstance(rc, int) and rc != 0:
+                raise RuntimeError(qca.last_error())
+        b.record(stream)
+        barrier()
+        stage[name] = a.elapsed_time(b) / args.steps
+    if dist is not None:
+        total_ms = reduce_time_max(total_ms, dist, "cuda")
+        stage = {k: reduce_time_max(v, dist, "cuda") for k, v in stage.items()}
+    ms_per_step = total_ms / args.steps
+    steps_h, fail_h = out[1].cpu().numpy(), out[2].cpu().numpy()
+    psteps_h, pfail_h = plain[1].cpu().numpy(), plain[2].cpu().numpy()
+    R_pairs = int(torch.count_nonzero(R ^ N).item()) if shots else 0
+
+    # end to end: host noise -> device, net + automaton, steps and flags back
+    e2e = None
+    if not args.no_e2e:
+        Nh = N.cpu().pin_memory()
+        so = torch.empty(shots, dtype=torch.int32, pin_memory=True)
+        fo = torch.empty(shots, dtype=torch.uint8, pin_memory=True)
+        Nd = torch.empty_like(N)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            Nd.copy_(Nh, non_blocking=True)
+            net.decode_batch(Nd, MAX_STEPS, out=out, scratch=scratch)
+            so.copy_(out[1], non_blocking=True)
+            fo.copy_(out[2], non_blocking=True)
+        barrier()
+        el = reduce_time_max((time.perf_counter() - t0) / args.steps, dist, "cuda")
+        e2e = {"value": world * shots / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(Nh.numel()), "d2h_bytes_per_step": shots * 5}
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        net.close()
+        return
+    sites = shots * L * L
+    peak, src = measured_peak("bf16_tflops", 1900.0)
+    achieved = NET_FLOP_PER_SITE * sites / (stage["predecode"] / 1e3) / 1e12
+    sig = lambda f: float(np.sqrt(max(f * (1 - f), 1e-300) / max(shots, 1)))
+    pl_net, pl_plain = float((fail_h > 0).mean()), float((pfail_h > 0).mean())
+    line = {
+        "metric": "shot-decodes/s of net + automaton (learned pre-decoder, then the exact "
+                  "automaton) vs the plain automaton",
+        "value": world * shots / (ms_per_step / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+u8",
+        "data": "synthetic",
+        "config": {"workload": (f"net + automaton decode, L={L} toric code, i.i.d. bit-flip "
+                                f"p={p} (seed 0), {shots} shots per GPU; net trained on "
+                                f"{train_iters * train_batch} automaton-labelled L={train_L} "
+                                f"syndromes (seed 1)"),
+                   "L": L, "p": p, "shots_per_gpu": shots,
+                   "l2": "inputs larger than L2 (no flush needed)",
+                   "train": {"syndromes": train_iters * train_batch, "seconds": train_s,
+                             "final_loss": float(np.mean(losses[-50:]))}},
+        "comparison": {
+            "plain_shot_decodes_per_s": world * shots / (stage["plain"] / 1e3),
+            "net_ca_shot_decodes_per_s": world * shots / (ms_per_step / 1e3),
+            "predecode_ms": stage["predecode"], "plain_ms": stage["plain"],
+            "p_log_net_ca": pl_net, "p_log_plain": pl_plain,
+            "p_log_sigma": [sig(pl_net), sig(pl_plain)],
+            "mean_steps_net_ca": float(steps_h.mean()), "mean_steps_plain": float(psteps_h.mean()),
+            "links_flipped_by_net_per_shot": R_pairs / max(shots, 1),
+            "site_updates_per_s_net_ca": float(steps_h.astype(np.int64).sum()) * L * L
+            / (ms_per_step / 1e3)},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "note": f"pre-decoder stage (all net launches), {NET_FLOP_PER_SITE} "
+                             f"FLOP/site, peak = bf16 burst ({src})"},
+        "clocks": clk,
+        "gpu_launches": args.steps * (2 + 6 * ((shots + qca.net_chunk_shots(L) - 1)
+                                               // qca.net_chunk_shots(L))),
+        "e2e": e2e,
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    net.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def ctypes_ptr(t):
+    import ctypes
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def ctypes_stream(s):
+    import ctypes
+    return ctypes.c_void_p(s.cuda_stream)
+
+
 def workload_config(args):
     return {
         "workload": (f"plain message-passing automaton decode, L={args.L} toric code, "
@@ -304,8 +478,9 @@ def main():
     ap.add_argument("--shots", type=int, default=SHOTS_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="uniform", choices=["uniform", "uneven"],
-                    help="uniform: the L=256 headline; uneven: 200 000 shots of mixed L")
+    ap.add_argument("--workload", default="uniform", choices=["uniform", "uneven", "net"],
+                    help="uniform: the L=256 headline; uneven: 200 000 shots of mixed L; "
+                         "net: learned pre-decoder + automaton at L=128, p=0.04")
     ap.add_argument("--autotune", action="store_true",
                     help="tune band height and sparse threshold per L before timing")
     args = ap.parse_args()
@@ -319,6 +494,9 @@ def main():
         return
     if args.workload == "uneven":
         run_uneven(args, rank, world, local)
+        return
+    if args.workload == "net":
+        run_net(args, rank, world, local)
         return
 
     # CPU baseline before the first GPU call (oracle pool is spawned)

@@ -286,6 +286,10 @@ int qca_net_train(qca_net_t net, int L, int64_t iterations, int batch, double p_
 int qca_net_labels_async(const uint8_t* noise, int L, int64_t shots, uint8_t* out_labels,
                          uint8_t* scratch, void* stream);
 
+/* Shots per inference chunk at size L (the net runs chunk by chunk: six
+ * kernel launches per chunk), or QCA_ERR_ARG for L outside [4, QCA_MAX_L]. */
+int64_t qca_net_chunk_shots(int L);
+
 /* Logits of the net: out_logits fp32 [shots][4][L][L].  The handle keeps an
  * inference workspace (about 130 bytes per site of up to 4 GiB worth of
  * shots) that grows on demand; growth synchronises the device, so make one

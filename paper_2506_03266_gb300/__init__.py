@@ -88,6 +88,7 @@ def lib():
             "qca_net_train": ([vp, i32, i64, i32, ctypes.c_double, ctypes.c_double, u64,
                                ctypes.c_float, vp], i32),
             "qca_net_labels_async": ([vp, i32, i64, vp, vp, vp], i32),
+            "qca_net_chunk_shots": ([i32], i64),
             "qca_net_logits_async": ([vp, vp, i32, i64, vp, vp], i32),
             "qca_net_predecode_async": ([vp, vp, i32, i64, vp, vp, vp], i32),
             "qca_net_decode_batch_async": ([vp, vp, i32, i64, i32, u64, vp, vp, vp, cfgp, vp,
@@ -365,6 +366,13 @@ def net_labels(errors, stream=None):
                                       ctypes.c_void_p(scratch.data_ptr()), _stream(torch, stream)))
     torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
     return out
+
+
+def net_chunk_shots(L: int) -> int:
+    n = int(lib().qca_net_chunk_shots(L))
+    if n < 0:
+        _check(n)
+    return n
 
 
 class Net:

@@ -903,6 +903,14 @@ int net_run(qca_net_s* n, const uint8_t* noise, int L, int64_t shots, float* log
 
 extern "C" {
 
+int64_t qca_net_chunk_shots(int L) {
+  if (L < 4 || L > QCA_MAX_L) {
+    set_error("qca_net_chunk_shots: L = %d outside [4, %d]", L, QCA_MAX_L);
+    return QCA_ERR_ARG;
+  }
+  return net_chunk(L);
+}
+
 int qca_net_logits_async(qca_net_t n, const uint8_t* noise, int L, int64_t shots,
                          float* out_logits, void* stream) {
   if (!n || L < 4 || L > QCA_MAX_L || shots < 0 || (shots > 0 && (!noise || !out_logits))) {
