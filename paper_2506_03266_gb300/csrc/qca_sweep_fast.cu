@@ -10,8 +10,10 @@
 //     "a value above m_max disappears" become a plain unsigned min and an add
 //     that saturates at 0xFF.
 //   * site bitmaps with rows padded to a power-of-two number of 32-bit words:
-//     sigma (current and next), flipped links, correction; and a compacted
-//     list of the current anyons ((y << 8) | x).
+//     sigma (the whole lattice in every CTA), two flipped-link maps (x and y
+//     links; the pair alternates with the step parity so the next step can
+//     clear one while the other is read), the correction (own rows); and a
+//     compacted list of the current anyons ((y << 8) | x).
 //
 // One decoder step (Def. "synchronous automaton decoder"):
 //   1. message update, the v = 3 applications of A^(D) (Def. Dd_msg_passing)
@@ -20,21 +22,28 @@
 //                     for d = 1, 2, 3,
 //                     satadd( min_{|j| <= 3} w0(r - 3 a^ + j b^), 3 ) ),
 //      i.e. a width-7 transverse window at longitudinal distance 3 (dense,
-//      in place with a rolling register window), then the anyon terms
-//      (sparse: each anyon writes its light-cone sections, largest value
-//      first).  The unsigned byte min runs on the native 16x2 integer min,
-//      each site in the high byte of a 16-bit lane.
-//   2. forces and feedback (Eqs. blahdef, degbreak, ddfeedback) for anyons
-//      only; a flipped-link bitmap implements the OR so a link crossed from
-//      both ends flips once; the flipping thread toggles the correction bit and
-//      sigma at both ends.
-//   3. early exit when sigma is empty; budget check.
+//      in place with a rolling register window), then the anyon terms: dense
+//      from dilated sigma rows on the first step and whenever anyons are
+//      many, else per anyon (each anyon writes its light-cone sections,
+//      largest value first).  The unsigned byte min runs on the native 16x2
+//      integer min, each site in the high byte of a 16-bit lane.
+//   2. forces and feedback (Eqs. blahdef, degbreak, ddfeedback) for the listed
+//      anyons: each ORs the bit of the link it crosses into the flipped-link
+//      map of every CTA of the cluster, so a link crossed from both ends flips
+//      once (the OR of the feedback rule).
+//   3. a dense pass over the own rows: sigma <- sigma xor (syndrome of the
+//      flipped links), correction ^= flipped links, the next anyon list, and
+//      the early exit when sigma is empty; budget check.
 // The homology check and the byte outputs follow the last step.
 //
 // Two-CTA clusters (L > 128) split every plane by rows; each CTA keeps the full
 // sigma, writes the cone sections that fall in its rows, moves the anyons of its
 // rows, and reaches the partner's planes and bitmaps through distributed shared
-// memory.  Two cluster barriers per step.
+// memory.  Two cluster barriers per step.  With a work counter (uneven
+// batches) the clusters take shots from it until it runs past the batch; rank
+// 0 fetches, the cluster reads the value over DSMEM between two barriers, and a
+// final barrier keeps every CTA's shared memory alive until its partner's last
+// remote access is done.
 #include <cooperative_groups.h>
 
 #include <algorithm>
