@@ -49,8 +49,8 @@ ALU_PEAK_LANE_OPS = 152 * 64 * 2 * 2.070e9
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 4000 shots,
 # profiles/fast_kernel_L256_p005_full.md), valid only for the kernel source
 # whose SHA-256 prefix is recorded with it; reported as null otherwise.
-TRAFFIC_PER_SHOT = {"sha256_prefix": "afbd23fa2d68cab7", "L": 256, "p": 0.05,
-                    "bytes_per_shot": (525.750784e6 + 479.547904e6) / 4000}
+TRAFFIC_PER_SHOT = {"sha256_prefix": "94133578eb47e24f", "L": 256, "p": 0.05,
+                    "bytes_per_shot": (526.192128e6 + 479.648000e6) / 4000}
 
 
 def traffic_per_launch(L, p, shots):
@@ -317,7 +317,7 @@ def run_net(args, rank, world, local):
     p = args.p if args.p != P_DEFAULT else 0.04
     shots = args.shots
     train_batch, train_L = 256, 32
-    train_iters = (1_000_000 + train_batch - 1) // train_batch
+    train_iters = max(1, (args.train_syndromes + train_batch - 1) // train_batch)
     net = qca.Net(seed=1)
     t0 = time.perf_counter()
     losses = net.train(L=train_L, iterations=train_iters, batch=train_batch, p_lo=0.02,
@@ -481,6 +481,8 @@ def main():
     ap.add_argument("--workload", default="uniform", choices=["uniform", "uneven", "net"],
                     help="uniform: the L=256 headline; uneven: 200 000 shots of mixed L; "
                          "net: learned pre-decoder + automaton at L=128, p=0.04")
+    ap.add_argument("--train-syndromes", type=int, default=1_000_000,
+                    help="net workload: automaton-labelled training syndromes (untimed)")
     ap.add_argument("--autotune", action="store_true",
                     help="tune band height and sparse threshold per L before timing")
     args = ap.parse_args()
