@@ -313,9 +313,22 @@ int qca_net_decode_batch_async(qca_net_t net, const uint8_t* noise, int L, int64
                                const qca_config* cfg, uint8_t* residual_scratch, void* stream);
 
 /* Kernel path chosen for a lattice size: 1 = on-chip fast sweep, 2 = on-chip
- * sweep on a 2-CTA cluster, 0 = generic sweep with HBM-resident state.
+ * sweep on a 2-CTA cluster, 3 = large-lattice sweep (8-CTA cluster per shot,
+ * state in global memory, bulk-copy staged bands; L a multiple of 128, chosen
+ * automatically above 256), 0 = generic sweep with HBM-resident state.
  * Returns a negative code for an unsupported L. */
 int qca_kernel_path(int L, const qca_config* cfg);
+
+/* Override the kernel path for one lattice size: path -1 = automatic (the
+ * default), 0 = generic sweep, 3 = large-lattice sweep (L a multiple of 128,
+ * 128 <= L <= QCA_MAX_L).  Every path gives bit-identical results; the
+ * override exists to compare them and to run the large-lattice kernel on
+ * sizes the oracle checks quickly.  Not thread-safe against concurrent
+ * decodes of the same L.  With the large-lattice path, out_logical_fail = 3
+ * marks a shot whose decode a device watchdog stopped (a staged copy did not
+ * complete within about two seconds); the rest of that call's outputs are
+ * then unreliable. */
+int qca_set_kernel_path(int L, int path);
 
 /* Release the device workspaces the library caches (generic-kernel state and
  * host-path staging buffers) on the current device. */

@@ -80,6 +80,7 @@ def lib():
             "qca_sample_errors_uneven_async": ([vp, vp, vp, i64, u64, vp, vp], i32),
             "qca_decode_uneven_async": ([vp, vp, i32, u64, vp, vp, vp, cfgp, vp], i32),
             "qca_kernel_path": ([i32, cfgp], i32),
+            "qca_set_kernel_path": ([i32, i32], i32),
             "qca_net_param_count": ([], i64),
             "qca_net_create": ([u64, ctypes.POINTER(vp)], i32),
             "qca_net_destroy": ([vp], i32),
@@ -144,6 +145,11 @@ def kernel_path(L: int, v: int = 3) -> int:
     if rc < 0:
         _check(rc)
     return rc
+
+
+def set_kernel_path(L: int, path: int = -1):
+    """Override the kernel for size L: -1 automatic, 0 generic, 3 large-lattice."""
+    _check(lib().qca_set_kernel_path(L, path))
 
 
 def sample_errors(L: int, shots: int, p: float, seed: int, shot0: int = 0, out=None,

@@ -79,11 +79,21 @@ static int check_sizes(int L, int64_t shots, int max_steps) {
   return QCA_OK;
 }
 
-static int dispatch(DecodeArgs& a, cudaStream_t stream) {
+int decode_path(int L, int v, int m_max) {
+  if (generic_forced(L)) return 0;
+  if (tiled_path_for(L, v, m_max) > 0) return 3;
+  return fast_path_for(L, v, m_max);
+}
+
+int launch_decode(const DecodeArgs& a, cudaStream_t stream) {
   if (a.shots == 0) return QCA_OK;
-  if (fast_path_for(a.L, a.v, a.m_max) > 0) return launch_fast(a, stream);
+  const int path = decode_path(a.L, a.v, a.m_max);
+  if (path == 3) return launch_tiled(a, stream);
+  if (path > 0) return launch_fast(a, stream);
   return launch_generic(a, stream);
 }
+
+static int dispatch(DecodeArgs& a, cudaStream_t stream) { return launch_decode(a, stream); }
 
 static int fill_args(DecodeArgs& a, const uint8_t* in, int L, int64_t shots, int max_steps,
                      uint64_t seed, const qca_config& c) {
@@ -228,7 +238,7 @@ int qca_kernel_path(int L, const qca_config* cfg) {
   if (rc) return rc;
   qca_config c;
   if ((rc = check_config(cfg, &c))) return rc;
-  return fast_path_for(L, c.v, c.m_max);
+  return decode_path(L, c.v, c.m_max);
 }
 
 int qca_decode_batch_host(const uint8_t* syndrome, int L, int64_t shots, int max_steps,
@@ -255,7 +265,9 @@ int qca_decode_batch_host(const uint8_t* syndrome, int L, int64_t shots, int max
   if (chunk < 1) chunk = 1;
   if (chunk > shots) chunk = shots;
   const size_t per_set = ((chunk * E + 255) & ~(size_t)255) * 2 + ((chunk * 5 + 255) & ~(size_t)255) + 512;
-  const bool concurrent = fast_path_for(L, c.v, c.m_max) > 0;  // the generic path shares one workspace
+  // the generic and tiled paths share one workspace per device: no concurrent chunks
+  const int path = decode_path(L, c.v, c.m_max);
+  const bool concurrent = path == 1 || path == 2;
   std::lock_guard<std::mutex> lk(g_stage_mu);
   Staging& st = g_stage[dev];
   if (st.bytes < 2 * per_set) {
@@ -308,6 +320,8 @@ int qca_decode_batch_host(const uint8_t* syndrome, int L, int64_t shots, int max
 
 int qca_free_workspace(void) {
   int rc = generic_workspace_release();
+  const int rc2 = tiled_workspace_release();
+  if (rc == QCA_OK) rc = rc2;
   std::lock_guard<std::mutex> lk(g_stage_mu);
   int dev = 0;
   cudaGetDevice(&dev);

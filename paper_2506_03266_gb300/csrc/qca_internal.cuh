@@ -80,6 +80,15 @@ int launch_generic(const DecodeArgs& a, cudaStream_t stream);
 int generic_workspace_release();
 int fast_path_for(int L, int v, int m_max);  // 0 generic, 1 single-CTA, 2 two-CTA cluster
 int launch_fast(const DecodeArgs& a, cudaStream_t stream);
+// Large-lattice kernel (cluster of 8 CTAs per shot, state in global memory).
+int tiled_path_for(int L, int v, int m_max);  // 1 if it takes (L, v, m_max)
+int launch_tiled(const DecodeArgs& a, cudaStream_t stream);
+int tiled_workspace_release();
+int generic_forced(int L);  // qca_set_kernel_path(L, 0) is in effect
+// Kernel path for (L, v, m_max) with the overrides applied: 0 generic,
+// 1 / 2 on-chip (one CTA / two-CTA cluster), 3 tiled; and the launch.
+int decode_path(int L, int v, int m_max);
+int launch_decode(const DecodeArgs& a, cudaStream_t stream);
 // Generic sweep on the library's fixed device array (no allocation).
 int launch_generic_noalloc(const DecodeArgs& a, cudaStream_t stream);
 size_t noalloc_slot_bytes(int L);

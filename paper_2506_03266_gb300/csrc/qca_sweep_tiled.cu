@@ -1,0 +1,720 @@
+// Large-lattice synchronous sweep: L a multiple of 128 up to 1024, v = 3.
+//
+// A 1024^2 lattice needs 4 MB of message fields, more than one SM holds, so the
+// state of a shot lives in a per-cluster slot of global memory (mostly L2
+// resident) and a cluster of 8 CTAs decodes one shot, each CTA owning L/8 rows
+// of every plane.  Each step:
+//   1. messages (the v = 3 applications of A^(D), Def. Dd_msg_passing, fused
+//      exactly as in the on-chip kernel): every CTA streams bands of 16 rows of
+//      each plane plus 3 halo rows on either side, and the matching rows of the
+//      syndrome bitmap, from the previous step's buffer into shared memory with
+//      bulk asynchronous copies (TMA, completion on an mbarrier, the next band
+//      prefetched while this one is computed); computes
+//        w3(r) = min( off + d - 1 for the smallest d <= 3 with an anyon on
+//                     {r - s d a^ + j b^, |j| <= d},
+//                     satadd( min_{|j| <= 3} w0(r - 3 s a^ + j b^), 3 ) )
+//      and writes the band to the other buffer;
+//   2. forces and feedback (Eqs. blahdef, degbreak, ddfeedback) for the anyons
+//      of the CTA's rows: each ORs the bit of the link it crosses into the
+//      flipped-link maps (a link crossed from both ends flips once);
+//   3. sigma <- sigma xor (syndrome of the flipped links), correction ^= flips,
+//      anyon count; the cluster agrees on the early exit.
+// Cluster barriers separate the phases (three per step).  Planes are stored as
+// in the on-chip kernel, each in the frame where its messages travel along the
+// byte axis (x fields [y][x], y fields [x][y]), with the offset encoding
+// w = m - 1 + (255 - m_max), 0xFF = no message.  The syndrome and the flipped
+// links are kept as bitmaps in both frames, so the terms of either plane family
+// and the sigma update read rows only.
+#include <cooperative_groups.h>
+
+#include <mutex>
+#include <vector>
+
+#include "qca_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace qca {
+
+namespace {
+
+constexpr int kTCL = 8;        // CTAs per cluster: one shot
+constexpr int kTThreads = 256;
+constexpr int kTB = 16;        // plane rows per staged band
+constexpr int kTRows = kTB + 6;  // staged rows: 3 halo rows on either side
+constexpr long long kWaitCycles = 4000000000LL;  // watchdog on a copy (about 2 s)
+
+struct TiledGeom {
+  int L;
+  int W;      // 32-bit words per bitmap row (L / 32)
+  int RL;     // rows per CTA in either frame (L / 8)
+  int cols;   // 32-bit words per plane row (L / 4)
+  int off;    // 255 - m_max
+  size_t LL;
+  // slot layout (byte offsets)
+  size_t o_sig, o_flip, o_C, slot;
+  // shared memory layout (byte offsets)
+  size_t s_band, s_sband, s_M, s_D, s_bar, s_misc, smem;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bulk copy global -> this CTA's shared memory, completion counted on bar.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Generic-proxy global writes <-> bulk-copy (async proxy) reads.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Wait for phase `parity` of bar, at most kWaitCycles; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+// Byte-wise unsigned min on the native 16x2 min (each byte alone in a lane).
+__device__ __forceinline__ uint32_t vmin4(uint32_t a, uint32_t b) {
+  return __vminu2(a & 0xFF00FF00u, b & 0xFF00FF00u) | __vminu2(a & 0x00FF00FFu, b & 0x00FF00FFu);
+}
+
+__device__ __forceinline__ int twrap(int i, int L) { return i < 0 ? i + L : (i >= L ? i - L : i); }
+
+// Four bits of a bitmap row starting at bit position pos (wrapping at the row end).
+__device__ __forceinline__ uint32_t bits4(const uint32_t* row, int W, int pos) {
+  const int q = pos >> 5, sh = pos & 31;
+  const int q1 = (q + 1 == W) ? 0 : q + 1;
+  const uint64_t two = ((uint64_t)row[q1] << 32) | row[q];
+  return (uint32_t)(two >> sh) & 0xFu;
+}
+
+// 4 bits -> 4 bytes of 0xFF / 0x00 (bit k -> byte k).
+__device__ __forceinline__ uint32_t nib_mask(uint32_t nib) {
+  return ((nib * 0x00204081u) & 0x01010101u) * 0xFFu;
+}
+__device__ __forceinline__ uint32_t nibble_of_bytes(uint32_t w) { return (w * 0x01020408u) >> 24; }
+
+// Direction from the four fields (offset encoding): readings R1-R4.
+// Codes: 0 none, 1 +x, 2 -x, 3 +y, 4 -y.
+__device__ __forceinline__ int tiled_dir(uint32_t wpx, uint32_t wmx, uint32_t wpy, uint32_t wmy) {
+  uint32_t best = wmy;
+  int axis_y = 1;
+  if (wmx < best) { best = wmx; axis_y = 0; }
+  if (wpx < best) { best = wpx; axis_y = 0; }
+  if (wpy < best) { best = wpy; axis_y = 1; }
+  if (best == 0xFFu) return 0;
+  const uint32_t up = axis_y ? wpy : wpx, um = axis_y ? wmy : wmx;
+  if (up == um) return 0;
+  if (up < um) return axis_y ? 4 : 2;
+  return axis_y ? 3 : 1;
+}
+
+template <class T>
+__device__ __forceinline__ T* rank_ptr(T* p, int r) {
+  return cg::this_cluster().map_shared_rank(p, (unsigned)r);
+}
+
+__global__ void __launch_bounds__(kTThreads, 1) tiled_kernel(DecodeArgs a, TiledGeom g,
+                                                             uint8_t* ws) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int L = g.L, W = g.W, RL = g.RL, cols = g.cols;
+  const size_t LL = g.LL;
+  const int r0 = rank * RL;  // first own row in either frame
+  const int nclusters = gridDim.x / kTCL;
+  const int cid = blockIdx.x / kTCL;
+
+  uint8_t* band = smem + g.s_band;                                         // [2][kTRows][L]
+  uint32_t* sband = reinterpret_cast<uint32_t*>(smem + g.s_sband);         // [2][kTRows][W]
+  uint32_t* M = reinterpret_cast<uint32_t*>(smem + g.s_M);                 // [kTB][cols]
+  uint32_t* D = reinterpret_cast<uint32_t*>(smem + g.s_D);                 // [3][kTB][W]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + g.s_bar);             // [2]
+  int* misc = reinterpret_cast<int*>(smem + g.s_misc);
+  // misc: [0..1] anyon counts by step parity (rank 0), [2] wx, [3] wy (rank 0),
+  //       [4] next shot (rank 0), [5] abort (rank 0), [6] block scratch
+
+  uint8_t* slot = ws + (size_t)cid * g.slot;
+  auto plane = [&](int buf, int p) -> uint8_t* { return slot + ((size_t)(buf * 4 + p)) * LL; };
+  uint32_t* sig = reinterpret_cast<uint32_t*>(slot + g.o_sig);  // [frame][L][W]
+  auto sigf = [&](int frame) -> uint32_t* { return sig + (size_t)frame * L * W; };
+  uint32_t* flipb = reinterpret_cast<uint32_t*>(slot + g.o_flip);  // [par][frame][kind][L][W]
+  auto flip = [&](int par, int frame, int kind) -> uint32_t* {
+    return flipb + ((size_t)((par * 2 + frame) * 2 + kind)) * L * W;
+  };
+  uint32_t* Cb = reinterpret_cast<uint32_t*>(slot + g.o_C);  // [kind][L][W], x frame
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  if (tid < 8) misc[tid] = 0;
+  __syncthreads();
+  uint32_t phase[2] = {0u, 0u};
+  bool inflight[2] = {false, false};  // copies issued and not yet waited for (thread 0)
+
+  const int nbands = RL / kTB;
+  const int ntasks = 4 * nbands;
+  const uint32_t task_bytes = (uint32_t)(kTRows * L + kTRows * W * 4);
+
+  // issue the copies of task i (plane p, band b) of a step reading buffer `src`
+  auto issue = [&](int i, int src) {
+    const int p = i / nbands, b = i - p * nbands;
+    const int buf = i & 1;
+    const int R0 = r0 + b * kTB;
+    const uint8_t* P = plane(src, p);
+    const uint32_t* S = sigf(p < 2 ? 0 : 1);
+    fence_proxy_async_global();
+    inflight[buf] = true;
+    mbar_expect_tx(&bar[buf], task_bytes);
+    for (int j = 0; j < kTRows; ++j) {
+      const int R = twrap(R0 - 3 + j, L);
+      bulk_g2s(band + ((size_t)buf * kTRows + j) * L, P + (size_t)R * L, (uint32_t)L, &bar[buf]);
+      bulk_g2s(sband + ((size_t)buf * kTRows + j) * W, S + (size_t)R * W, (uint32_t)(W * 4),
+               &bar[buf]);
+    }
+  };
+
+  auto next_work = [&](int64_t prev) -> int64_t {
+    if (!a.queue) return prev < 0 ? (int64_t)cid : prev + nclusters;
+    if (rank == 0 && tid == 0) misc[4] = (int)atomicAdd(a.queue, 1u);
+    cluster.sync();
+    const int64_t k = (int64_t)*rank_ptr(&misc[4], 0);
+    cluster.sync();
+    return k;
+  };
+
+  bool aborted = false;
+  for (int64_t k = next_work(-1); k < a.shots && !aborted; k = next_work(k)) {
+    const int64_t shot = a.shot_list ? (int64_t)a.shot_list[k] : k;
+    const uint8_t* N = a.in + shot_offset_of(a, shot);
+
+    // ---- init (own rows): empty planes, cleared maps, sigma in the x frame
+    {
+      for (int p = 0; p < 4; ++p) {
+        uint32_t* P = reinterpret_cast<uint32_t*>(plane(0, p)) + (size_t)r0 * cols;
+        for (int i = tid; i < RL * cols; i += nt) P[i] = 0xFFFFFFFFu;
+      }
+      for (int par = 0; par < 2; ++par)
+        for (int fr = 0; fr < 2; ++fr)
+          for (int kd = 0; kd < 2; ++kd) {
+            uint32_t* F = flip(par, fr, kd) + (size_t)r0 * W;
+            for (int i = tid; i < RL * W; i += nt) F[i] = 0;
+          }
+      for (int kd = 0; kd < 2; ++kd) {
+        uint32_t* C = Cb + (size_t)kd * L * W + (size_t)r0 * W;
+        for (int i = tid; i < RL * W; i += nt) C[i] = 0;
+      }
+      // sigma (Def. synch_ccqs: parity of the four links incident to r)
+      uint32_t* Sx = sigf(0);
+      int cnt = 0;
+      for (int i = tid; i < RL * W; i += nt) {
+        const int y = r0 + i / W, x0 = (i % W) * 32;
+        uint32_t bits = 0;
+        if (a.from_sigma) {
+          const uint8_t* row = N + (size_t)y * L + x0;
+          for (int q = 0; q < 32; q += 4) {
+            const uint32_t w = *reinterpret_cast<const uint32_t*>(row + q);
+            const uint32_t nz = (((w & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w) & 0x80808080u;
+            bits |= nibble_of_bytes(nz >> 7) << q;
+          }
+        } else {
+          const uint8_t* ex = N + (size_t)y * L + x0;
+          const uint8_t* ey = N + LL + (size_t)y * L + x0;
+          const uint8_t* eyd = N + LL + (size_t)twrap(y - 1, L) * L + x0;
+          uint32_t bx = 0, by = 0, byd = 0;
+          for (int q = 0; q < 32; q += 4) {
+            bx |= nibble_of_bytes(*reinterpret_cast<const uint32_t*>(ex + q)) << q;
+            by |= nibble_of_bytes(*reinterpret_cast<const uint32_t*>(ey + q)) << q;
+            byd |= nibble_of_bytes(*reinterpret_cast<const uint32_t*>(eyd + q)) << q;
+          }
+          const uint32_t left = N[(size_t)y * L + twrap(x0 - 1, L)] & 1u;  // e_x(r - x^)
+          bits = bx ^ ((bx << 1) | left) ^ by ^ byd;
+        }
+        Sx[(size_t)y * W + (i % W)] = bits;
+        cnt += __popc(bits);
+      }
+      fence_proxy_async_global();
+      cluster.sync();  // the x-frame sigma of every row is written
+      // y-frame sigma of the own rows (x = r0 .. r0 + RL - 1) by 32 x 32 bit
+      // transposes: lane i loads row y = 32 wy + i, ballot j gives column x
+      uint32_t* Sy = sigf(1);
+      const int qlo = r0 >> 5, nq = ((r0 + RL - 1) >> 5) - qlo + 1;
+      for (int blk = warp; blk < W * nq; blk += nw) {
+        const int wy = blk / nq, qx = qlo + blk % nq;
+        const uint32_t v = Sx[(size_t)(32 * wy + lane) * W + qx];
+        uint32_t mine = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const uint32_t col = __ballot_sync(0xFFFFFFFFu, (v >> j) & 1u);
+          if (lane == j) mine = col;
+        }
+        const int x = 32 * qx + lane;
+        if (x >= r0 && x < r0 + RL) Sy[(size_t)x * W + wy] = mine;
+      }
+      // anyon count of the own x-frame rows, summed on rank 0
+      for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+      if (lane == 0 && cnt) atomicAdd(rank_ptr(&misc[1], 0), cnt);
+      fence_proxy_async_global();
+      cluster.sync();
+    }
+    int any = *rank_ptr(&misc[1], 0);
+
+    int t = 0, flag = 0;
+    while (any) {
+      if (t >= a.max_steps) {
+        flag = 2;
+        break;
+      }
+      const int src = t & 1, dst = src ^ 1;
+      // ================= 1. messages: bands staged by bulk copies
+      if (tid == 0) issue(0, src);
+      for (int i = 0; i < ntasks; ++i) {
+        if (tid == 0 && i + 1 < ntasks && !aborted) issue(i + 1, src);
+        const int buf = i & 1;
+        const bool ok = mbar_wait_bounded(&bar[buf], phase[buf]);
+        if (ok) {
+          phase[buf] ^= 1u;
+          inflight[buf] = false;
+        }
+        if (__syncthreads_or(!ok)) {
+          aborted = true;
+          break;
+        }
+        const int p = i / nbands, b = i - p * nbands;
+        const int R0 = r0 + b * kTB;
+        const uint8_t* Bk = band + (size_t)buf * kTRows * L;
+        const uint32_t* Sb = sband + (size_t)buf * kTRows * W;
+        // dilated syndrome rows D_d(R) = OR_{|j| <= d} sigma(R + j), d = 1, 2, 3
+        for (int idx = tid; idx < kTB * W; idx += nt) {
+          const int r = idx / W, w = idx - r * W;
+          const uint32_t* c = Sb + (size_t)(r + 3) * W + w;
+          const uint32_t d1 = c[-W] | c[0] | c[W];
+          const uint32_t d2 = d1 | c[-2 * W] | c[2 * W];
+          const uint32_t d3 = d2 | c[-3 * W] | c[3 * W];
+          D[(size_t)r * W + w] = d1;
+          D[(size_t)(kTB + r) * W + w] = d2;
+          D[(size_t)(2 * kTB + r) * W + w] = d3;
+        }
+        // transverse window min over 7 rows, rolling down the band
+        for (int kc = tid; kc < cols; kc += nt) {
+          const uint32_t* col = reinterpret_cast<const uint32_t*>(Bk) + kc;
+          uint32_t hi[7], lo[7];
+#pragma unroll
+          for (int j = 0; j < 6; ++j) {
+            const uint32_t w = col[(size_t)j * cols];
+            hi[j] = w & 0xFF00FF00u;
+            lo[j] = w & 0x00FF00FFu;
+          }
+#pragma unroll 4
+          for (int r = 0; r < kTB; ++r) {
+            const uint32_t w = col[(size_t)(r + 6) * cols];
+            hi[6] = w & 0xFF00FF00u;
+            lo[6] = w & 0x00FF00FFu;
+            uint32_t mh = __vminu2(__vminu2(__vminu2(hi[0], hi[1]), __vminu2(hi[2], hi[3])),
+                                   __vminu2(__vminu2(hi[4], hi[5]), hi[6]));
+            uint32_t ml = __vminu2(__vminu2(__vminu2(lo[0], lo[1]), __vminu2(lo[2], lo[3])),
+                                   __vminu2(__vminu2(lo[4], lo[5]), lo[6]));
+            M[(size_t)r * cols + kc] = mh | ml;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+              hi[j] = hi[j + 1];
+              lo[j] = lo[j + 1];
+            }
+          }
+        }
+        __syncthreads();
+        // shift by 3 sites along the byte axis, +3 (saturating), anyon terms
+        const bool plus = (p % 2) == 0;  // m^{+a} reads from r - 3 a^
+        uint32_t* out = reinterpret_cast<uint32_t*>(plane(dst, p)) + (size_t)R0 * cols;
+        const uint32_t v1 = (uint32_t)(g.off) * 0x01010101u;
+        for (int idx = tid; idx < kTB * cols; idx += nt) {
+          const int r = idx / cols, kc = idx - r * cols;
+          const uint32_t* Mr = M + (size_t)r * cols;
+          uint32_t s;
+          if (plus) {
+            const int km = kc == 0 ? cols - 1 : kc - 1;
+            s = __funnelshift_r(Mr[km], Mr[kc], 8);
+          } else {
+            const int kp = kc + 1 == cols ? 0 : kc + 1;
+            s = __funnelshift_r(Mr[kc], Mr[kp], 24);
+          }
+          uint32_t v = vmin4(s, 0xFCFCFCFCu) + 0x03030303u;
+          // terms: the smallest d wins (d = 3 first, overwritten by smaller d)
+          uint32_t T = 0xFFFFFFFFu;
+#pragma unroll
+          for (int d = 3; d >= 1; --d) {
+            const int pos = twrap(4 * kc + (plus ? -d : d), L);
+            const uint32_t m = nib_mask(bits4(D + (size_t)((d - 1) * kTB + r) * W, W, pos));
+            T = (T & ~m) | ((v1 + (uint32_t)(d - 1) * 0x01010101u) & m);
+          }
+          out[(size_t)r * cols + kc] = vmin4(v, T);
+        }
+        __syncthreads();  // M, D and the band buffer are free again
+      }
+      fence_proxy_async_global();
+      if (aborted && tid == 0) atomicOr(rank_ptr(&misc[5], 0), 1);
+      cluster.sync();  // every plane of the new buffer is complete
+      // ================= 2. forces and feedback for the anyons of own x-frame rows
+      const int par = t & 1;
+      if (!*rank_ptr(&misc[5], 0)) {
+        const uint8_t* Ppx = plane(dst, 0);
+        const uint8_t* Pmx = plane(dst, 1);
+        const uint8_t* Ppy = plane(dst, 2);
+        const uint8_t* Pmy = plane(dst, 3);
+        const uint32_t* Sx = sigf(0);
+        uint64_t kstep = 0;
+        if (a.move_thr) kstep = move_step_key(a.move_key, a.shot_offset + shot, t);
+        for (int i = tid; i < RL * W; i += nt) {
+          const int y = r0 + i / W, wq = i % W;
+          uint32_t bits = Sx[(size_t)y * W + wq];
+          while (bits) {
+            const int bpos = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int x = wq * 32 + bpos;
+            int dir = tiled_dir(Ppx[(size_t)y * L + x], Pmx[(size_t)y * L + x],
+                                Ppy[(size_t)x * L + y], Pmy[(size_t)x * L + y]);
+            if (a.move_thr) {
+              const uint64_t u = splitmix64(kstep ^ (uint64_t)((int64_t)y * L + x));
+              if (u < a.move_thr) dir = 1 + (int)(splitmix64(u) >> 62);
+            }
+            if (!dir) continue;
+            const int kind = (dir <= 2) ? 0 : 1;
+            const int lx = (dir == 2) ? twrap(x - 1, L) : x;
+            const int ly = (dir == 4) ? twrap(y - 1, L) : y;
+            atomicOr(flip(par, 0, kind) + (size_t)ly * W + (lx >> 5), 1u << (lx & 31));
+            atomicOr(flip(par, 1, kind) + (size_t)lx * W + (ly >> 5), 1u << (ly & 31));
+          }
+        }
+      }
+      cluster.sync();  // flipped-link maps complete
+      // ================= 3. sigma and correction from the flipped links
+      int cnt = 0;
+      if (!*rank_ptr(&misc[5], 0)) {
+        for (int fr = 0; fr < 2; ++fr) {
+          // frame 0: rows y, kind 0 (x links) along the row, kind 1 (y links) across rows;
+          // frame 1: rows x, kind 1 along the row, kind 0 across rows
+          const uint32_t* Fa = flip(par, fr, fr == 0 ? 0 : 1);  // links along the row
+          const uint32_t* Fc = flip(par, fr, fr == 0 ? 1 : 0);  // links across rows
+          uint32_t* S = sigf(fr);
+          for (int i = tid; i < RL * W; i += nt) {
+            const int R = r0 + i / W, wq = i % W;
+            const int Rm = twrap(R - 1, L), wm = wq == 0 ? W - 1 : wq - 1;
+            const uint32_t fa = Fa[(size_t)R * W + wq];
+            const uint32_t fa_prev = Fa[(size_t)R * W + wm];
+            const uint32_t along = fa ^ ((fa << 1) | (fa_prev >> 31));
+            const uint32_t fc = Fc[(size_t)R * W + wq];
+            const uint32_t across = fc ^ Fc[(size_t)Rm * W + wq];
+            const uint32_t s = S[(size_t)R * W + wq] ^ along ^ across;
+            S[(size_t)R * W + wq] = s;
+            if (fr == 0) {
+              cnt += __popc(s);
+              Cb[(size_t)R * W + wq] ^= fa;                       // x links
+              Cb[(size_t)L * W + (size_t)R * W + wq] ^= fc;       // y links
+            }
+          }
+        }
+        // the other parity's maps (read last step, written next step): clear own rows
+        for (int fr = 0; fr < 2; ++fr)
+          for (int kd = 0; kd < 2; ++kd) {
+            uint32_t* F = flip(par ^ 1, fr, kd) + (size_t)r0 * W;
+            for (int i = tid; i < RL * W; i += nt) F[i] = 0;
+          }
+      }
+      for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+      if (lane == 0 && cnt) atomicAdd(rank_ptr(&misc[par], 0), cnt);
+      fence_proxy_async_global();
+      cluster.sync();
+      ++t;
+      any = *rank_ptr(&misc[par], 0);
+      if (*rank_ptr(&misc[5], 0)) {
+        aborted = true;
+        flag = 3;
+        break;
+      }
+      // rank 0 clears the counter of the next step (last read a step ago)
+      if (rank == 0 && tid == 0) misc[par ^ 1] = 0;
+    }
+    if (aborted) {
+      // copies may still be in flight: wait for them (bounded) before leaving
+      if (tid == 0)
+        for (int b2 = 0; b2 < 2; ++b2)
+          if (inflight[b2]) (void)mbar_wait_bounded(&bar[b2], phase[b2]);
+      __syncthreads();
+      flag = 3;
+    }
+    // ================= outputs: correction bytes, homology, steps, flag
+    uint8_t* outC = a.out_C + correction_offset_of(a, shot);
+    for (int kd = 0; kd < 2; ++kd) {
+      const uint32_t* C = Cb + (size_t)kd * L * W;
+      for (int i = tid; i < RL * (L / 4); i += nt) {
+        const int y = r0 + i / (L / 4), x = (i % (L / 4)) * 4;
+        const uint32_t nib = (C[(size_t)y * W + (x >> 5)] >> (x & 31)) & 0xFu;
+        *reinterpret_cast<uint32_t*>(outC + (size_t)kd * LL + (size_t)y * L + x) =
+            (nib * 0x00204081u) & 0x01010101u;
+      }
+    }
+    int wx = 0, wy = 0;
+    for (int y = r0 + tid; y < r0 + RL; y += nt) {  // e_x((0, y))
+      wx ^= (int)(Cb[(size_t)y * W] & 1u);
+      if (!a.from_sigma) wx ^= N[(size_t)y * L];
+    }
+    if (rank == 0) {
+      for (int x = tid; x < L; x += nt) {  // e_y((x, 0))
+        wy ^= (int)((Cb[(size_t)L * W + (x >> 5)] >> (x & 31)) & 1u);
+        if (!a.from_sigma) wy ^= N[LL + x];
+      }
+    }
+    wx = __reduce_xor_sync(0xFFFFFFFFu, wx);
+    wy = __reduce_xor_sync(0xFFFFFFFFu, wy);
+    if (lane == 0) {
+      if (wx) atomicXor(rank_ptr(&misc[2], 0), 1);
+      if (wy) atomicXor(rank_ptr(&misc[3], 0), 1);
+    }
+    cluster.sync();
+    if (rank == 0 && tid == 0) {
+      a.out_steps[shot] = t;
+      if (a.from_sigma) {
+        a.out_cut[2 * shot] = (uint8_t)misc[2];
+        a.out_cut[2 * shot + 1] = (uint8_t)misc[3];
+        if (a.out_exhausted) a.out_exhausted[shot] = (uint8_t)(flag == 2);
+      } else {
+        a.out_flag[shot] = (uint8_t)(flag >= 2 ? flag : ((misc[2] | misc[3]) ? 1 : 0));
+      }
+      misc[0] = misc[1] = misc[2] = misc[3] = 0;
+    }
+    cluster.sync();  // counters reset before the next shot's init
+  }
+  // no CTA leaves while a partner could still reach its shared memory
+  cluster.sync();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host ----
+
+namespace {
+
+// Kernel-path overrides per L (qca_set_kernel_path): -1 automatic.
+int g_path_override[QCA_MAX_L + 1];
+std::once_flag g_override_once;
+
+void init_overrides() {
+  for (int i = 0; i <= QCA_MAX_L; ++i) g_path_override[i] = -1;
+}
+
+bool tiled_geom(int L, int m_max, TiledGeom& g) {
+  if (L % 128 != 0 || L < 128 || L > QCA_MAX_L || m_max < 3 || m_max > 255) return false;
+  g.L = L;
+  g.W = L / 32;
+  g.RL = L / kTCL;
+  g.cols = L / 4;
+  g.off = 255 - m_max;
+  g.LL = (size_t)L * L;
+  const size_t bm = (size_t)L * g.W * 4;  // one bitmap, bytes
+  g.o_sig = 8 * g.LL;
+  g.o_flip = g.o_sig + 2 * bm;
+  g.o_C = g.o_flip + 8 * bm;
+  g.slot = ((g.o_C + 2 * bm) + 255) & ~(size_t)255;
+  size_t o = 0;
+  g.s_band = o;
+  o += 2 * (size_t)kTRows * L;
+  g.s_sband = o;
+  o += 2 * (size_t)kTRows * g.W * 4;
+  g.s_M = o;
+  o += (size_t)kTB * g.cols * 4;
+  g.s_D = o;
+  o += 3 * (size_t)kTB * g.W * 4;
+  o = (o + 15) & ~(size_t)15;
+  g.s_bar = o;
+  o += 16;
+  g.s_misc = o;
+  o += 64;
+  g.smem = o;
+  return true;
+}
+
+struct TiledWorkspace {
+  uint8_t* ptr = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t done = nullptr;
+};
+std::mutex g_tws_mu;
+TiledWorkspace g_tws[64];
+
+struct TiledShape {
+  int dev;
+  size_t smem;
+  int clusters;
+};
+std::mutex g_tshape_mu;
+std::vector<TiledShape> g_tshapes;
+
+}  // namespace
+
+int tiled_path_for(int L, int v, int m_max) {
+  std::call_once(g_override_once, init_overrides);
+  if (v != 3) return 0;
+  TiledGeom g;
+  if (!tiled_geom(L, m_max, g)) return 0;
+  const int ov = g_path_override[L];
+  if (ov == 3) return 1;
+  if (ov == 0) return 0;
+  return L > 256 ? 1 : 0;
+}
+
+int generic_forced(int L) {
+  std::call_once(g_override_once, init_overrides);
+  return (L >= 3 && L <= QCA_MAX_L && g_path_override[L] == 0) ? 1 : 0;
+}
+
+int launch_tiled(const DecodeArgs& a, cudaStream_t stream) {
+  if (a.shots == 0) return QCA_OK;
+  TiledGeom g;
+  if (a.v != 3 || !tiled_geom(a.L, a.m_max, g)) {
+    set_error("no tiled kernel for L=%d v=%d m_max=%d", a.L, a.v, a.m_max);
+    return QCA_ERR_UNSUPPORTED;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) {
+    set_error("device index %d out of range", dev);
+    return QCA_ERR_UNSUPPORTED;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kTCL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.blockDim = dim3(kTThreads);
+  cfg.dynamicSmemBytes = g.smem;
+  cfg.stream = stream;
+  int clusters = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_tshape_mu);
+    for (const TiledShape& s : g_tshapes)
+      if (s.dev == dev && s.smem == g.smem) clusters = s.clusters;
+  }
+  e = cudaFuncSetAttribute(tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)g.smem);
+  if (e != cudaSuccess) return cuda_fail(e, "tiled sweep smem attribute");
+  if (clusters < 0) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cfg.gridDim = dim3((unsigned)(kTCL * sms));
+    e = cudaOccupancyMaxActiveClusters(&clusters, tiled_kernel, &cfg);
+    if (e != cudaSuccess) return cuda_fail(e, "tiled cluster occupancy query");
+    if (clusters < 1) {
+      set_error("tiled sweep cluster does not fit (L=%d)", a.L);
+      return QCA_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lk(g_tshape_mu);
+    g_tshapes.push_back({dev, g.smem, clusters});
+  }
+  int64_t grid = clusters;
+  if (grid > a.shots) grid = a.shots;
+  const size_t need = g.slot * (size_t)grid;
+  std::lock_guard<std::mutex> lk(g_tws_mu);
+  TiledWorkspace& w = g_tws[dev];
+  if (w.bytes < need) {
+    // the previous workspace may still be in use by queued work on any stream
+    if (w.ptr) {
+      e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) return cuda_fail(e, "synchronise before workspace growth");
+      cudaFree(w.ptr);
+      w.ptr = nullptr;
+      w.bytes = 0;
+    }
+    e = cudaMalloc(&w.ptr, need);
+    if (e != cudaSuccess) return cuda_fail(e, "tiled workspace allocation");
+    w.bytes = need;
+  }
+  if (!w.done) {
+    e = cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "event creation");
+  }
+  // launches on different streams share the workspace: order them
+  e = cudaStreamWaitEvent(stream, w.done, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "stream wait");
+  cfg.gridDim = dim3((unsigned)(grid * kTCL));
+  e = cudaLaunchKernelEx(&cfg, tiled_kernel, a, g, w.ptr);
+  if (e != cudaSuccess) return cuda_fail(e, "tiled sweep launch");
+  return cuda_fail(cudaEventRecord(w.done, stream), "event record");
+}
+
+int tiled_workspace_release() {
+  std::lock_guard<std::mutex> lk(g_tws_mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !g_tws[dev].ptr) return QCA_OK;
+  cudaError_t e = cudaFree(g_tws[dev].ptr);
+  g_tws[dev].ptr = nullptr;
+  g_tws[dev].bytes = 0;
+  return cuda_fail(e, "tiled workspace free");
+}
+
+}  // namespace qca
+
+using namespace qca;
+
+extern "C" int qca_set_kernel_path(int L, int path) {
+  std::call_once(g_override_once, init_overrides);
+  if (L < 3 || L > QCA_MAX_L || (path != -1 && path != 0 && path != 3)) {
+    set_error("qca_set_kernel_path: L=%d path=%d (allowed: -1 automatic, 0 generic, 3 tiled)", L,
+              path);
+    return QCA_ERR_ARG;
+  }
+  TiledGeom g;
+  if (path == 3 && !tiled_geom(L, 255, g)) {
+    set_error("qca_set_kernel_path: the tiled kernel needs L a multiple of 128 (L=%d)", L);
+    return QCA_ERR_UNSUPPORTED;
+  }
+  g_path_override[L] = path;
+  return QCA_OK;
+}

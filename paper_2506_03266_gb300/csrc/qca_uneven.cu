@@ -240,8 +240,7 @@ int qca_decode_uneven_async(qca_uneven_plan_t p, const uint8_t* errors, int max_
     a.shot_list = p->d_list + p->start[i];
     a.offsets = p->d_offsets;
     a.queue = p->d_counters + i;
-    rc = fast_path_for(a.L, a.v, a.m_max) > 0 ? launch_fast(a, p->side[i])
-                                                : launch_generic(a, p->side[i]);
+    rc = launch_decode(a, p->side[i]);
     if (rc) return rc;
     e = cudaEventRecord(p->join[i], p->side[i]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->join[i], 0);
