@@ -302,6 +302,23 @@ int qca_net_logits_async(qca_net_t net, const uint8_t* noise, int L, int64_t sho
 int qca_net_predecode_async(qca_net_t net, const uint8_t* noise, int L, int64_t shots,
                             uint8_t* out_residual, uint8_t* out_c0, void* stream);
 
+/* FP8 (E4M3) form of the net.  Layers 2-4 run on e4m3 tensor-core MMAs with
+ * fp32 accumulation: weights quantised per output channel as e4m3(W / s_co),
+ * s_co = max|W_co| / 448 (fp32; 1 for an all-zero channel), each layer's input
+ * quantised as e4m3(x / s_l) with per-layer activation scales s_1..s_3
+ * (round to nearest even, saturating at 448); layer 1 is the bf16 form's.
+ * qca_net_calibrate_fp8 sets s_l = max(activation) / 448 from the bf16 form's
+ * activations on the given noise (device uint8 [shots][2][L][L]; at most one
+ * inference chunk of it is used); synchronous.  qca_net_set_fp8_scales sets
+ * them directly (three positive floats, HOST), qca_net_get_fp8_scales reads
+ * them.  qca_net_set_precision(net, 1) makes every inference entry point
+ * (logits, pre-decode, net + automaton decode) use the FP8 form, 0 the bf16
+ * form; FP8 needs scales first (QCA_ERR_ARG otherwise). */
+int qca_net_calibrate_fp8(qca_net_t net, const uint8_t* noise, int L, int64_t shots, void* stream);
+int qca_net_set_fp8_scales(qca_net_t net, const float* scales);
+int qca_net_get_fp8_scales(qca_net_t net, float* scales);
+int qca_net_set_precision(qca_net_t net, int precision);
+
 /* Net + automaton: pre-decode, run qca_decode_batch_async on the residual
  * N xor C0 (arguments as there), then out_correction = C0 xor C_automaton.
  * out_steps counts the automaton's steps; out_logical_fail is the failure

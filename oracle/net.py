@@ -127,3 +127,58 @@ def pairing_links(anyon: np.ndarray, prop: np.ndarray) -> np.ndarray:
     C0[0] = ((prop == 0) & (np.roll(prop, -1, axis=1) == 1)).astype(np.uint8)
     C0[1] = ((prop == 2) & (np.roll(prop, -1, axis=0) == 3)).astype(np.uint8)
     return C0
+
+
+# ---------------------------------------------------------------- FP8 form
+
+E4M3_MAX = 448.0
+
+
+def e4m3_round(x: np.ndarray) -> np.ndarray:
+    """Round to the nearest FP8 E4M3 value (ties to even), saturating at +-448.
+
+    E4M3: 4 exponent bits (bias 7), 3 mantissa bits, subnormals down to 2^-9,
+    largest finite value 1.75 * 2^8 = 448.  Returned as float64."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    _, E = np.frexp(a)                  # a = m 2^E, m in [0.5, 1)
+    e = np.maximum(E - 1, -6)           # binade exponent, subnormals share 2^-6's quantum
+    quantum = np.ldexp(1.0, e - 3)
+    q = np.round(a / quantum) * quantum  # numpy rounds halves to even
+    q = np.minimum(q, E4M3_MAX)
+    return np.where(x < 0, -q, q)
+
+
+def fp8_weight_scales(W: np.ndarray) -> np.ndarray:
+    """Per output channel: amax over (c_in, taps) / 448 in float32 (1 if the
+    channel is all zero)."""
+    amax = np.max(np.abs(W.astype(np.float32)).reshape(W.shape[0], -1), axis=1)
+    s = (amax / np.float32(E4M3_MAX)).astype(np.float32)
+    return np.where(amax > 0, s, np.float32(1.0)).astype(np.float32)
+
+
+def fp8_weights(W: np.ndarray) -> np.ndarray:
+    """Per-channel scaled E4M3 weights, dequantised: e4m3(W / s_co) * s_co with
+    the division in float32."""
+    W32 = W.astype(np.float32)
+    s = fp8_weight_scales(W32)
+    q = e4m3_round((W32 / s[:, None, None, None]).astype(np.float32))
+    return q * s.astype(np.float64)[:, None, None, None]
+
+
+def forward_fp8(anyon: np.ndarray, params: np.ndarray, act_scales) -> np.ndarray:
+    """Logits [4][L][L] of the FP8 form: layer 1 as the bf16 form (exact inputs,
+    bf16 weights); layers 2-4 with per-channel E4M3 weights and E4M3 inputs
+    quantised per layer as e4m3(x / s) * s, s = act_scales[layer - 2]."""
+    layers = unpack(params)
+    x = np.stack([anyon.astype(np.float64), np.ones_like(anyon, dtype=np.float64)])
+    for i, (W, b) in enumerate(layers):
+        if i == 0:
+            x = conv3x3_circular(x, bf16_round(W), b)
+        else:
+            s = float(np.float32(act_scales[i - 1]))
+            xq = e4m3_round(x / s) * s
+            x = conv3x3_circular(xq, fp8_weights(W), b)
+        if i < len(layers) - 1:
+            x = np.maximum(x, 0.0)
+    return x

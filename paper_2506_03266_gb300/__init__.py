@@ -90,6 +90,10 @@ def lib():
                                ctypes.c_float, vp], i32),
             "qca_net_labels_async": ([vp, i32, i64, vp, vp, vp], i32),
             "qca_net_chunk_shots": ([i32], i64),
+            "qca_net_calibrate_fp8": ([vp, vp, i32, i64, vp], i32),
+            "qca_net_set_fp8_scales": ([vp, vp], i32),
+            "qca_net_get_fp8_scales": ([vp, vp], i32),
+            "qca_net_set_precision": ([vp, i32], i32),
             "qca_net_logits_async": ([vp, vp, i32, i64, vp, vp], i32),
             "qca_net_predecode_async": ([vp, vp, i32, i64, vp, vp, vp], i32),
             "qca_net_decode_batch_async": ([vp, vp, i32, i64, i32, u64, vp, vp, vp, cfgp, vp,
@@ -427,6 +431,30 @@ class Net:
                                    seed & (2**64 - 1), float(lr),
                                    losses.ctypes.data_as(ctypes.c_void_p)))
         return losses[:iterations]
+
+    def calibrate_fp8(self, errors, stream=None):
+        """Per-layer activation scales of the FP8 form from these noise realisations."""
+        torch = _torch()
+        shots, L = errors.shape[0], errors.shape[-1]
+        _dev_u8(torch, errors, (shots, 2, L, L), "errors")
+        _check(lib().qca_net_calibrate_fp8(self.handle, ctypes.c_void_p(errors.data_ptr()), L,
+                                           shots, _stream(torch, stream)))
+        return self.fp8_scales()
+
+    def fp8_scales(self):
+        import numpy as np
+        out = np.zeros(3, dtype=np.float32)
+        _check(lib().qca_net_get_fp8_scales(self.handle, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def set_fp8_scales(self, scales):
+        import numpy as np
+        a = np.ascontiguousarray(scales, dtype=np.float32)
+        _check(lib().qca_net_set_fp8_scales(self.handle, a.ctypes.data_as(ctypes.c_void_p)))
+
+    def set_precision(self, precision: str):
+        """"bf16" or "fp8" for every inference entry point."""
+        _check(lib().qca_net_set_precision(self.handle, {"bf16": 0, "fp8": 1}[precision]))
 
     def logits(self, errors, stream=None):
         """fp32 [shots][4][L][L] logits of the noise realisations' syndromes."""

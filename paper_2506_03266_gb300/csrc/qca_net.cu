@@ -20,6 +20,7 @@
 // Training: fp32 kernels on the CUDA cores (forward, softmax cross-entropy,
 // backward data/weights, Adam).
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <math.h>
 #include <string.h>
 
@@ -553,6 +554,221 @@ __global__ void __launch_bounds__(128) conv_mma_kernel(
   }
 }
 
+// ------------------------------------------------------ inference (FP8) ----
+//
+// FP8 (E4M3) form of layers 2-4: weights quantised per output channel,
+// e4m3(W / s_co) with s_co = amax_co / 448; each layer's input quantised per
+// layer, e4m3(x / s_in), with calibrated scales; products accumulate in fp32 on
+// mma.sync m16n8k32 (e4m3 x e4m3), and the epilogue dequantises with
+// s_in * s_co.  Layer 1 stays on the CUDA cores as in the bf16 form.
+
+__device__ __forceinline__ uint16_t pack_e4m3x2(float lo, float hi) {
+  return (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(lo, hi), __NV_SATFINITE, __NV_E4M3);
+}
+
+// One CTA per (layer, output channel): 32 + 32 + 8 CTAs (layer 4 padded to 8
+// channels with zeros).  Wq layout per layer: [tap][co][ci] bytes.
+__global__ void prepare_fp8_kernel(const float* __restrict__ P, uint8_t* __restrict__ Wq,
+                                   float* __restrict__ wscale) {
+  const int b = blockIdx.x;
+  const int l = b < 32 ? 0 : (b < 64 ? 1 : 2);
+  const int co = b - 32 * l;
+  const int CO = l < 2 ? 32 : 8;
+  const bool real = l < 2 || co < 4;
+  const float* W = P + (l == 0 ? kW1 : (l == 1 ? kW2 : kW3)) + (size_t)co * 32 * 9;
+  __shared__ float red[32];
+  float amax = 0.f;
+  for (int i = threadIdx.x; i < 32 * 9; i += blockDim.x) amax = fmaxf(amax, real ? fabsf(W[i]) : 0.f);
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xFFFFFFFFu, amax, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    amax = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xFFFFFFFFu, amax, o));
+    if (threadIdx.x == 0) red[0] = amax;
+  }
+  __syncthreads();
+  amax = red[0];
+  const float s = amax > 0.f ? amax / 448.f : 1.f;
+  uint8_t* out = Wq + (size_t)l * 9 * 32 * 32;
+  for (int i = threadIdx.x; i < 32 * 9; i += blockDim.x) {
+    const int ci = i / 9, tap = i % 9;
+    const float q = real ? W[i] / s : 0.f;
+    out[((size_t)tap * CO + co) * 32 + ci] =
+        (uint8_t)__nv_cvt_float_to_fp8(q, __NV_SATFINITE, __NV_E4M3);
+  }
+  if (threadIdx.x == 0) wscale[l * 32 + co] = s;
+}
+
+// layer 1 (CUDA cores) writing e4m3(relu(.) / s_out), 32 bytes per site
+__global__ void layer1_fp8_kernel(const uint8_t* __restrict__ sig, int L, int64_t shots,
+                                  const float* __restrict__ W1, const float* __restrict__ P,
+                                  float inv_s_out, uint8_t* __restrict__ out) {
+  __shared__ float sW[9][32];
+  __shared__ float sb[32];
+  for (int i = threadIdx.x; i < 32 * 9; i += blockDim.x) sW[i % 9][i / 9] = W1[(i / 9) * 18 + i % 9];
+  for (int co = threadIdx.x; co < 32; co += blockDim.x) {
+    float b = P[kB0 + co];
+    for (int tap = 0; tap < 9; ++tap) b += W1[co * 18 + 9 + tap];
+    sb[co] = b;
+  }
+  __syncthreads();
+  const int64_t LL = (int64_t)L * L;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < shots * LL;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / LL;
+    const int r = (int)(i - s * LL), x = r % L, y = r / L;
+    const uint8_t* g = sig + s * LL;
+    float acc[32];
+#pragma unroll
+    for (int co = 0; co < 32; ++co) acc[co] = sb[co];
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+      const int nb = wrapL(y + tap / 3 - 1, L) * L + wrapL(x + tap % 3 - 1, L);
+      if (g[nb]) {
+#pragma unroll
+        for (int co = 0; co < 32; ++co) acc[co] += sW[tap][co];
+      }
+    }
+    uint32_t w[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const uint32_t lo = pack_e4m3x2(fmaxf(acc[4 * c], 0.f) * inv_s_out,
+                                      fmaxf(acc[4 * c + 1], 0.f) * inv_s_out);
+      const uint32_t hi = pack_e4m3x2(fmaxf(acc[4 * c + 2], 0.f) * inv_s_out,
+                                      fmaxf(acc[4 * c + 3], 0.f) * inv_s_out);
+      w[c] = lo | (hi << 16);
+    }
+    uint4* o = reinterpret_cast<uint4*>(out + i * 32);
+    o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+  }
+}
+
+__device__ __forceinline__ void mma_e4m3(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int kW8Pitch = 12;  // words per [tap][co] row of 32 e4m3 weights (conflict-free)
+
+// FP8 implicit-GEMM conv: as conv_mma_kernel with 32 input channels of e4m3
+// (32 bytes per site) and one k32 step per tap.  acc * (s_in * s_co) + bias;
+// kActs writes e4m3(relu(.) * inv_s_out).
+template <int NT, int MODE>
+__global__ void __launch_bounds__(128) conv_fp8_kernel(
+    const uint8_t* __restrict__ in, const uint8_t* __restrict__ Wq,
+    const float* __restrict__ wscale, const float* __restrict__ bias, float s_in,
+    float inv_s_out, int L, int64_t shots, uint8_t* __restrict__ out,
+    float* __restrict__ logits, const uint8_t* __restrict__ sig, uint8_t* __restrict__ prop) {
+  constexpr int CO = 8 * NT;
+  __shared__ uint32_t sW[9 * CO * kW8Pitch];
+  __shared__ float sb[CO], sc[CO];
+  for (int i = threadIdx.x; i < 9 * CO * 8; i += blockDim.x)
+    sW[(i / 8) * kW8Pitch + (i % 8)] = reinterpret_cast<const uint32_t*>(Wq)[i];
+  for (int i = threadIdx.x; i < CO; i += blockDim.x) {
+    const bool real = MODE == kActs || i < 4;
+    sb[i] = real ? bias[i] : 0.f;
+    sc[i] = real ? s_in * wscale[i] : 0.f;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int64_t LL = (int64_t)L * L, S = shots * LL;
+  const int64_t tiles = (S + 15) / 16;
+  const uint32_t* inw = reinterpret_cast<const uint32_t*>(in);  // 8 words per site
+  for (int64_t tile = blockIdx.x * 4 + warp; tile < tiles; tile += (int64_t)gridDim.x * 4) {
+    const int64_t s0 = tile * 16;
+    int64_t site[2], shot[2];
+    int xs[2], ys[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      site[h] = s0 + g + 8 * h;
+      const int64_t scl = site[h] < S ? site[h] : S - 1;
+      shot[h] = scl / LL;
+      const int r = (int)(scl - shot[h] * LL);
+      xs[h] = r % L;
+      ys[h] = r / L;
+    }
+    float acc[NT][4];
+#pragma unroll
+    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+      int64_t nbw[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        nbw[h] = (shot[h] * LL + wrapL(ys[h] + dy, L) * L + wrapL(xs[h] + dx, L)) * 8;
+      uint32_t a[4];
+      a[0] = __ldg(inw + nbw[0] + t);      // row g,     k = 4t .. 4t+3
+      a[1] = __ldg(inw + nbw[1] + t);      // row g + 8
+      a[2] = __ldg(inw + nbw[0] + 4 + t);  // row g,     k = 16+4t ..
+      a[3] = __ldg(inw + nbw[1] + 4 + t);  // row g + 8
+#pragma unroll
+      for (int n = 0; n < NT; ++n) {
+        const uint32_t* wr = sW + (tap * CO + n * 8 + g) * kW8Pitch + t;
+        mma_e4m3(acc[n], a, wr[0], wr[4]);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const bool valid = site[h] < S;
+      const int r = ys[h] * L + xs[h];
+      if (MODE == kProposals) {
+        const float v0 = acc[0][2 * h] * sc[2 * t] + sb[2 * t];
+        const float v1 = acc[0][2 * h + 1] * sc[2 * t + 1] + sb[2 * t + 1];
+        const float w0 = __shfl_down_sync(0xFFFFFFFFu, v0, 1);
+        const float w1 = __shfl_down_sync(0xFFFFFFFFu, v1, 1);
+        if (t == 0 && valid) {
+          const float z[4] = {v0, v1, w0, w1};
+          float best = z[0];
+          int bk = 0;
+#pragma unroll
+          for (int q = 1; q < 4; ++q)
+            if (z[q] > best) {
+              best = z[q];
+              bk = q;
+            }
+          prop[site[h]] = (sig[site[h]] && best > 0.f) ? (uint8_t)bk : (uint8_t)4;
+        }
+        continue;
+      }
+      if (!valid) continue;
+#pragma unroll
+      for (int n = 0; n < NT; ++n) {
+        const int c0 = n * 8 + 2 * t;
+        const float v0 = acc[n][2 * h] * sc[c0] + sb[c0];
+        const float v1 = acc[n][2 * h + 1] * sc[c0 + 1] + sb[c0 + 1];
+        if (MODE == kLogits) {
+          float* lb = logits + shot[h] * 4 * LL + r;
+          if (c0 < 4) lb[(int64_t)c0 * LL] = v0;
+          if (c0 + 1 < 4) lb[(int64_t)(c0 + 1) * LL] = v1;
+        } else {
+          reinterpret_cast<uint16_t*>(out)[site[h] * 16 + c0 / 2] =
+              pack_e4m3x2(fmaxf(v0, 0.f) * inv_s_out, fmaxf(v1, 0.f) * inv_s_out);
+        }
+      }
+    }
+  }
+}
+
+// max over a bf16 activation buffer (values >= 0 after ReLU): float bits
+// compare as integers
+__global__ void amax_bf16_kernel(const __nv_bfloat16* __restrict__ a, int64_t n,
+                                 unsigned int* __restrict__ out) {
+  float m = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, __bfloat162float(a[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
 // Links whose two end anyons propose each other: e_x(r) iff prop(r) = +x and
 // prop(r + x^) = -x; e_y likewise.  residual = N xor C0; C0 written if given.
 __global__ void pairing_kernel(const uint8_t* __restrict__ N, const uint8_t* __restrict__ prop,
@@ -629,6 +845,13 @@ struct qca_net_s {
   __nv_bfloat16* wb = nullptr;     // bf16 weights of layers 2-4, [tap][co][ci]
   float* w1 = nullptr;             // layer 1 fp32 (bf16-rounded) [co][ci][tap]
   bool prepared = false;
+  // FP8 form: per-channel e4m3 weights of layers 2-4 ([tap][co][ci] bytes), their
+  // scales, the per-layer input scales (host), and the active precision
+  uint8_t* wq = nullptr;
+  float* wscale = nullptr;
+  float act_scale[3] = {0.f, 0.f, 0.f};
+  int precision = 0;  // 0 bf16, 1 fp8
+  bool prepared8 = false;
   // inference workspace
   uint8_t* ws = nullptr;
   size_t ws_bytes = 0;
@@ -664,6 +887,8 @@ int qca_net_create(uint64_t seed, qca_net_t* out) {
   if (e == cudaSuccess) e = cudaMalloc(&n->m2, sizeof(float) * kParams);
   if (e == cudaSuccess) e = cudaMalloc(&n->wb, sizeof(__nv_bfloat16) * (2 * 9 * 32 * 32 + 9 * 8 * 32));
   if (e == cudaSuccess) e = cudaMalloc(&n->w1, sizeof(float) * 32 * 2 * 9);
+  if (e == cudaSuccess) e = cudaMalloc(&n->wq, 2 * 9 * 32 * 32 + 9 * 8 * 32);
+  if (e == cudaSuccess) e = cudaMalloc(&n->wscale, sizeof(float) * 96);
   if (e == cudaSuccess) e = cudaMemcpy(n->params, h.data(), sizeof(float) * kParams, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(n->m1, 0, sizeof(float) * kParams);
   if (e == cudaSuccess) e = cudaMemset(n->m2, 0, sizeof(float) * kParams);
@@ -683,6 +908,8 @@ int qca_net_destroy(qca_net_t n) {
   cudaFree(n->m2);
   cudaFree(n->wb);
   cudaFree(n->w1);
+  cudaFree(n->wq);
+  cudaFree(n->wscale);
   cudaFree(n->ws);
   delete n;
   return QCA_OK;
@@ -703,6 +930,7 @@ int qca_net_set_params(qca_net_t n, const float* host, int64_t count) {
     return QCA_ERR_ARG;
   }
   n->prepared = false;
+  n->prepared8 = false;
   return cuda_fail(cudaMemcpy(n->params, host, sizeof(float) * kParams, cudaMemcpyHostToDevice),
                    "qca_net_set_params");
 }
@@ -801,6 +1029,7 @@ int qca_net_train(qca_net_t n, int L, int64_t iterations, int batch, double p_lo
   cudaFree(losses);
   cudaFree(counts);
   n->prepared = false;
+  n->prepared8 = false;
   return rc;
 }
 
@@ -861,6 +1090,12 @@ int net_run(qca_net_s* n, const uint8_t* noise, int L, int64_t shots, float* log
     if (e != cudaSuccess) return cuda_fail(e, "prepare weights");
     n->prepared = true;
   }
+  if (n->precision == 1 && !n->prepared8) {
+    prepare_fp8_kernel<<<72, 288, 0, st>>>(n->params, n->wq, n->wscale);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "prepare fp8 weights");
+    n->prepared8 = true;
+  }
   const int64_t LL = (int64_t)L * L;
   const int64_t chunk = net_chunk(L);
   int rc = net_workspace(n, (shots < chunk ? shots : chunk) * LL);
@@ -875,9 +1110,37 @@ int net_run(qca_net_s* n, const uint8_t* noise, int L, int64_t shots, float* log
     __nv_bfloat16* actB = actA + S * 32;
     const uint8_t* Nc = noise + c0s * 2 * LL;
     syndrome_kernel<<<grid_for(S, 256), 256, 0, st>>>(Nc, L, m, sig);
-    layer1_kernel<<<grid_for(S, 256), 256, 0, st>>>(sig, L, m, n->w1, n->params, actA);
     const int64_t tiles = (S + 15) / 16;
     const int gm = grid_for(tiles * 32, 128);
+    if (n->precision == 1) {
+      // FP8 form: e4m3 activations, 32 bytes per site, in the bf16 buffers
+      uint8_t* a8A = reinterpret_cast<uint8_t*>(actA);
+      uint8_t* a8B = a8A + S * 32;
+      const float* sa = n->act_scale;
+      layer1_fp8_kernel<<<grid_for(S, 256), 256, 0, st>>>(sig, L, m, n->w1, n->params,
+                                                          1.f / sa[0], a8A);
+      conv_fp8_kernel<4, kActs><<<gm, 128, 0, st>>>(a8A, n->wq, n->wscale, n->params + kB1,
+                                                    sa[0], 1.f / sa[1], L, m, a8B, nullptr,
+                                                    nullptr, nullptr);
+      conv_fp8_kernel<4, kActs><<<gm, 128, 0, st>>>(a8B, n->wq + 9 * 32 * 32, n->wscale + 32,
+                                                    n->params + kB2, sa[1], 1.f / sa[2], L, m,
+                                                    a8A, nullptr, nullptr, nullptr);
+      if (logits) {
+        conv_fp8_kernel<1, kLogits><<<gm, 128, 0, st>>>(
+            a8A, n->wq + 2 * 9 * 32 * 32, n->wscale + 64, n->params + kB3, sa[2], 0.f, L, m,
+            nullptr, logits + c0s * 4 * LL, nullptr, nullptr);
+      } else {
+        conv_fp8_kernel<1, kProposals><<<gm, 128, 0, st>>>(
+            a8A, n->wq + 2 * 9 * 32 * 32, n->wscale + 64, n->params + kB3, sa[2], 0.f, L, m,
+            nullptr, nullptr, sig, prop);
+        pairing_kernel<<<grid_for(S, 256), 256, 0, st>>>(Nc, prop, L, m, resid + c0s * 2 * LL,
+                                                         c0 ? c0 + c0s * 2 * LL : nullptr);
+      }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e, "net fp8 inference kernels");
+      continue;
+    }
+    layer1_kernel<<<grid_for(S, 256), 256, 0, st>>>(sig, L, m, n->w1, n->params, actA);
     conv_mma_kernel<4, kActs><<<gm, 128, 0, st>>>(actA, n->wb, n->params + kB1, L, m, actB,
                                                   nullptr, nullptr, nullptr);
     conv_mma_kernel<4, kActs><<<gm, 128, 0, st>>>(actB, n->wb + 9 * 32 * 32, n->params + kB2, L, m,
@@ -929,6 +1192,87 @@ int qca_net_predecode_async(qca_net_t n, const uint8_t* noise, int L, int64_t sh
   }
   if (shots == 0) return QCA_OK;
   return net_run(n, noise, L, shots, nullptr, out_residual, out_c0, (cudaStream_t)stream);
+}
+
+int qca_net_set_fp8_scales(qca_net_t n, const float* scales) {
+  if (!n || !scales || !(scales[0] > 0.f && scales[1] > 0.f && scales[2] > 0.f)) {
+    set_error("qca_net_set_fp8_scales: NULL or non-positive scale");
+    return QCA_ERR_ARG;
+  }
+  for (int i = 0; i < 3; ++i) n->act_scale[i] = scales[i];
+  return QCA_OK;
+}
+
+int qca_net_get_fp8_scales(qca_net_t n, float* scales) {
+  if (!n || !scales) {
+    set_error("qca_net_get_fp8_scales: NULL argument");
+    return QCA_ERR_ARG;
+  }
+  for (int i = 0; i < 3; ++i) scales[i] = n->act_scale[i];
+  return QCA_OK;
+}
+
+int qca_net_set_precision(qca_net_t n, int precision) {
+  if (!n || (precision != 0 && precision != 1)) {
+    set_error("qca_net_set_precision: precision must be 0 (bf16) or 1 (fp8)");
+    return QCA_ERR_ARG;
+  }
+  if (precision == 1 && !(n->act_scale[0] > 0.f && n->act_scale[1] > 0.f && n->act_scale[2] > 0.f)) {
+    set_error("qca_net_set_precision: fp8 needs activation scales (calibrate or set them)");
+    return QCA_ERR_ARG;
+  }
+  n->precision = precision;
+  return QCA_OK;
+}
+
+int qca_net_calibrate_fp8(qca_net_t n, const uint8_t* noise, int L, int64_t shots, void* stream) {
+  if (!n || L < 4 || L > QCA_MAX_L || shots < 1 || !noise) {
+    set_error("qca_net_calibrate_fp8: bad arguments");
+    return QCA_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!n->prepared) {
+    prepare_weights_kernel<<<64, 256, 0, st>>>(n->params, n->wb, n->w1);
+    n->prepared = true;
+  }
+  const int64_t LL = (int64_t)L * L;
+  const int64_t m = shots < net_chunk(L) ? shots : net_chunk(L);
+  int rc = net_workspace(n, m * LL);
+  if (rc) return rc;
+  unsigned int* amax = nullptr;
+  cudaError_t e = cudaMalloc(&amax, 3 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(amax, 0, 3 * sizeof(unsigned int), st);
+  if (e != cudaSuccess) {
+    cudaFree(amax);
+    return cuda_fail(e, "calibration buffer");
+  }
+  const int64_t S = m * LL;
+  uint8_t* sig = n->ws;
+  __nv_bfloat16* actA = reinterpret_cast<__nv_bfloat16*>(n->ws + ((2 * S + 255) & ~(int64_t)255));
+  __nv_bfloat16* actB = actA + S * 32;
+  const int gm = grid_for((S + 15) / 16 * 32, 128);
+  const int ga = grid_for(S * 32, 256);
+  syndrome_kernel<<<grid_for(S, 256), 256, 0, st>>>(noise, L, m, sig);
+  layer1_kernel<<<grid_for(S, 256), 256, 0, st>>>(sig, L, m, n->w1, n->params, actA);
+  amax_bf16_kernel<<<ga, 256, 0, st>>>(actA, S * 32, amax + 0);
+  conv_mma_kernel<4, kActs><<<gm, 128, 0, st>>>(actA, n->wb, n->params + kB1, L, m, actB, nullptr,
+                                                nullptr, nullptr);
+  amax_bf16_kernel<<<ga, 256, 0, st>>>(actB, S * 32, amax + 1);
+  conv_mma_kernel<4, kActs><<<gm, 128, 0, st>>>(actB, n->wb + 9 * 32 * 32, n->params + kB2, L, m,
+                                                actA, nullptr, nullptr, nullptr);
+  amax_bf16_kernel<<<ga, 256, 0, st>>>(actA, S * 32, amax + 2);
+  unsigned int h[3] = {0, 0, 0};
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, amax, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(amax);
+  if (e != cudaSuccess) return cuda_fail(e, "qca_net_calibrate_fp8");
+  for (int i = 0; i < 3; ++i) {
+    float a;
+    memcpy(&a, &h[i], sizeof(a));
+    n->act_scale[i] = a > 0.f ? a / 448.f : 1.f;
+  }
+  return QCA_OK;
 }
 
 int qca_net_decode_batch_async(qca_net_t n, const uint8_t* noise, int L, int64_t shots,

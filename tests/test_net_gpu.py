@@ -207,3 +207,73 @@ def test_net_plus_automaton_plog_within_2sigma(trained):
     b = (f_net == 1).double().mean().item()
     sigma = np.sqrt((a * (1 - a) + b * (1 - b)) / shots)
     assert a > 0.0 and abs(a - b) <= 2 * sigma + 1e-12, (a, b, sigma)
+
+
+# ------------------------------------------------------------------- FP8 form
+
+@pytest.fixture(scope="module")
+def trained_fp8(trained):
+    net, _ = trained
+    N = qca.sample_errors(32, 256, 0.05, seed=99)
+    scales = net.calibrate_fp8(N)
+    assert np.all(scales > 0)
+    net.set_precision("fp8")
+    yield net, scales
+    net.set_precision("bf16")
+
+
+def test_fp8_needs_scales():
+    net = qca.Net(seed=3)
+    try:
+        with pytest.raises(qca.QcaError):
+            net.set_precision("fp8")
+        net.set_fp8_scales([0.01, 0.02, 0.03])
+        np.testing.assert_array_equal(net.fp8_scales(), np.float32([0.01, 0.02, 0.03]))
+        net.set_precision("fp8")
+    finally:
+        net.close()
+
+
+def test_fp8_logits_match_fp64_forward(trained_fp8):
+    # E4M3 keeps 3 mantissa bits: where the fp32 accumulation and the FP64
+    # reference land on opposite sides of a rounding boundary of an
+    # intermediate activation (rare), that activation differs by one E4M3 step.
+    # The bar: 99.9 % of the logits within 1e-2 and none beyond 0.25.
+    net, scales = trained_fp8
+    L, shots = 24, 6
+    N = oracle.sample_errors(L, shots, 0.05, seed=41)
+    z = net.logits(dev(N)).cpu().numpy()
+    params = net.get_params()
+    A = anyon_maps(N)
+    d = np.concatenate([np.abs(z[s] - onet.forward_fp8(A[s], params, scales)).ravel()
+                        for s in range(shots)])
+    assert np.mean(d <= 1e-2) >= 0.999, (np.mean(d <= 1e-2), d.max())
+    assert d.max() <= 0.25, d.max()
+
+
+def test_fp8_pairing_bit_exact(trained_fp8):
+    net, _ = trained_fp8
+    L, shots = 21, 6
+    N = oracle.sample_errors(L, shots, 0.07, seed=42)
+    Nd = dev(N)
+    z = net.logits(Nd).cpu().numpy()
+    R, C0 = net.predecode(Nd)
+    torch.cuda.synchronize()
+    R, C0 = R.cpu().numpy(), C0.cpu().numpy()
+    A = anyon_maps(N)
+    for s in range(shots):
+        want = onet.pairing_links(A[s], onet.proposals(A[s], z[s]))
+        np.testing.assert_array_equal(C0[s], want, err_msg=f"shot {s}")
+    np.testing.assert_array_equal(R, N ^ C0)
+
+
+def test_fp8_net_plus_automaton_plog_within_2sigma(trained_fp8):
+    net, _ = trained_fp8
+    L, shots = 32, 40000
+    N = qca.sample_errors(L, shots, 0.058, seed=1)
+    _, _, f_plain = qca.decode_batch(N, max_steps=4096)
+    _, _, f_net = net.decode_batch(N, max_steps=4096)
+    a = (f_plain == 1).double().mean().item()
+    b = (f_net == 1).double().mean().item()
+    sigma = np.sqrt((a * (1 - a) + b * (1 - b)) / shots)
+    assert a > 0.0 and abs(a - b) <= 2 * sigma + 1e-12, (a, b, sigma)

@@ -227,3 +227,54 @@ def test_labels_as_proposals_pair_exactly_the_labelled_anyons():
     C0 = onet.pairing_links(anyon, prop)
     paired = oracle.syndrome(C0) == -1
     np.testing.assert_array_equal(paired, lab < 4)
+
+
+# --------------------------------------------------------------- FP8 (E4M3)
+
+def test_e4m3_hand_values():
+    x = np.array([0.0, 1.0, 1.0625, 1.1875, 448.0, 500.0, -600.0, 2.0**-9, 2.0**-10,
+                  3 * 2.0**-10, 240.0, 232.0, 0.3])
+    want = [0.0, 1.0, 1.0, 1.25, 448.0, 448.0, -448.0, 2.0**-9, 0.0, 2.0**-8, 240.0, 224.0,
+            0.3125]
+    np.testing.assert_array_equal(onet.e4m3_round(x), want)
+
+
+def test_e4m3_matches_torch_conversion_in_range():
+    r = np.random.default_rng(5)
+    x = (r.standard_normal(50000) * 10.0 ** r.uniform(-3, 2.3, 50000)).astype(np.float32)
+    x = x[np.abs(x) < 440]
+    want = torch.from_numpy(x).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    np.testing.assert_array_equal(onet.e4m3_round(x), want)
+
+
+def test_fp8_weights_per_channel_scale():
+    r = np.random.default_rng(6)
+    W = (r.standard_normal((4, 3, 3, 3)) * np.array([1, 10, 0.01, 0])[:, None, None, None]
+         ).astype(np.float32)
+    s = onet.fp8_weight_scales(W)
+    assert s[3] == 1.0
+    Wq = onet.fp8_weights(W)
+    # the largest entry of each nonzero channel maps exactly onto +-448 * s
+    for c in range(3):
+        k = np.argmax(np.abs(W[c]))
+        assert abs(Wq[c].ravel()[k]) == pytest.approx(448.0 * float(s[c]), rel=1e-7)
+        assert np.max(np.abs(Wq[c] - W[c])) <= np.max(np.abs(W[c])) / 16 + 1e-12
+    assert np.all(Wq[3] == 0)
+
+
+def test_forward_fp8_close_to_bf16_form():
+    L = 10
+    r = np.random.default_rng(8)
+    anyon = (r.random((L, L)) < 0.2).astype(np.uint8)
+    params = rng_params(9, scale=0.1)
+    zb = onet.forward(anyon, params, quantize=True)
+    # activation scales from the exact form's per-layer input maxima
+    acts, x = [], np.stack([anyon.astype(np.float64), np.ones((L, L))])
+    for i, (W, b) in enumerate(onet.unpack(params)):
+        if i > 0:
+            acts.append(np.max(x))
+        x = np.maximum(onet.conv3x3_circular(x, W, b), 0) if i < 3 else x
+    scales = [max(a, 1e-6) / 448.0 for a in acts]
+    z8 = onet.forward_fp8(anyon, params, scales)
+    assert np.max(np.abs(z8 - zb)) < 0.2 * max(1.0, np.max(np.abs(zb)))
+    assert np.max(np.abs(z8 - zb)) > 0  # the FP8 points do change the result
