@@ -446,6 +446,151 @@ def run_net(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def step_stats(steps_h, fail_h, shots):
+    import numpy as np
+    st = steps_h.astype(np.int64)
+    f = float((fail_h > 0).mean())
+    hist_edges = [0, 8, 16, 32, 64, 128, 256, 512, 4097]
+    hist = np.histogram(st, bins=hist_edges)[0].tolist()
+    return {"p_log": f, "p_log_sigma": float(np.sqrt(max(f * (1 - f), 0.0) / max(shots, 1))),
+            "budget_exhausted": int((fail_h == 2).sum()), "watchdog": int((fail_h == 3).sum()),
+            "mean_steps": float(st.mean()), "p50_steps": float(np.percentile(st, 50)),
+            "p99_steps": float(np.percentile(st, 99)), "max_steps": int(st.max()),
+            "steps_histogram": {"edges": hist_edges, "counts": hist}}
+
+
+def run_large(args, rank, world, local):
+    """Large-lattice stress: L = 1024, p in {0.05, 0.07}, 10 000 shots; the
+    plain automaton on the large-lattice kernel is the timed step (p = 0.05),
+    then the FP8 pre-decoder + automaton on the same noise, at both p, with
+    step-count distributions and p_log."""
+    import numpy as np
+    import torch
+
+    import paper_2506_03266_gb300 as qca
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    qca.build()
+    qca.lib()
+    L = args.L if args.L != L_DEFAULT else 1024
+    shots = args.shots if args.shots != SHOTS_DEFAULT else 10_000
+    p_list = [0.05, 0.07]
+    train_batch = 256
+    train_iters = max(1, (args.train_syndromes + train_batch - 1) // train_batch)
+    net = qca.Net(seed=1)
+    t0 = time.perf_counter()
+    losses = net.train(L=32, iterations=train_iters, batch=train_batch, p_lo=0.02, p_hi=0.07,
+                       seed=1, lr=2e-3)
+    train_s = time.perf_counter() - t0
+    cal = qca.sample_errors(L, min(16, shots), 0.06, seed=2)
+    scales = net.calibrate_fp8(cal)
+    del cal
+    net.set_precision("fp8")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    shot0, _ = shard(rank, shots)
+    results = {}
+    timed = None
+    for p in p_list:
+        N = qca.sample_errors(L, shots, p, seed=0, shot0=shot0)
+        out = (torch.empty_like(N), torch.empty(shots, dtype=torch.int32, device="cuda"),
+               torch.empty(shots, dtype=torch.uint8, device="cuda"))
+        if p == p_list[0]:
+            for _ in range(args.warmup):
+                qca.decode_batch(N, MAX_STEPS, out=out)
+            barrier()
+            clocks = ClockSampler(local)
+            clocks.start()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+            barrier()
+            ev[0].record(stream)
+            for i in range(args.steps):
+                qca.decode_batch(N, MAX_STEPS, out=out)
+                ev[i + 1].record(stream)
+            barrier()
+            clk = clocks.stop()
+            kernel_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+            total_ms = ev[0].elapsed_time(ev[-1])
+            if dist is not None:
+                total_ms = reduce_time_max(total_ms, dist, "cuda")
+            timed = {"ms_per_step": total_ms / args.steps, "kernel_ms": kernel_ms, "clocks": clk}
+            plain_ms = statistics.mean(kernel_ms)
+        else:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            qca.decode_batch(N, MAX_STEPS, out=out)
+            b.record(stream)
+            barrier()
+            plain_ms = a.elapsed_time(b)
+        plain = step_stats(out[1].cpu().numpy(), out[2].cpu().numpy(), shots)
+        plain["shot_decodes_per_s"] = world * shots / (plain_ms / 1e3)
+        plain["site_updates_per_s"] = float(out[1].cpu().numpy().astype(np.int64).sum()) * L * L \
+            / (plain_ms / 1e3)
+        if p == p_list[0]:
+            site_updates = float(out[1].cpu().numpy().astype(np.int64).sum()) * L * L
+        scratch = torch.empty_like(N)
+        net.decode_batch(N, MAX_STEPS, out=out, scratch=scratch)  # first call sizes workspaces
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        net.decode_batch(N, MAX_STEPS, out=out, scratch=scratch)
+        b.record(stream)
+        barrier()
+        net_ms = a.elapsed_time(b)
+        netca = step_stats(out[1].cpu().numpy(), out[2].cpu().numpy(), shots)
+        netca["shot_decodes_per_s"] = world * shots / (net_ms / 1e3)
+        results[str(p)] = {"plain": plain, "fp8_net_ca": netca}
+        del N, out, scratch
+        torch.cuda.empty_cache()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        net.close()
+        return
+    ms_per_step = timed["ms_per_step"]
+    kernel_s = statistics.mean(timed["kernel_ms"]) / 1e3
+    achieved = ALU_OPS_PER_SITE_UPDATE * site_updates / kernel_s
+    line = {
+        "metric": "shot-decodes/s of the plain automaton at L=1024, p=0.05 (large-lattice "
+                  "kernel), with the FP8 net + automaton compared at p=0.05 and 0.07",
+        "value": world * shots / (ms_per_step / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "site_updates_per_s": site_updates / (ms_per_step / 1e3),
+        "config": {"workload": (f"plain automaton decode, L={L} toric code, i.i.d. bit-flip "
+                                f"p=0.05 (seed 0), {shots} shots per GPU, budget {MAX_STEPS}; "
+                                f"comparison at p in {p_list} with an FP8 pre-decoder trained on "
+                                f"{train_iters * train_batch} automaton-labelled L=32 syndromes"),
+                   "L": L, "shots_per_gpu": shots, "kernel_path": qca.kernel_path(L),
+                   "l2": "inputs larger than L2 (no flush needed)",
+                   "train": {"syndromes": train_iters * train_batch, "seconds": train_s,
+                             "final_loss": float(np.mean(losses[-50:]))},
+                   "fp8_activation_scales": [float(x) for x in scales]},
+        "comparison": results,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": ALU_PEAK_LANE_OPS / 1e9,
+                     "unit": "Glane-op/s", "frac": achieved / ALU_PEAK_LANE_OPS, "traffic": None,
+                     "kernel_ms": statistics.mean(timed["kernel_ms"])},
+        "clocks": timed["clocks"],
+        "gpu_launches": args.steps,
+        "e2e": None,
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    net.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def ctypes_ptr(t):
     import ctypes
     return ctypes.c_void_p(t.data_ptr())
@@ -478,9 +623,11 @@ def main():
     ap.add_argument("--shots", type=int, default=SHOTS_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="uniform", choices=["uniform", "uneven", "net"],
+    ap.add_argument("--workload", default="uniform",
+                    choices=["uniform", "uneven", "net", "large"],
                     help="uniform: the L=256 headline; uneven: 200 000 shots of mixed L; "
-                         "net: learned pre-decoder + automaton at L=128, p=0.04")
+                         "net: learned pre-decoder + automaton at L=128, p=0.04; "
+                         "large: L=1024 plain vs FP8 net + automaton")
     ap.add_argument("--train-syndromes", type=int, default=1_000_000,
                     help="net workload: automaton-labelled training syndromes (untimed)")
     ap.add_argument("--autotune", action="store_true",
@@ -499,6 +646,9 @@ def main():
         return
     if args.workload == "net":
         run_net(args, rank, world, local)
+        return
+    if args.workload == "large":
+        run_large(args, rank, world, local)
         return
 
     # CPU baseline before the first GPU call (oracle pool is spawned)
