@@ -23,6 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qca_oracle.c")
+_SRC_1D = os.path.join(_HERE, "qca_oracle_1d.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libqca_oracle.so")
 _lock = threading.Lock()
@@ -39,10 +40,12 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     hdr = os.path.join(_HERE, "qca_oracle.h")
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(hdr))):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
+                                                   os.path.getmtime(_SRC_1D),
+                                                   os.path.getmtime(hdr))):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, _SRC_1D, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -89,6 +92,23 @@ def _load():
         lib.qo_decode_batch.argtypes = [u8p, c_int, c_i64, c_i64, c_int, c_int, c_int, c_u64,
                                         c_u64, u8p, i32p, u8p]
         lib.qo_decode_batch.restype = None
+        lib.qo1_sample_errors.argtypes = [c_int, c_i64, c_i64, c_u64, c_u64, u8p]
+        lib.qo1_sample_errors.restype = None
+        lib.qo1_syndrome.argtypes = [c_int, u8p, i8p]
+        lib.qo1_syndrome.restype = None
+        lib.qo1_substep.argtypes = [c_int, c_int, i8p, i32p, i32p]
+        lib.qo1_substep.restype = None
+        lib.qo1_forces.argtypes = [c_int, i8p, i32p, i8p]
+        lib.qo1_forces.restype = None
+        lib.qo1_feedback.argtypes = [c_int, i8p, i8p, u8p]
+        lib.qo1_feedback.restype = None
+        lib.qo1_step.argtypes = [c_int, c_int, c_int, c_u64, c_u64, c_i64, ctypes.c_int32,
+                                 i8p, i32p, u8p]
+        lib.qo1_step.restype = c_int
+        lib.qo1_decode_shot.argtypes = [u8p, c_int, c_int, c_int, c_int, c_u64, c_u64, c_i64,
+                                        u8p, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_uint8)]
+        lib.qo1_decode_shot.restype = c_int
         _lib = lib
         return lib
 
@@ -227,3 +247,62 @@ def decode_batch(N: np.ndarray, *, v: int = V_DEFAULT, m_max: int = M_MAX_DEFAUL
         _load().qo_decode_batch(N, L, shot0, shots, v, m_max, max_steps, move_thr, seed, C, steps,
                                 flags)
     return C, steps, flags
+
+
+# ------------------------------------------------------------- 1D variant
+# Repetition code on a ring (Sec. 3.1, Def. "message passing automaton, 1D";
+# Sec. 7.1 numerics); readings in qca_oracle_1d.c.
+
+def sample_errors_1d(L: int, shots: int, p: float, seed: int, shot0: int = 0) -> np.ndarray:
+    out = np.zeros((shots, L), dtype=np.uint8)
+    _load().qo1_sample_errors(L, shot0, shots, prob_threshold(p), seed, out)
+    return out
+
+
+def syndrome_1d(links: np.ndarray) -> np.ndarray:
+    links = np.ascontiguousarray(links, dtype=np.uint8)
+    sigma = np.zeros(links.shape[-1], dtype=np.int8)
+    _load().qo1_syndrome(links.shape[-1], links, sigma)
+    return sigma
+
+
+def substep_1d(sigma: np.ndarray, m: np.ndarray, m_max: int = M_MAX_DEFAULT) -> np.ndarray:
+    sigma = np.ascontiguousarray(sigma, dtype=np.int8)
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    out = np.zeros_like(m)
+    _load().qo1_substep(sigma.shape[0], m_max, sigma, m, out)
+    return out
+
+
+def forces_1d(sigma: np.ndarray, m: np.ndarray) -> np.ndarray:
+    sigma = np.ascontiguousarray(sigma, dtype=np.int8)
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    f = np.zeros(sigma.shape[0], dtype=np.int8)
+    _load().qo1_forces(sigma.shape[0], sigma, m, f)
+    return f
+
+
+def feedback_1d(sigma: np.ndarray, f: np.ndarray) -> np.ndarray:
+    sigma = np.ascontiguousarray(sigma, dtype=np.int8)
+    f = np.ascontiguousarray(f, dtype=np.int8)
+    out = np.zeros(sigma.shape[0], dtype=np.uint8)
+    _load().qo1_feedback(sigma.shape[0], sigma, f, out)
+    return out
+
+
+def step_1d(sigma, m, C, *, v=V_DEFAULT, m_max=M_MAX_DEFAULT, move_thr=0, seed=0, shot=0, t=0):
+    """One step in place on (sigma, m, C); returns the anyon count."""
+    return _load().qo1_step(sigma.shape[0], v, m_max, move_thr, seed, shot, t, sigma, m, C)
+
+
+def decode_shot_1d(N: np.ndarray, *, v: int = V_DEFAULT, m_max: int = M_MAX_DEFAULT,
+                   max_steps: int = 4096, move_thr: int = 0, seed: int = 0, shot: int = 0):
+    """Returns (C, steps, flag, majority_flag)."""
+    N = np.ascontiguousarray(N, dtype=np.uint8)
+    L = N.shape[-1]
+    C = np.zeros_like(N)
+    steps = ctypes.c_int32()
+    maj = ctypes.c_uint8()
+    flag = _load().qo1_decode_shot(N, L, v, m_max, max_steps, move_thr, seed, shot, C,
+                                   ctypes.byref(steps), ctypes.byref(maj))
+    return C, steps.value, flag, maj.value

@@ -73,6 +73,22 @@ void qo_decode_batch(const uint8_t* N, int L, int64_t shot0, int64_t shots, int 
                      int max_steps, uint64_t move_thr, uint64_t seed,
                      uint8_t* C, int32_t* steps, uint8_t* flags);
 
+/* ---- 1D repetition code (qca_oracle_1d.c; Sec. 3.1, Def. "message passing
+ * automaton, 1D"; Sec. 7.1).  Ring of L sites, link <r, r+1> = bit r. */
+void qo1_sample_errors(int L, int64_t shot0, int64_t shots, uint64_t thr, uint64_t seed,
+                       uint8_t* out);
+void qo1_syndrome(int L, const uint8_t* links, int8_t* sigma);
+/* One application of A^(1); m is int32 [2][L] (m^+, m^-). */
+void qo1_substep(int L, int m_max, const int8_t* sigma, const int32_t* m_in, int32_t* m_out);
+void qo1_forces(int L, const int8_t* sigma, const int32_t* m, int8_t* f);
+void qo1_feedback(int L, const int8_t* sigma, const int8_t* f, uint8_t* flips);
+int qo1_step(int L, int v, int m_max, uint64_t move_thr, uint64_t seed, int64_t shot, int32_t t,
+             int8_t* sigma, int32_t* m, uint8_t* C);
+/* Returns the flag: 0 success (N xor C = 0), 1 N xor C = all ones, 2 budget.
+ * maj_fail (may be NULL): 1 if the output value differs from majority(N). */
+int qo1_decode_shot(const uint8_t* N, int L, int v, int m_max, int max_steps, uint64_t move_thr,
+                    uint64_t seed, int64_t shot, uint8_t* C, int32_t* steps, uint8_t* maj_fail);
+
 #ifdef __cplusplus
 }
 #endif
