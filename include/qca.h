@@ -46,6 +46,7 @@ extern "C" {
 
 #define QCA_MAX_L 1024       /* largest lattice any kernel accepts                  */
 #define QCA_MAX_STEPS (1 << 20)
+#define QCA_MAX_L_1D 16384   /* longest ring of the 1D decoder                      */
 
 /* Decoder options.  Defaults (qca_default_config) are the paper's numerics
  * (Sec. 7: v = 3, deterministic rule) with an 8-bit message register. */
@@ -218,6 +219,37 @@ int qca_get_tuning(int L, int* band_height, int* sparse_divisor, int* threads_pe
  * temporary device memory; synchronises. */
 int qca_autotune(int L, int64_t shots, double p, uint64_t seed, int max_steps,
                  int* best_band_height, int* best_sparse_divisor, float* best_ms);
+
+/* ---------------------------------------------------------------------------
+ * 1D message-passing automaton decoder for the repetition code (Sec. 3.1,
+ * Def. "message passing automaton, 1D"; Sec. 7.1 numerics).  A ring of L sites
+ * (3 <= L <= QCA_MAX_L_1D); the qubit of link <r, r+1> is byte r of the noise
+ * and correction arrays, device uint8 [shots][L]; anyons sit on sites.  Each
+ * step applies A^(1) v times (fields m^+ from the left, m^- from the right,
+ * value = distance travelled, a value above m_max vanishes), then moves every
+ * anyon one link toward the smaller field (an empty field counts as +infinity;
+ * no move on a tie), a link crossed from both ends flipping once.  With
+ * cfg->p_move > 0 an anyon moves in a uniformly random direction with that
+ * probability instead (Sec. 7.1 uses 10 %); the draw per (shot, step, site)
+ * is splitmix64 of the same key chain as the 2D option.
+ * ------------------------------------------------------------------------- */
+
+/* Noise: link r of shot s (counted from shot0) flips iff
+ * splitmix64(splitmix64(splitmix64(seed ^ 0x4E4F49534531) ^ s) ^ r) < floor(p * 2^64). */
+int qca_sample_errors_1d_async(int L, int64_t shot0, int64_t shots, double p, uint64_t seed,
+                               uint8_t* out_errors, void* stream);
+
+/* Decode: out_correction [shots][L]; out_steps int32 [shots]; out_flag uint8
+ * [shots] = 0 when N xor C is all zeros (the encoded value), 1 when it is all
+ * ones (a logical error), 2 when the budget ran out with anyons left;
+ * out_majority_flag (may be NULL) = 1 when the decoded value differs from the
+ * majority vote of the input bits (more than L/2 set), the success criterion
+ * of the paper's 1D numerics, 2 on an exhausted budget.  cfg may be NULL
+ * (v = 3, m_max = 255, no random moves); v 1..8, m_max 1..255. */
+int qca_decode_1d_batch_async(const uint8_t* noise, int L, int64_t shots, int max_steps,
+                              uint64_t rng_seed, const qca_config* cfg, uint8_t* out_correction,
+                              int32_t* out_steps, uint8_t* out_flag, uint8_t* out_majority_flag,
+                              void* stream);
 
 /* ---------------------------------------------------------------------------
  * Learned pre-decoder in front of the automaton.  The paper has no learned

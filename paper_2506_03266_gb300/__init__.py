@@ -81,6 +81,9 @@ def lib():
             "qca_decode_uneven_async": ([vp, vp, i32, u64, vp, vp, vp, cfgp, vp], i32),
             "qca_kernel_path": ([i32, cfgp], i32),
             "qca_set_kernel_path": ([i32, i32], i32),
+            "qca_sample_errors_1d_async": ([i32, i64, i64, ctypes.c_double, u64, vp, vp], i32),
+            "qca_decode_1d_batch_async": ([vp, i32, i64, i32, u64, cfgp, vp, vp, vp, vp, vp],
+                                          i32),
             "qca_net_param_count": ([], i64),
             "qca_net_create": ([u64, ctypes.POINTER(vp)], i32),
             "qca_net_destroy": ([vp], i32),
@@ -149,6 +152,38 @@ def kernel_path(L: int, v: int = 3) -> int:
     if rc < 0:
         _check(rc)
     return rc
+
+
+def sample_errors_1d(L: int, shots: int, p: float, seed: int, shot0: int = 0, stream=None):
+    """i.i.d. link flips of the ring (uint8 [shots][L] on the current cuda device)."""
+    torch = _torch()
+    out = torch.empty((shots, L), dtype=torch.uint8, device="cuda")
+    _check(lib().qca_sample_errors_1d_async(L, shot0, shots, float(p), seed & (2**64 - 1),
+                                            ctypes.c_void_p(out.data_ptr()),
+                                            _stream(torch, stream)))
+    return out
+
+
+def decode_1d_batch(errors, max_steps: int = 4096, rng_seed: int = 0, *, v: int = 3,
+                    m_max: int = 255, p_move: float = 0.0, shot_offset: int = 0, out=None,
+                    stream=None):
+    """1D decode of uint8 [shots][L] ring noise (cuda).  Returns (correction,
+    steps, flag, majority_flag)."""
+    torch = _torch()
+    shots, L = errors.shape
+    _dev_u8(torch, errors, (shots, L), "errors")
+    if out is None:
+        out = (torch.empty_like(errors), torch.empty(shots, dtype=torch.int32, device=errors.device),
+               torch.empty(shots, dtype=torch.uint8, device=errors.device),
+               torch.empty(shots, dtype=torch.uint8, device=errors.device))
+    C, steps, flag, maj = out
+    cfg = make_config(v, m_max, p_move, shot_offset)
+    _check(lib().qca_decode_1d_batch_async(
+        ctypes.c_void_p(errors.data_ptr()), L, shots, max_steps, rng_seed & (2**64 - 1),
+        ctypes.byref(cfg), ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(steps.data_ptr()),
+        ctypes.c_void_p(flag.data_ptr()), ctypes.c_void_p(maj.data_ptr()),
+        _stream(torch, stream)))
+    return C, steps, flag, maj
 
 
 def set_kernel_path(L: int, path: int = -1):
