@@ -24,6 +24,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qca_oracle.c")
 _SRC_1D = os.path.join(_HERE, "qca_oracle_1d.c")
+_SRC_VAR = os.path.join(_HERE, "qca_oracle_variants.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libqca_oracle.so")
 _lock = threading.Lock()
@@ -42,10 +43,12 @@ def build(force: bool = False) -> str:
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
                                                    os.path.getmtime(_SRC_1D),
+                                                   os.path.getmtime(_SRC_VAR),
                                                    os.path.getmtime(hdr))):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, _SRC_1D, "-lm"]
+    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, _SRC_1D, _SRC_VAR,
+           "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -109,6 +112,18 @@ def _load():
                                         u8p, ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_uint8)]
         lib.qo1_decode_shot.restype = c_int
+        lib.qo_open_link_exists.argtypes = [c_int, c_int, c_int, c_int]
+        lib.qo_open_link_exists.restype = c_int
+        lib.qo_open_syndrome.argtypes = [c_int, u8p, i8p]
+        lib.qo_open_syndrome.restype = None
+        lib.qo_open_substep.argtypes = [c_int, c_int, i8p, i32p, i32p]
+        lib.qo_open_substep.restype = None
+        lib.qo_open_decode_shot.argtypes = [u8p, c_int, c_int, c_int, c_int, u8p,
+                                            ctypes.POINTER(ctypes.c_int32)]
+        lib.qo_open_decode_shot.restype = c_int
+        lib.qo_desync_decode_shot.argtypes = [u8p, c_int, c_int, c_int, c_int, c_u64, c_u64,
+                                              c_u64, c_i64, u8p, ctypes.POINTER(ctypes.c_int32)]
+        lib.qo_desync_decode_shot.restype = c_int
         _lib = lib
         return lib
 
@@ -306,3 +321,62 @@ def decode_shot_1d(N: np.ndarray, *, v: int = V_DEFAULT, m_max: int = M_MAX_DEFA
     flag = _load().qo1_decode_shot(N, L, v, m_max, max_steps, move_thr, seed, shot, C,
                                    ctypes.byref(steps), ctypes.byref(maj))
     return C, steps.value, flag, maj.value
+
+
+# ---------------------------------------------------------- 2D variants
+# Open boundaries (Appendix "Open boundary conditions") and uncoordinated
+# desynchronisation (Sec. 7.3); readings R16 / R17 in qca_oracle_variants.c.
+
+def open_link_mask(L: int) -> np.ndarray:
+    """uint8 [2][L][L]: 1 where the open lattice has a qubit."""
+    lib = _load()
+    m = np.zeros((2, L, L), np.uint8)
+    for a in range(2):
+        for y in range(L):
+            for x in range(L):
+                m[a, y, x] = lib.qo_open_link_exists(L, a, x, y)
+    return m
+
+
+def open_syndrome(E: np.ndarray) -> np.ndarray:
+    E = np.ascontiguousarray(E, dtype=np.uint8)
+    L = E.shape[-1]
+    s = np.zeros((L, L), np.int8)
+    _load().qo_open_syndrome(L, E, s)
+    return s
+
+
+def open_substep(sigma, m, m_max: int = M_MAX_DEFAULT):
+    sigma = np.ascontiguousarray(sigma, dtype=np.int8)
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    out = np.zeros_like(m)
+    _load().qo_open_substep(sigma.shape[0], m_max, sigma, m, out)
+    return out
+
+
+def open_decode_shot(N, *, v: int = V_DEFAULT, m_max: int = M_MAX_DEFAULT, max_steps: int = 4096):
+    """Returns (C, steps, flag) on the open lattice."""
+    N = np.ascontiguousarray(N, dtype=np.uint8)
+    L = N.shape[-1]
+    C = np.zeros_like(N)
+    steps = ctypes.c_int32()
+    flag = _load().qo_open_decode_shot(N, L, v, m_max, max_steps, C, ctypes.byref(steps))
+    return C, steps.value, flag
+
+
+def desync_thresholds(q: float, v: int = V_DEFAULT):
+    """(message, move) firing thresholds of a tick of length q."""
+    return prob_threshold(min(1.0, v * q)), prob_threshold(q)
+
+
+def desync_decode_shot(N, q: float, *, v: int = V_DEFAULT, m_max: int = M_MAX_DEFAULT,
+                       max_ticks: int = 100000, seed: int = 0, shot: int = 0):
+    """Returns (C, ticks, flag) of the uncoordinated decoder."""
+    N = np.ascontiguousarray(N, dtype=np.uint8)
+    L = N.shape[-1]
+    C = np.zeros_like(N)
+    ticks = ctypes.c_int32()
+    tm, tf = desync_thresholds(q, v)
+    flag = _load().qo_desync_decode_shot(N, L, v, m_max, max_ticks, tm, tf, seed, shot, C,
+                                         ctypes.byref(ticks))
+    return C, ticks.value, flag

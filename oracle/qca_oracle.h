@@ -89,6 +89,20 @@ int qo1_step(int L, int v, int m_max, uint64_t move_thr, uint64_t seed, int64_t 
 int qo1_decode_shot(const uint8_t* N, int L, int v, int m_max, int max_steps, uint64_t move_thr,
                     uint64_t seed, int64_t shot, uint8_t* C, int32_t* steps, uint8_t* maj_fail);
 
+/* ---- 2D variants (qca_oracle_variants.c): open boundaries (Appendix "Open
+ * boundary conditions"; readings R17 in the .c file) and uncoordinated
+ * desynchronisation (Sec. 7.3; reading R16). */
+int qo_open_link_exists(int L, int plane, int x, int y);
+void qo_open_syndrome(int L, const uint8_t* E, int8_t* sigma);
+void qo_open_substep(int L, int m_max, const int8_t* sigma, const int32_t* m_in, int32_t* m_out);
+/* Returns 0 success, 1 logical error (odd crossing of the cut x = 0|1), 2 budget. */
+int qo_open_decode_shot(const uint8_t* N, int L, int v, int m_max, int max_steps, uint8_t* C,
+                        int32_t* steps);
+/* Returns the flag as qo_decode_shot; ticks receives the ticks taken. */
+int qo_desync_decode_shot(const uint8_t* N, int L, int v, int m_max, int max_ticks,
+                          uint64_t thr_msg, uint64_t thr_move, uint64_t seed, int64_t shot,
+                          uint8_t* C, int32_t* ticks);
+
 #ifdef __cplusplus
 }
 #endif

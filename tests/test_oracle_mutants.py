@@ -19,6 +19,7 @@ from test_oracle import _closed_form, _prose_link
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "qca_oracle.c")
 SRC_1D = os.path.join(os.path.dirname(SRC), "qca_oracle_1d.c")
+SRC_VAR = os.path.join(os.path.dirname(SRC), "qca_oracle_variants.c")
 HDR = os.path.join(os.path.dirname(oracle.__file__), "qca_oracle.h")
 
 MUTANTS = {
@@ -95,8 +96,10 @@ def test_pins_catch_planted_mistake(tmp_path, monkeypatch, name):
     (d / "qca_oracle.c").write_text(src.replace(old, new))
     lib = d / "libmut.so"
     shutil.copy(SRC_1D, d / "qca_oracle_1d.c")
+    shutil.copy(SRC_VAR, d / "qca_oracle_variants.c")
     subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", str(lib),
-                    str(d / "qca_oracle.c"), str(d / "qca_oracle_1d.c"), "-lm"], check=True)
+                    str(d / "qca_oracle.c"), str(d / "qca_oracle_1d.c"),
+                    str(d / "qca_oracle_variants.c"), "-lm"], check=True)
     monkeypatch.setattr(oracle, "_lib", None)
     monkeypatch.setattr(oracle, "build", lambda force=False: str(lib))
     try:
