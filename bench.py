@@ -591,6 +591,112 @@ def run_large(args, rank, world, local):
         dist.destroy_process_group()
 
 
+# Shared-memory bytes the 1D kernel reads and writes per site-update (derivation
+# in the design doc): two fields x (up to 3 syndrome bytes, 1 old value, 1 new
+# value), the move pass (syndrome, fields, move byte), feedback (two move
+# bytes, correction read/write), syndrome update (two correction bytes,
+# syndrome read/write) and the flag clear (correction read/write).
+SMEM_BYTES_PER_SITE_UPDATE_1D = 22
+SMEM_PEAK_BYTES = 152 * 128 * 2.070e9  # 128 B/clk/SM at the maximum SM clock
+
+
+def run_1d(args, rank, world, local):
+    """1D repetition code (Sec. 7.1): ring of L = 1024, p = 0.3, 100 000 shots,
+    v = 3 with 10 % random moves; one step is one decode of the batch.  T_dec at
+    L in {64, 256, 1024, 4096} follows, untimed."""
+    import numpy as np
+    import torch
+
+    import paper_2506_03266_gb300 as qca
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    qca.build()
+    qca.lib()
+    L = args.L if args.L != L_DEFAULT else 1024
+    p = args.p if args.p != P_DEFAULT else 0.3
+    shots = args.shots
+    shot0, _ = shard(rank, shots)
+    N = qca.sample_errors_1d(L, shots, p, seed=0, shot0=shot0)
+    out = (torch.empty_like(N), torch.empty(shots, dtype=torch.int32, device="cuda"),
+           torch.empty(shots, dtype=torch.uint8, device="cuda"),
+           torch.empty(shots, dtype=torch.uint8, device="cuda"))
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def decode():
+        qca.decode_1d_batch(N, MAX_STEPS, rng_seed=7, p_move=0.1, shot_offset=shot0, out=out)
+
+    for _ in range(args.warmup):
+        decode()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        decode()
+        ev[i + 1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    kernel_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if dist is not None:
+        total_ms = reduce_time_max(total_ms, dist, "cuda")
+    ms_per_step = total_ms / args.steps
+    steps_h, flag_h, maj_h = out[1].cpu().numpy(), out[2].cpu().numpy(), out[3].cpu().numpy()
+    site_updates = float(steps_h.astype(np.int64).sum()) * L
+    tdec = {}
+    for Ls in (64, 256, 1024, 4096):
+        n = 20000
+        Ns = qca.sample_errors_1d(Ls, n, p, seed=1)
+        _, s_, f_, m_ = qca.decode_1d_batch(Ns, MAX_STEPS, rng_seed=7, p_move=0.1)
+        s_, f_, m_ = s_.cpu().numpy(), f_.cpu().numpy(), m_.cpu().numpy()
+        tdec[str(Ls)] = {"mean_steps": float(s_.mean()), "p_log": float((f_ > 0).mean()),
+                         "p_log_majority": float((m_ > 0).mean())}
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    kernel_s = statistics.mean(kernel_ms) / 1e3
+    achieved = SMEM_BYTES_PER_SITE_UPDATE_1D * site_updates / kernel_s
+    line = {
+        "metric": "shot-decodes/s of the 1D repetition-code automaton (L=1024, p=0.3, "
+                  "10 % random moves)",
+        "value": world * shots / (ms_per_step / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "site_updates_per_s": site_updates / (ms_per_step / 1e3),
+        "config": {"workload": (f"1D message-passing automaton decode, ring L={L}, i.i.d. "
+                                f"bit-flip p={p} (seed 0), {shots} shots per GPU, v=3, "
+                                f"random moves 10 %, budget {MAX_STEPS}"),
+                   "L": L, "p": p, "shots_per_gpu": shots,
+                   "l2": "inputs smaller than L2 (102 MB); each shot is read once per step"},
+        "decoder": {"p_log": float((flag_h > 0).mean()),
+                    "p_log_majority": float((maj_h > 0).mean()),
+                    "budget_exhausted": int((flag_h == 2).sum()),
+                    "mean_steps": float(steps_h.mean()),
+                    "p99_steps": float(np.percentile(steps_h, 99)),
+                    "tdec_vs_L": tdec},
+        "roofline": {"bound": "smem", "achieved": achieved / 1e9, "peak": SMEM_PEAK_BYTES / 1e9,
+                     "unit": "GB/s", "frac": achieved / SMEM_PEAK_BYTES, "traffic": None,
+                     "note": f"{SMEM_BYTES_PER_SITE_UPDATE_1D} shared-memory bytes per "
+                             "site-update against 128 B/clk/SM"},
+        "clocks": clk, "gpu_launches": args.steps, "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def ctypes_ptr(t):
     import ctypes
     return ctypes.c_void_p(t.data_ptr())
@@ -624,10 +730,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="uniform",
-                    choices=["uniform", "uneven", "net", "large"],
+                    choices=["uniform", "uneven", "net", "large", "1d"],
                     help="uniform: the L=256 headline; uneven: 200 000 shots of mixed L; "
                          "net: learned pre-decoder + automaton at L=128, p=0.04; "
-                         "large: L=1024 plain vs FP8 net + automaton")
+                         "large: L=1024 plain vs FP8 net + automaton; "
+                         "1d: the repetition-code automaton")
     ap.add_argument("--train-syndromes", type=int, default=1_000_000,
                     help="net workload: automaton-labelled training syndromes (untimed)")
     ap.add_argument("--autotune", action="store_true",
@@ -649,6 +756,9 @@ def main():
         return
     if args.workload == "large":
         run_large(args, rank, world, local)
+        return
+    if args.workload == "1d":
+        run_1d(args, rank, world, local)
         return
 
     # CPU baseline before the first GPU call (oracle pool is spawned)

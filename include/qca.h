@@ -252,6 +252,43 @@ int qca_decode_1d_batch_async(const uint8_t* noise, int L, int64_t shots, int ma
                               void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Two variants of the 2D decoder (literal per-site sweep, state in a cached
+ * device workspace of 14 L^2 bytes per resident shot; noise, correction,
+ * steps and flag arrays as in qca_decode_batch).
+ * ------------------------------------------------------------------------- */
+
+/* Open boundaries (Appendix "Open boundary conditions", Def. "message passing
+ * automaton with open boundaries"): an L x L grid without wrap whose columns
+ * x = 0 and x = L-1 are rough boundaries.  Qubits: e_x(x, y) for x <= L-2 and
+ * e_y(x, y) for 1 <= x <= L-2, y <= L-2; the other entries of the noise array
+ * are ignored and stay 0 in the correction.  The boundary holds no messages,
+ * sources x messages into the bulk (m^{+x} from x = 0, m^{-x} from x = L-1)
+ * and absorbs anyons; sets C^(a) lose their members outside the grid.
+ * out_logical_fail: 0 success, 1 N xor C crosses the cut between columns 0
+ * and 1 an odd number of times (it joins the two boundaries), 2 budget.  cfg:
+ * v and m_max as for the torus; p_move must be 0. */
+int qca_decode_open_batch_async(const uint8_t* noise, int L, int64_t shots, int max_steps,
+                                const qca_config* cfg, uint8_t* out_correction,
+                                int32_t* out_steps, uint8_t* out_logical_fail, void* stream);
+
+/* Uncoordinated desynchronisation (Sec. 7.3) on the torus: time advances in
+ * ticks of length q (0 <= q <= 1); per tick each site fires its message
+ * update with probability min(1, v q) and, holding an anyon, its move with
+ * probability q, from the draws
+ *   splitmix64(splitmix64(splitmix64(splitmix64(rng_seed ^ 0x444553594E43)
+ *              ^ (shot_offset + shot)) ^ tick) ^ (2 r + c)) < floor(prob * 2^64),
+ * c = 0 (messages) or 1 (move), r = y L + x.  The firing message updates of a
+ * tick are one application of A^(D) at those sites, from the fields before
+ * the tick; the firing anyons then move by the forces of the updated fields
+ * (OR feedback); sigma is updated last.  out_ticks: ticks until no anyon is
+ * left (or max_ticks); out_logical_fail as for qca_decode_batch.  q = 1 with
+ * v = 1 is exactly the synchronous decoder with v = 1. */
+int qca_decode_desync_batch_async(const uint8_t* noise, int L, int64_t shots, int max_ticks,
+                                  double q, uint64_t rng_seed, const qca_config* cfg,
+                                  uint8_t* out_correction, int32_t* out_ticks,
+                                  uint8_t* out_logical_fail, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Learned pre-decoder in front of the automaton.  The paper has no learned
  * component; this stage is an addition whose only job is to pair off nearby
  * anyons before the automaton (the paper's decoder, unchanged) finishes every

@@ -84,6 +84,9 @@ def lib():
             "qca_sample_errors_1d_async": ([i32, i64, i64, ctypes.c_double, u64, vp, vp], i32),
             "qca_decode_1d_batch_async": ([vp, i32, i64, i32, u64, cfgp, vp, vp, vp, vp, vp],
                                           i32),
+            "qca_decode_open_batch_async": ([vp, i32, i64, i32, cfgp, vp, vp, vp, vp], i32),
+            "qca_decode_desync_batch_async": ([vp, i32, i64, i32, ctypes.c_double, u64, cfgp,
+                                               vp, vp, vp, vp], i32),
             "qca_net_param_count": ([], i64),
             "qca_net_create": ([u64, ctypes.POINTER(vp)], i32),
             "qca_net_destroy": ([vp], i32),
@@ -184,6 +187,47 @@ def decode_1d_batch(errors, max_steps: int = 4096, rng_seed: int = 0, *, v: int 
         ctypes.c_void_p(flag.data_ptr()), ctypes.c_void_p(maj.data_ptr()),
         _stream(torch, stream)))
     return C, steps, flag, maj
+
+
+def _variant_out(errors, out):
+    torch = _torch()
+    shots = errors.shape[0]
+    if out is None:
+        out = (torch.empty_like(errors), torch.empty(shots, dtype=torch.int32, device=errors.device),
+               torch.empty(shots, dtype=torch.uint8, device=errors.device))
+    return out
+
+
+def decode_open_batch(errors, max_steps: int = 4096, *, v: int = 3, m_max: int = 255, out=None,
+                      stream=None):
+    """Open-boundary decode of uint8 [shots][2][L][L] noise: (correction, steps, flag)."""
+    torch = _torch()
+    shots, L = errors.shape[0], errors.shape[-1]
+    _dev_u8(torch, errors, (shots, 2, L, L), "errors")
+    C, steps, fail = _variant_out(errors, out)
+    cfg = make_config(v, m_max, 0.0, 0)
+    _check(lib().qca_decode_open_batch_async(
+        ctypes.c_void_p(errors.data_ptr()), L, shots, max_steps, ctypes.byref(cfg),
+        ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(steps.data_ptr()),
+        ctypes.c_void_p(fail.data_ptr()), _stream(torch, stream)))
+    return C, steps, fail
+
+
+def decode_desync_batch(errors, q: float, max_ticks: int = 100000, rng_seed: int = 0, *,
+                        v: int = 3, m_max: int = 255, shot_offset: int = 0, out=None,
+                        stream=None):
+    """Uncoordinated (desynchronised) decode: (correction, ticks, flag)."""
+    torch = _torch()
+    shots, L = errors.shape[0], errors.shape[-1]
+    _dev_u8(torch, errors, (shots, 2, L, L), "errors")
+    C, ticks, fail = _variant_out(errors, out)
+    cfg = make_config(v, m_max, 0.0, shot_offset)
+    _check(lib().qca_decode_desync_batch_async(
+        ctypes.c_void_p(errors.data_ptr()), L, shots, max_ticks, float(q),
+        rng_seed & (2**64 - 1), ctypes.byref(cfg), ctypes.c_void_p(C.data_ptr()),
+        ctypes.c_void_p(ticks.data_ptr()), ctypes.c_void_p(fail.data_ptr()),
+        _stream(torch, stream)))
+    return C, ticks, fail
 
 
 def set_kernel_path(L: int, path: int = -1):
