@@ -697,6 +697,92 @@ def run_1d(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_variant(args, rank, world, local):
+    """Open boundaries (L = 64, p = 0.05) or uncoordinated desynchronisation
+    (torus L = 32, p = 0.03, ticks of q = 0.1), 100 000 shots each; one step is
+    one decode of the batch on the literal per-site variant kernel."""
+    import numpy as np
+    import torch
+
+    import paper_2506_03266_gb300 as qca
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    qca.build()
+    qca.lib()
+    open_ = args.workload == "open"
+    L = args.L if args.L != L_DEFAULT else (64 if open_ else 32)
+    p = args.p if args.p != P_DEFAULT else (0.05 if open_ else 0.03)
+    q = 0.1
+    shots = args.shots
+    shot0, _ = shard(rank, shots)
+    N = qca.sample_errors(L, shots, p, seed=0, shot0=shot0)
+    out = (torch.empty_like(N), torch.empty(shots, dtype=torch.int32, device="cuda"),
+           torch.empty(shots, dtype=torch.uint8, device="cuda"))
+    stream = torch.cuda.current_stream()
+
+    def decode():
+        if open_:
+            qca.decode_open_batch(N, MAX_STEPS, out=out)
+        else:
+            qca.decode_desync_batch(N, q, max_ticks=100000, rng_seed=5, shot_offset=shot0, out=out)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        decode()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        decode()
+        ev[i + 1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if dist is not None:
+        total_ms = reduce_time_max(total_ms, dist, "cuda")
+    ms_per_step = total_ms / args.steps
+    st, fl = out[1].cpu().numpy(), out[2].cpu().numpy()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    stats = step_stats(st, fl, shots)
+    unit_steps = "steps" if open_ else "ticks"
+    if not open_:
+        stats["mean_time"] = float(st.mean() * q)   # in units of the move clock's mean period
+    name = ("open-boundary decode (rough left/right boundaries), L x L grid" if open_ else
+            f"uncoordinated desynchronised decode (ticks of q={q}), L x L torus")
+    line = {
+        "metric": f"shot-decodes/s of the {name.split(',')[0]}",
+        "value": world * shots / (ms_per_step / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "site_updates_per_s": float(st.astype(np.int64).sum()) * L * L / (ms_per_step / 1e3),
+        "config": {"workload": (f"{name} L={L}, i.i.d. bit-flip p={p} (seed 0), {shots} shots "
+                                f"per GPU, v=3; {unit_steps} counted"),
+                   "L": L, "p": p, "shots_per_gpu": shots,
+                   "l2": "each CTA's state slot is reused across its shots"},
+        "decoder": stats,
+        "roofline": None,
+        "clocks": clk, "gpu_launches": args.steps, "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def ctypes_ptr(t):
     import ctypes
     return ctypes.c_void_p(t.data_ptr())
@@ -730,11 +816,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="uniform",
-                    choices=["uniform", "uneven", "net", "large", "1d"],
+                    choices=["uniform", "uneven", "net", "large", "1d", "open", "desync"],
                     help="uniform: the L=256 headline; uneven: 200 000 shots of mixed L; "
                          "net: learned pre-decoder + automaton at L=128, p=0.04; "
                          "large: L=1024 plain vs FP8 net + automaton; "
-                         "1d: the repetition-code automaton")
+                         "1d: the repetition-code automaton; open / desync: the 2D variants")
     ap.add_argument("--train-syndromes", type=int, default=1_000_000,
                     help="net workload: automaton-labelled training syndromes (untimed)")
     ap.add_argument("--autotune", action="store_true",
@@ -759,6 +845,9 @@ def main():
         return
     if args.workload == "1d":
         run_1d(args, rank, world, local)
+        return
+    if args.workload in ("open", "desync"):
+        run_variant(args, rank, world, local)
         return
 
     # CPU baseline before the first GPU call (oracle pool is spawned)
