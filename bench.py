@@ -815,6 +815,8 @@ def main():
     ap.add_argument("--shots", type=int, default=SHOTS_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-net", action="store_true",
+                    help="skip the net + automaton comparison of the default workload")
     ap.add_argument("--workload", default="uniform",
                     choices=["uniform", "uneven", "net", "large", "1d", "open", "desync"],
                     help="uniform: the L=256 headline; uneven: 200 000 shots of mixed L; "
@@ -943,6 +945,42 @@ def main():
                "h2d_bytes_per_step": int(Nh.numel()), "d2h_bytes_per_step": shots * 5}
         del Nh
 
+    # the metric's other half: net + automaton on the same noise (trained first,
+    # untimed), one warm and one timed decode with CUDA events
+    net_ca = None
+    if not args.no_net:
+        import numpy as np
+        net = qca.Net(seed=1)
+        t0 = time.perf_counter()
+        losses = net.train(L=32, iterations=(args.train_syndromes + 255) // 256, batch=256,
+                           p_lo=0.02, p_hi=0.07, seed=1, lr=2e-3)
+        train_s = time.perf_counter() - t0
+        nout = (torch.empty_like(N), torch.empty(shots, dtype=torch.int32, device="cuda"),
+                torch.empty(shots, dtype=torch.uint8, device="cuda"))
+        scratch = torch.empty_like(N)
+        net.decode_batch(N, MAX_STEPS, out=nout, scratch=scratch)
+        barrier()
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_ev.record(stream)
+        net.decode_batch(N, MAX_STEPS, out=nout, scratch=scratch)
+        b_ev.record(stream)
+        barrier()
+        net_ms = reduce_time_max(a_ev.elapsed_time(b_ev), dist, "cuda")
+        fn = nout[2].cpu().numpy()
+        pn = float((fn > 0).mean())
+        pp = float((fail_h > 0).float().mean())
+        sig = float(np.sqrt((pn * (1 - pn) + pp * (1 - pp)) / max(shots, 1)))
+        net_ca = {"shot_decodes_per_s": world * shots / (net_ms / 1e3), "ms_per_step": net_ms,
+                  "p_log": pn, "p_log_plain": pp, "p_log_diff_sigma": sig,
+                  "same_p_log_within_2sigma": bool(abs(pn - pp) <= 2 * sig),
+                  "mean_steps": float(nout[1].float().mean()),
+                  "train": {"syndromes": 256 * ((args.train_syndromes + 255) // 256),
+                            "seconds": train_s, "final_loss": float(np.mean(losses[-50:]))},
+                  "note": "bf16 pre-decoder (tensor cores) + the exact automaton on the residual; "
+                          "timed after the plain steps, outside the timed region"}
+        net.close()
+        del scratch, nout
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -969,6 +1007,7 @@ def main():
         "gpu_launches": launches,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "net_ca": net_ca,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

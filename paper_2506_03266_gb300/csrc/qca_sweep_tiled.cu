@@ -153,7 +153,7 @@ __device__ __forceinline__ T* rank_ptr(T* p, int r) {
   return cg::this_cluster().map_shared_rank(p, (unsigned)r);
 }
 
-__global__ void __launch_bounds__(kTThreads, 1) tiled_kernel(DecodeArgs a, TiledGeom g,
+__global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, TiledGeom g,
                                                              uint8_t* ws) {
   extern __shared__ __align__(128) uint8_t smem[];
   cg::cluster_group cluster = cg::this_cluster();
@@ -411,21 +411,42 @@ __global__ void __launch_bounds__(kTThreads, 1) tiled_kernel(DecodeArgs a, Tiled
           const int y = r0 + i / W, wq = i % W;
           uint32_t bits = Sx[(size_t)y * W + wq];
           while (bits) {
-            const int bpos = __ffs(bits) - 1;
-            bits &= bits - 1;
-            const int x = wq * 32 + bpos;
-            int dir = tiled_dir(Ppx[(size_t)y * L + x], Pmx[(size_t)y * L + x],
-                                Ppy[(size_t)x * L + y], Pmy[(size_t)x * L + y]);
-            if (a.move_thr) {
-              const uint64_t u = splitmix64(kstep ^ (uint64_t)((int64_t)y * L + x));
-              if (u < a.move_thr) dir = 1 + (int)(splitmix64(u) >> 62);
+            // up to four anyons of the word at a time: all sixteen field loads
+            // are issued before the first one is used
+            int xs[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              xs[k] = -1;
+              if (bits) {
+                xs[k] = wq * 32 + __ffs(bits) - 1;
+                bits &= bits - 1;
+              }
             }
-            if (!dir) continue;
-            const int kind = (dir <= 2) ? 0 : 1;
-            const int lx = (dir == 2) ? twrap(x - 1, L) : x;
-            const int ly = (dir == 4) ? twrap(y - 1, L) : y;
-            atomicOr(flip(par, 0, kind) + (size_t)ly * W + (lx >> 5), 1u << (lx & 31));
-            atomicOr(flip(par, 1, kind) + (size_t)lx * W + (ly >> 5), 1u << (ly & 31));
+            uint32_t f[4][4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const int x = xs[k] < 0 ? 0 : xs[k];
+              f[k][0] = Ppx[(size_t)y * L + x];
+              f[k][1] = Pmx[(size_t)y * L + x];
+              f[k][2] = Ppy[(size_t)x * L + y];
+              f[k][3] = Pmy[(size_t)x * L + y];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              if (xs[k] < 0) continue;
+              const int x = xs[k];
+              int dir = tiled_dir(f[k][0], f[k][1], f[k][2], f[k][3]);
+              if (a.move_thr) {
+                const uint64_t u = splitmix64(kstep ^ (uint64_t)((int64_t)y * L + x));
+                if (u < a.move_thr) dir = 1 + (int)(splitmix64(u) >> 62);
+              }
+              if (!dir) continue;
+              const int kind = (dir <= 2) ? 0 : 1;
+              const int lx = (dir == 2) ? twrap(x - 1, L) : x;
+              const int ly = (dir == 4) ? twrap(y - 1, L) : y;
+              atomicOr(flip(par, 0, kind) + (size_t)ly * W + (lx >> 5), 1u << (lx & 31));
+              atomicOr(flip(par, 1, kind) + (size_t)lx * W + (ly >> 5), 1u << (ly & 31));
+            }
           }
         }
       }

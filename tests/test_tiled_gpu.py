@@ -61,12 +61,15 @@ def test_path_selection():
         qca.set_kernel_path(96, 3)
 
 
-@pytest.mark.parametrize("p,shots", [(0.05, 120), (0.09, 60), (0.02, 60)])
-def test_forced_L128_bit_exact(p, shots):
+@pytest.mark.parametrize("p,shots,budget", [(0.05, 120, 4096), (0.09, 30, 300), (0.02, 60, 4096)])
+def test_forced_L128_bit_exact(p, shots, budget):
+    # above threshold (p = 0.09) many shots run long: a 300-step budget keeps
+    # the oracle quick and still checks exhausted shots
     qca.set_kernel_path(128, 3)
     try:
         N = oracle.sample_errors(128, shots, p, seed=11)
-        assert_same(gpu_decode(N), oracle_decode(N), f"L=128 p={p}")
+        assert_same(gpu_decode(N, max_steps=budget), oracle_decode(N, max_steps=budget),
+                    f"L=128 p={p}")
     finally:
         qca.set_kernel_path(128, -1)
 
@@ -75,8 +78,8 @@ def test_forced_L128_budget_and_options():
     qca.set_kernel_path(128, 3)
     try:
         N = oracle.sample_errors(128, 24, 0.08, seed=12)
-        for kw in [dict(max_steps=3), dict(max_steps=0), dict(m_max=7),
-                   dict(p_move=0.2, rng_seed=5)]:
+        for kw in [dict(max_steps=3), dict(max_steps=0), dict(m_max=7, max_steps=400),
+                   dict(p_move=0.2, rng_seed=5, max_steps=400)]:
             ms = kw.pop("max_steps", 4096)
             okw = {}
             if "m_max" in kw:
