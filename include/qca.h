@@ -388,6 +388,17 @@ int qca_net_set_fp8_scales(qca_net_t net, const float* scales);
 int qca_net_get_fp8_scales(qca_net_t net, float* scales);
 int qca_net_set_precision(qca_net_t net, int precision);
 
+/* Tensor path of the bf16 form's layers 2-4: 1 (default) = tcgen05 MMAs with
+ * the accumulator in tensor memory where L is a multiple of 128 (mma.sync
+ * elsewhere); 0 = mma.sync everywhere.  Both give the same arithmetic up to
+ * the fp32 accumulation order. */
+int qca_net_set_tensor_path(qca_net_t net, int use_tcgen05);
+
+/* Synchronise and report the device watchdog of the tensor-core kernels:
+ * QCA_ERR_WATCHDOG if a wait for an MMA timed out since the last call (the
+ * flag is then cleared), else QCA_OK. */
+int qca_net_status(qca_net_t net);
+
 /* Net + automaton: pre-decode, run qca_decode_batch_async on the residual
  * N xor C0 (arguments as there), then out_correction = C0 xor C_automaton.
  * out_steps counts the automaton's steps; out_logical_fail is the failure

@@ -100,6 +100,8 @@ def lib():
             "qca_net_set_fp8_scales": ([vp, vp], i32),
             "qca_net_get_fp8_scales": ([vp, vp], i32),
             "qca_net_set_precision": ([vp, i32], i32),
+            "qca_net_set_tensor_path": ([vp, i32], i32),
+            "qca_net_status": ([vp], i32),
             "qca_net_logits_async": ([vp, vp, i32, i64, vp, vp], i32),
             "qca_net_predecode_async": ([vp, vp, i32, i64, vp, vp, vp], i32),
             "qca_net_decode_batch_async": ([vp, vp, i32, i64, i32, u64, vp, vp, vp, cfgp, vp,
@@ -534,6 +536,13 @@ class Net:
     def set_precision(self, precision: str):
         """"bf16" or "fp8" for every inference entry point."""
         _check(lib().qca_net_set_precision(self.handle, {"bf16": 0, "fp8": 1}[precision]))
+
+    def set_tensor_path(self, use_tcgen05: bool):
+        _check(lib().qca_net_set_tensor_path(self.handle, 1 if use_tcgen05 else 0))
+
+    def status(self):
+        """Raises QcaError if a tensor-core wait timed out since the last call."""
+        _check(lib().qca_net_status(self.handle))
 
     def logits(self, errors, stream=None):
         """fp32 [shots][4][L][L] logits of the noise realisations' syndromes."""

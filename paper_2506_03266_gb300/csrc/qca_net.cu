@@ -554,6 +554,293 @@ __global__ void __launch_bounds__(128) conv_mma_kernel(
   }
 }
 
+// ------------------------------------------------ inference (tcgen05) -----
+//
+// Layers 2-4 of the bf16 form on the fifth-generation tensor cores, for L a
+// multiple of 128: a CTA takes tiles of 128 consecutive sites of one row and
+// issues, for each of the 9 taps and both 16-channel halves, one tcgen05.mma
+// (M = 128 sites, N = 32 output channels (16 for layer 4, 4 real), K = 16,
+// bf16 operands, fp32 accumulator in tensor memory).  Both operands sit in
+// shared memory in the no-swizzle K-major layout built from 8 x 16-byte core
+// matrices: activations as [row y-1, y, y+1][channel octet][site x0-1 ..
+// x0+128][8 bf16], so the operand of tap (dy, dx) is the same layout started
+// dx sites (16 bytes) later and the periodic wrap lives in the halo sites;
+// weights as [tap][channel octet][co][8 bf16].  The epilogue reads the
+// accumulator with tcgen05.ld (one site per thread, one column per channel).
+
+constexpr int kTcM = 128;            // sites per tile
+constexpr int kTcRow = kTcM + 2;     // staged sites per row (one halo site each side)
+constexpr int kTcThreads = 128;
+constexpr long long kTcWaitCycles = 4000000000LL;
+
+__device__ __forceinline__ uint32_t tc_smem(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, leading-dimension (K)
+// and stride-dimension (M/N) byte offsets in 16-byte units, descriptor
+// version 1 (bits 46-48), base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: D f32 (bits 4-5 = 1), A and B bf16
+// (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
+// M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t tc_idesc(int N, int M) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   tc_smem(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_proxy_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_bar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ bool tc_bar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(tc_smem(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kTcWaitCycles) return false;
+  }
+}
+
+// 32 consecutive accumulator columns of this thread's lane
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// cp.async 16-byte copy global -> shared, and its group fences
+__device__ __forceinline__ void tc_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc_smem(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void tc_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void tc_cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+constexpr int kTcStrip = 32;  // rows per work unit (a vertical strip of one 128-site column block)
+
+// NOUT = 32 (layers 2, 3; weights [tap][32][32]) or 16 (layer 4; weights
+// [tap][8][32], channels 8..15 zero).  A work unit is a strip of kTcStrip
+// rows of one 128-site column block of one shot: the staged rows live in a
+// ring of four [octet][site][16 B] buffers; while tile y's accumulator is read
+// out, the MMAs of tile y + 1 (rows y .. y + 2) run into the other of two
+// accumulators and row y + 3 streams into the buffer tile y no longer needs.
+// err: device word, set to 1 when a wait for the tensor core times out (the
+// CTA then stops).
+template <int NOUT, int MODE>
+__global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(
+    const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Wg,
+    const float* __restrict__ bias, int L, int64_t shots, __nv_bfloat16* __restrict__ out,
+    float* __restrict__ logits, const uint8_t* __restrict__ sig, uint8_t* __restrict__ prop,
+    unsigned int* __restrict__ err) {
+  constexpr int CO_SRC = NOUT == 32 ? 32 : 8;
+  constexpr uint32_t kRowBytes = 4 * kTcRow * 16;  // one staged row
+  constexpr uint32_t kA = 4 * kRowBytes;           // ring of four rows
+  constexpr uint32_t kB = 9 * 4 * NOUT * 16;       // weights
+  extern __shared__ __align__(128) uint8_t sm[];
+  uint8_t* sA = sm;
+  uint8_t* sB = sm + kA;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kA + kB);  // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kA + kB + 16);
+  float* sbias = reinterpret_cast<float*>(sm + kA + kB + 32);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  for (int i = tid; i < 9 * NOUT * 4; i += kTcThreads) {
+    const int tap = i / (NOUT * 4), rem = i % (NOUT * 4), co = rem / 4, oct = rem % 4;
+    uint4 w = make_uint4(0, 0, 0, 0);
+    if (co < CO_SRC)
+      w = *reinterpret_cast<const uint4*>(Wg + ((size_t)(tap * CO_SRC + co) * 32 + oct * 8));
+    *reinterpret_cast<uint4*>(sB + ((size_t)(tap * 4 + oct) * NOUT + co) * 16) = w;
+  }
+  for (int i = tid; i < NOUT; i += kTcThreads) sbias[i] = (MODE == kActs || i < 4) ? bias[i] : 0.f;
+  if (tid == 0) {
+    tc_bar_init(&bar[0]);
+    tc_bar_init(&bar[1]);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     tc_smem(tslot)),
+                 "r"(64)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;  // two accumulators: columns 0-31 and 32-63
+  const uint32_t idesc = tc_idesc(NOUT, kTcM);
+  const int64_t LL = (int64_t)L * L;
+  const int xblocks = L / kTcM, strips = L / kTcStrip;
+  const int64_t units = shots * xblocks * strips;
+  uint32_t phase[2] = {0u, 0u};
+  bool stop = false;
+
+  // stage row yy of (shot, x0) into ring slot `slot` (asynchronous copies)
+  auto stage = [&](int64_t shot, int yy, int x0, int slot) {
+    yy = yy < 0 ? yy + L : (yy >= L ? yy - L : yy);
+    uint8_t* dst = sA + (size_t)slot * kRowBytes;
+    const __nv_bfloat16* row = in + (shot * LL + (int64_t)yy * L) * 32;
+    for (int i = tid; i < kTcRow * 4; i += kTcThreads) {
+      const int j = i / 4, oct = i % 4;
+      int xx = x0 + j - 1;
+      xx = xx < 0 ? xx + L : (xx >= L ? xx - L : xx);
+      tc_cp16(dst + ((size_t)oct * kTcRow + j) * 16, row + (int64_t)xx * 32 + oct * 8);
+    }
+  };
+  // MMAs of tile y (rows y-1, y, y+1 in ring slots) into accumulator `acc`
+  auto issue = [&](int y, int acc) {
+    const uint32_t a0 = tc_smem(sA), b0 = tc_smem(sB);
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = tap / 3, dx = tap % 3 - 1;
+      const int slot = (y - 1 + dy + 4 * L) & 3;  // ring slot of row y - 1 + dy
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t aaddr =
+            a0 + (uint32_t)slot * kRowBytes + ((uint32_t)((2 * h) * kTcRow + 1 + dx)) * 16;
+        const uint32_t baddr = b0 + ((uint32_t)((tap * 4 + 2 * h) * NOUT)) * 16;
+        tc_mma(tmem + (uint32_t)(acc * 32), tc_desc(aaddr, kTcRow * 16, 128),
+               tc_desc(baddr, NOUT * 16, 128), idesc, (tap | h) != 0);
+      }
+    }
+    tc_commit(&bar[acc]);
+  };
+
+  for (int64_t u = blockIdx.x; u < units && !stop; u += gridDim.x) {
+    const int64_t shot = u / ((int64_t)xblocks * strips);
+    const int rem = (int)(u - shot * (int64_t)xblocks * strips);
+    const int x0 = (rem % xblocks) * kTcM, y0 = (rem / xblocks) * kTcStrip;
+    // prologue: rows y0-1 .. y0+1, then tile y0's MMAs; row y0+2 in flight
+    for (int r = -1; r <= 1; ++r) stage(shot, y0 + r, x0, (y0 + r + 4 * L) & 3);
+    tc_cp_commit();
+    tc_cp_wait_all();
+    tc_fence_proxy_shared();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      issue(y0, 0);
+    }
+    stage(shot, y0 + 2, x0, (y0 + 2 + 4 * L) & 3);
+    tc_cp_commit();
+    for (int i = 0; i < kTcStrip; ++i) {
+      const int y = y0 + i, acc = i & 1;
+      // row y + 2 has landed: tile y + 1 can start while tile y is read out
+      tc_cp_wait_all();
+      tc_fence_proxy_shared();
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0 && i + 1 < kTcStrip) {
+        tc_fence_after();
+        issue(y + 1, acc ^ 1);
+      }
+      const bool ok = tc_bar_wait(&bar[acc], phase[acc]);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(err, 1u);
+        (void)tc_bar_wait(&bar[acc], phase[acc]);
+        (void)tc_bar_wait(&bar[acc ^ 1], phase[acc ^ 1]);
+        stop = true;
+        break;
+      }
+      phase[acc] ^= 1u;
+      // tile y no longer needs row y - 1: its slot takes row y + 3
+      if (i + 2 < kTcStrip) stage(shot, y + 3, x0, (y + 3 + 4 * L) & 3);
+      tc_cp_commit();
+      tc_fence_after();
+      // epilogue: thread (warp w, lane l) holds site x0 + 32 w + l
+      const int x = x0 + 32 * warp + lane;
+      const int64_t site = shot * LL + (int64_t)y * L + x;
+      float v[32];
+      tc_ld32(tmem + (uint32_t)(acc * 32) + ((uint32_t)(32 * warp) << 16), v);
+      if (MODE == kActs) {
+        uint32_t w[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          w[c] = pack_bf16(fmaxf(v[2 * c] + sbias[2 * c], 0.f),
+                           fmaxf(v[2 * c + 1] + sbias[2 * c + 1], 0.f));
+        uint4* o = reinterpret_cast<uint4*>(out + site * 32);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          o[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+      } else {
+        const float z[4] = {v[0] + sbias[0], v[1] + sbias[1], v[2] + sbias[2], v[3] + sbias[3]};
+        if (MODE == kLogits) {
+          float* lb = logits + shot * 4 * LL + (int64_t)y * L + x;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) lb[(int64_t)k * LL] = z[k];
+        } else {
+          float best = z[0];
+          int bk = 0;
+#pragma unroll
+          for (int q = 1; q < 4; ++q)
+            if (z[q] > best) {
+              best = z[q];
+              bk = q;
+            }
+          prop[site] = (sig[site] && best > 0.f) ? (uint8_t)bk : (uint8_t)4;
+        }
+      }
+    }
+    tc_cp_wait_all();
+    __syncthreads();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64)
+                 : "memory");
+}
+
+template <int NOUT>
+constexpr size_t tc_smem_bytes() {
+  return 4 * 4 * kTcRow * 16 + 9 * 4 * NOUT * 16 + 32 + 4 * NOUT;
+}
+
 // ------------------------------------------------------ inference (FP8) ----
 //
 // FP8 (E4M3) form of layers 2-4: weights quantised per output channel,
@@ -852,6 +1139,8 @@ struct qca_net_s {
   float act_scale[3] = {0.f, 0.f, 0.f};
   int precision = 0;  // 0 bf16, 1 fp8
   bool prepared8 = false;
+  int use_tc = 1;                // bf16 layers 2-4 on tcgen05 where L % 128 == 0
+  unsigned int* err = nullptr;   // device word: a tensor-core wait timed out
   // inference workspace
   uint8_t* ws = nullptr;
   size_t ws_bytes = 0;
@@ -889,6 +1178,8 @@ int qca_net_create(uint64_t seed, qca_net_t* out) {
   if (e == cudaSuccess) e = cudaMalloc(&n->w1, sizeof(float) * 32 * 2 * 9);
   if (e == cudaSuccess) e = cudaMalloc(&n->wq, 2 * 9 * 32 * 32 + 9 * 8 * 32);
   if (e == cudaSuccess) e = cudaMalloc(&n->wscale, sizeof(float) * 96);
+  if (e == cudaSuccess) e = cudaMalloc(&n->err, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(n->err, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemcpy(n->params, h.data(), sizeof(float) * kParams, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(n->m1, 0, sizeof(float) * kParams);
   if (e == cudaSuccess) e = cudaMemset(n->m2, 0, sizeof(float) * kParams);
@@ -910,6 +1201,7 @@ int qca_net_destroy(qca_net_t n) {
   cudaFree(n->w1);
   cudaFree(n->wq);
   cudaFree(n->wscale);
+  cudaFree(n->err);
   cudaFree(n->ws);
   delete n;
   return QCA_OK;
@@ -1141,6 +1433,37 @@ int net_run(qca_net_s* n, const uint8_t* noise, int L, int64_t shots, float* log
       continue;
     }
     layer1_kernel<<<grid_for(S, 256), 256, 0, st>>>(sig, L, m, n->w1, n->params, actA);
+    if (n->use_tc && L % kTcM == 0 && L % kTcStrip == 0) {
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const int64_t units = S / ((int64_t)kTcM * kTcStrip);
+      const int gt = (int)(units < (int64_t)sms * 4 ? units : (int64_t)sms * 4);
+      cudaFuncSetAttribute(conv_tc_kernel<32, kActs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_smem_bytes<32>());
+      cudaFuncSetAttribute(conv_tc_kernel<16, kLogits>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes<16>());
+      cudaFuncSetAttribute(conv_tc_kernel<16, kProposals>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes<16>());
+      conv_tc_kernel<32, kActs><<<gt, kTcThreads, tc_smem_bytes<32>(), st>>>(
+          actA, n->wb, n->params + kB1, L, m, actB, nullptr, nullptr, nullptr, n->err);
+      conv_tc_kernel<32, kActs><<<gt, kTcThreads, tc_smem_bytes<32>(), st>>>(
+          actB, n->wb + 9 * 32 * 32, n->params + kB2, L, m, actA, nullptr, nullptr, nullptr, n->err);
+      if (logits) {
+        conv_tc_kernel<16, kLogits><<<gt, kTcThreads, tc_smem_bytes<16>(), st>>>(
+            actA, n->wb + 2 * 9 * 32 * 32, n->params + kB3, L, m, nullptr, logits + c0s * 4 * LL,
+            nullptr, nullptr, n->err);
+      } else {
+        conv_tc_kernel<16, kProposals><<<gt, kTcThreads, tc_smem_bytes<16>(), st>>>(
+            actA, n->wb + 2 * 9 * 32 * 32, n->params + kB3, L, m, nullptr, nullptr, sig, prop,
+            n->err);
+        pairing_kernel<<<grid_for(S, 256), 256, 0, st>>>(Nc, prop, L, m, resid + c0s * 2 * LL,
+                                                         c0 ? c0 + c0s * 2 * LL : nullptr);
+      }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e, "net tcgen05 inference kernels");
+      continue;
+    }
     conv_mma_kernel<4, kActs><<<gm, 128, 0, st>>>(actA, n->wb, n->params + kB1, L, m, actB,
                                                   nullptr, nullptr, nullptr);
     conv_mma_kernel<4, kActs><<<gm, 128, 0, st>>>(actB, n->wb + 9 * 32 * 32, n->params + kB2, L, m,
@@ -1209,6 +1532,32 @@ int qca_net_get_fp8_scales(qca_net_t n, float* scales) {
     return QCA_ERR_ARG;
   }
   for (int i = 0; i < 3; ++i) scales[i] = n->act_scale[i];
+  return QCA_OK;
+}
+
+int qca_net_set_tensor_path(qca_net_t n, int use_tcgen05) {
+  if (!n || (use_tcgen05 != 0 && use_tcgen05 != 1)) {
+    set_error("qca_net_set_tensor_path: 0 (mma.sync) or 1 (tcgen05 where L %% 128 == 0)");
+    return QCA_ERR_ARG;
+  }
+  n->use_tc = use_tcgen05;
+  return QCA_OK;
+}
+
+int qca_net_status(qca_net_t n) {
+  if (!n) {
+    set_error("qca_net_status: NULL net");
+    return QCA_ERR_ARG;
+  }
+  unsigned int h = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&h, n->err, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "qca_net_status");
+  if (h) {
+    cudaMemset(n->err, 0, sizeof(h));
+    set_error("qca_net_status: a tensor-core wait timed out; the outputs since the last check are unreliable");
+    return QCA_ERR_WATCHDOG;
+  }
   return QCA_OK;
 }
 

@@ -277,3 +277,51 @@ def test_fp8_net_plus_automaton_plog_within_2sigma(trained_fp8):
     b = (f_net == 1).double().mean().item()
     sigma = np.sqrt((a * (1 - a) + b * (1 - b)) / shots)
     assert a > 0.0 and abs(a - b) <= 2 * sigma + 1e-12, (a, b, sigma)
+
+
+# ------------------------------------------------ tcgen05 path (L % 128 == 0)
+
+def test_tcgen05_logits_match_fp64_and_mma_path(trained):
+    # The tcgen05 and mma.sync paths accumulate the same products in the same
+    # order: their logits agree bit for bit.  Against the FP64 forward, an
+    # intermediate activation whose fp32 and fp64 values straddle a bf16
+    # rounding boundary differs by one bf16 step (|a| 2^-8) and moves a logit
+    # by up to |W| times that: at L = 128 (3 M activations per shot) a few such
+    # flips occur, so the bar is 99.99 % of logits within 1e-2 and none beyond
+    # 0.03; the small lattices above hold every logit to 1e-2.
+    net, _ = trained
+    L, shots = 128, 2
+    N = oracle.sample_errors(L, shots, 0.05, seed=51)
+    Nd = dev(N)
+    net.set_tensor_path(True)
+    z_tc = net.logits(Nd).cpu().numpy()
+    net.status()
+    net.set_tensor_path(False)
+    z_ms = net.logits(Nd).cpu().numpy()
+    net.set_tensor_path(True)
+    np.testing.assert_array_equal(z_tc, z_ms)
+    params = net.get_params()
+    A = anyon_maps(N)
+    d = np.concatenate([np.abs(z_tc[s] - onet.forward(A[s], params, quantize=True)).ravel()
+                        for s in range(shots)])
+    assert np.mean(d <= 1e-2) >= 0.9999 and d.max() <= 0.03, (np.mean(d <= 1e-2), d.max())
+
+
+def test_tcgen05_pairing_bit_exact_and_decode(trained):
+    net, _ = trained
+    net.set_tensor_path(True)
+    L, shots = 256, 3
+    N = oracle.sample_errors(L, shots, 0.05, seed=52)
+    Nd = dev(N)
+    z = net.logits(Nd).cpu().numpy()
+    R, C0 = net.predecode(Nd)
+    C, steps, fail = net.decode_batch(Nd)
+    net.status()
+    R, C0 = R.cpu().numpy(), C0.cpu().numpy()
+    A = anyon_maps(N)
+    for s in range(shots):
+        np.testing.assert_array_equal(C0[s], onet.pairing_links(A[s], onet.proposals(A[s], z[s])))
+    np.testing.assert_array_equal(R, N ^ C0)
+    Co, so, fo = oracle.decode_shot(R[0], max_steps=4096)
+    np.testing.assert_array_equal(C[0].cpu().numpy(), Co ^ C0[0])
+    assert (int(steps[0]), int(fail[0])) == (so, fo)
