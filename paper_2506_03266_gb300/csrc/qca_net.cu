@@ -554,6 +554,22 @@ __global__ void __launch_bounds__(128) conv_mma_kernel(
   }
 }
 
+// Layer 1 as a table: its output at a site depends only on the 3 x 3 anyon
+// pattern around it (bit tap = ky * 3 + kx).  Entry p holds the 32 bf16
+// outputs for pattern p, summed in the order layer1_kernel uses (bias, the
+// constant channel's taps, then the anyon taps), so both give the same bits.
+__global__ void layer1_lut_kernel(const float* __restrict__ W1, const float* __restrict__ P,
+                                  __nv_bfloat16* __restrict__ lut) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 512 * 32; i += gridDim.x * blockDim.x) {
+    const int pat = i / 32, co = i % 32;
+    float b = P[kB0 + co];
+    for (int tap = 0; tap < 9; ++tap) b += W1[co * 18 + 9 + tap];
+    for (int tap = 0; tap < 9; ++tap)
+      if ((pat >> tap) & 1) b += W1[co * 18 + tap];
+    lut[i] = __float2bfloat16_rn(fmaxf(b, 0.f));
+  }
+}
+
 // ------------------------------------------------ inference (tcgen05) -----
 //
 // Layers 2-4 of the bf16 form on the fifth-generation tensor cores, for L a
@@ -659,6 +675,10 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
 __device__ __forceinline__ void tc_cp16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc_smem(dst)), "l"(src) : "memory");
 }
+// the same through L1 (for small tables that stay cached)
+__device__ __forceinline__ void tc_cp16_ca(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(tc_smem(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void tc_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void tc_cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
@@ -672,12 +692,15 @@ constexpr int kTcStrip = 32;  // rows per work unit (a vertical strip of one 128
 // accumulators and row y + 3 streams into the buffer tile y no longer needs.
 // err: device word, set to 1 when a wait for the tensor core times out (the
 // CTA then stops).
-template <int NOUT, int MODE>
+// FROM_SIG: the layer's input is layer 1 of the net, looked up while staging
+// from the anyon bytes `sig` in the table `lut` of layer-1 outputs per 3 x 3
+// anyon pattern, so the layer-1 activations never reach global memory.
+template <int NOUT, int MODE, bool FROM_SIG>
 __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(
     const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Wg,
     const float* __restrict__ bias, int L, int64_t shots, __nv_bfloat16* __restrict__ out,
     float* __restrict__ logits, const uint8_t* __restrict__ sig, uint8_t* __restrict__ prop,
-    unsigned int* __restrict__ err) {
+    unsigned int* __restrict__ err, const __nv_bfloat16* __restrict__ lut) {
   constexpr int CO_SRC = NOUT == 32 ? 32 : 8;
   constexpr uint32_t kRowBytes = 4 * kTcRow * 16;  // one staged row
   constexpr uint32_t kA = 4 * kRowBytes;           // ring of four rows
@@ -724,6 +747,27 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(
   auto stage = [&](int64_t shot, int yy, int x0, int slot) {
     yy = yy < 0 ? yy + L : (yy >= L ? yy - L : yy);
     uint8_t* dst = sA + (size_t)slot * kRowBytes;
+    if (FROM_SIG) {
+      // layer 1 (2 -> 32, ReLU, bf16) of every staged site: its 3 x 3 anyon
+      // pattern indexes the 512-entry table `lut` (64 bytes per pattern)
+      const uint8_t* g = sig + shot * LL;
+      const int ym = yy == 0 ? L - 1 : yy - 1, yp = yy == L - 1 ? 0 : yy + 1;
+      for (int j = tid; j < kTcRow; j += kTcThreads) {
+        int xx = x0 + j - 1;
+        xx = xx < 0 ? xx + L : (xx >= L ? xx - L : xx);
+        const int xm = xx == 0 ? L - 1 : xx - 1, xp = xx == L - 1 ? 0 : xx + 1;
+        const int rows[3] = {ym, yy, yp}, cols[3] = {xm, xx, xp};
+        uint32_t idx = 0;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap)
+          idx |= (g[(int64_t)rows[tap / 3] * L + cols[tap % 3]] ? 1u : 0u) << tap;
+        const __nv_bfloat16* src = lut + (size_t)idx * 32;
+#pragma unroll
+        for (int oct = 0; oct < 4; ++oct)
+          tc_cp16_ca(dst + ((size_t)oct * kTcRow + j) * 16, src + oct * 8);
+      }
+      return;
+    }
     const __nv_bfloat16* row = in + (shot * LL + (int64_t)yy * L) * 32;
     for (int i = tid; i < kTcRow * 4; i += kTcThreads) {
       const int j = i / 4, oct = i % 4;
@@ -1141,6 +1185,7 @@ struct qca_net_s {
   bool prepared8 = false;
   int use_tc = 1;                // bf16 layers 2-4 on tcgen05 where L % 128 == 0
   unsigned int* err = nullptr;   // device word: a tensor-core wait timed out
+  __nv_bfloat16* lut = nullptr;  // layer-1 outputs per 3 x 3 anyon pattern [512][32]
   // inference workspace
   uint8_t* ws = nullptr;
   size_t ws_bytes = 0;
@@ -1179,6 +1224,7 @@ int qca_net_create(uint64_t seed, qca_net_t* out) {
   if (e == cudaSuccess) e = cudaMalloc(&n->wq, 2 * 9 * 32 * 32 + 9 * 8 * 32);
   if (e == cudaSuccess) e = cudaMalloc(&n->wscale, sizeof(float) * 96);
   if (e == cudaSuccess) e = cudaMalloc(&n->err, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&n->lut, sizeof(__nv_bfloat16) * 512 * 32);
   if (e == cudaSuccess) e = cudaMemset(n->err, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemcpy(n->params, h.data(), sizeof(float) * kParams, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(n->m1, 0, sizeof(float) * kParams);
@@ -1202,6 +1248,7 @@ int qca_net_destroy(qca_net_t n) {
   cudaFree(n->wq);
   cudaFree(n->wscale);
   cudaFree(n->err);
+  cudaFree(n->lut);
   cudaFree(n->ws);
   delete n;
   return QCA_OK;
@@ -1378,6 +1425,7 @@ int net_run(qca_net_s* n, const uint8_t* noise, int L, int64_t shots, float* log
             uint8_t* resid, uint8_t* c0, cudaStream_t st) {
   if (!n->prepared) {
     prepare_weights_kernel<<<64, 256, 0, st>>>(n->params, n->wb, n->w1);
+    layer1_lut_kernel<<<64, 256, 0, st>>>(n->w1, n->params, n->lut);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "prepare weights");
     n->prepared = true;
@@ -1432,31 +1480,34 @@ int net_run(qca_net_s* n, const uint8_t* noise, int L, int64_t shots, float* log
       if (e != cudaSuccess) return cuda_fail(e, "net fp8 inference kernels");
       continue;
     }
-    layer1_kernel<<<grid_for(S, 256), 256, 0, st>>>(sig, L, m, n->w1, n->params, actA);
     if (n->use_tc && L % kTcM == 0 && L % kTcStrip == 0) {
       int dev = 0, sms = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       const int64_t units = S / ((int64_t)kTcM * kTcStrip);
       const int gt = (int)(units < (int64_t)sms * 4 ? units : (int64_t)sms * 4);
-      cudaFuncSetAttribute(conv_tc_kernel<32, kActs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)tc_smem_bytes<32>());
-      cudaFuncSetAttribute(conv_tc_kernel<16, kLogits>,
+      cudaFuncSetAttribute(conv_tc_kernel<32, kActs, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes<32>());
+      cudaFuncSetAttribute(conv_tc_kernel<32, kActs, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes<32>());
+      cudaFuncSetAttribute(conv_tc_kernel<16, kLogits, false>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes<16>());
-      cudaFuncSetAttribute(conv_tc_kernel<16, kProposals>,
+      cudaFuncSetAttribute(conv_tc_kernel<16, kProposals, false>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes<16>());
-      conv_tc_kernel<32, kActs><<<gt, kTcThreads, tc_smem_bytes<32>(), st>>>(
-          actA, n->wb, n->params + kB1, L, m, actB, nullptr, nullptr, nullptr, n->err);
-      conv_tc_kernel<32, kActs><<<gt, kTcThreads, tc_smem_bytes<32>(), st>>>(
-          actB, n->wb + 9 * 32 * 32, n->params + kB2, L, m, actA, nullptr, nullptr, nullptr, n->err);
+      // layers 1 + 2 (layer 1 computed while staging), 3, 4
+      conv_tc_kernel<32, kActs, true><<<gt, kTcThreads, tc_smem_bytes<32>(), st>>>(
+          nullptr, n->wb, n->params + kB1, L, m, actB, nullptr, sig, nullptr, n->err, n->lut);
+      conv_tc_kernel<32, kActs, false><<<gt, kTcThreads, tc_smem_bytes<32>(), st>>>(
+          actB, n->wb + 9 * 32 * 32, n->params + kB2, L, m, actA, nullptr, nullptr, nullptr,
+          n->err, nullptr);
       if (logits) {
-        conv_tc_kernel<16, kLogits><<<gt, kTcThreads, tc_smem_bytes<16>(), st>>>(
+        conv_tc_kernel<16, kLogits, false><<<gt, kTcThreads, tc_smem_bytes<16>(), st>>>(
             actA, n->wb + 2 * 9 * 32 * 32, n->params + kB3, L, m, nullptr, logits + c0s * 4 * LL,
-            nullptr, nullptr, n->err);
+            nullptr, nullptr, n->err, nullptr);
       } else {
-        conv_tc_kernel<16, kProposals><<<gt, kTcThreads, tc_smem_bytes<16>(), st>>>(
+        conv_tc_kernel<16, kProposals, false><<<gt, kTcThreads, tc_smem_bytes<16>(), st>>>(
             actA, n->wb + 2 * 9 * 32 * 32, n->params + kB3, L, m, nullptr, nullptr, sig, prop,
-            n->err);
+            n->err, nullptr);
         pairing_kernel<<<grid_for(S, 256), 256, 0, st>>>(Nc, prop, L, m, resid + c0s * 2 * LL,
                                                          c0 ? c0 + c0s * 2 * LL : nullptr);
       }
@@ -1464,6 +1515,7 @@ int net_run(qca_net_s* n, const uint8_t* noise, int L, int64_t shots, float* log
       if (e != cudaSuccess) return cuda_fail(e, "net tcgen05 inference kernels");
       continue;
     }
+    layer1_kernel<<<grid_for(S, 256), 256, 0, st>>>(sig, L, m, n->w1, n->params, actA);
     conv_mma_kernel<4, kActs><<<gm, 128, 0, st>>>(actA, n->wb, n->params + kB1, L, m, actB,
                                                   nullptr, nullptr, nullptr);
     conv_mma_kernel<4, kActs><<<gm, 128, 0, st>>>(actB, n->wb + 9 * 32 * 32, n->params + kB2, L, m,
@@ -1582,6 +1634,7 @@ int qca_net_calibrate_fp8(qca_net_t n, const uint8_t* noise, int L, int64_t shot
   cudaStream_t st = (cudaStream_t)stream;
   if (!n->prepared) {
     prepare_weights_kernel<<<64, 256, 0, st>>>(n->params, n->wb, n->w1);
+    layer1_lut_kernel<<<64, 256, 0, st>>>(n->w1, n->params, n->lut);
     n->prepared = true;
   }
   const int64_t LL = (int64_t)L * L;
