@@ -586,7 +586,7 @@ __global__ void layer1_lut_kernel(const float* __restrict__ W1, const float* __r
 
 constexpr int kTcM = 128;            // sites per tile
 constexpr int kTcRow = kTcM + 2;     // staged sites per row (one halo site each side)
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;   // two warpgroups: each reads half the accumulator columns
 constexpr long long kTcWaitCycles = 4000000000LL;
 
 __device__ __forceinline__ uint32_t tc_smem(const void* p) {
@@ -654,23 +654,6 @@ __device__ __forceinline__ bool tc_bar_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
-// 32 consecutive accumulator columns of this thread's lane
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // cp.async 16-byte copy global -> shared, and its group fences
 __device__ __forceinline__ void tc_cp16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc_smem(dst)), "l"(src) : "memory");
@@ -682,7 +665,22 @@ __device__ __forceinline__ void tc_cp16_ca(void* dst, const void* src) {
 __device__ __forceinline__ void tc_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void tc_cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-constexpr int kTcStrip = 32;  // rows per work unit (a vertical strip of one 128-site column block)
+constexpr int kTcStrip = 64;  // rows per work unit (a vertical strip of one 128-site column block)
+
+// 16 consecutive accumulator columns of this thread's lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
 
 // NOUT = 32 (layers 2, 3; weights [tap][32][32]) or 16 (layer 4; weights
 // [tap][8][32], channels 8..15 zero).  A work unit is a strip of kTcStrip
@@ -835,22 +833,22 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(
       if (i + 2 < kTcStrip) stage(shot, y + 3, x0, (y + 3 + 4 * L) & 3);
       tc_cp_commit();
       tc_fence_after();
-      // epilogue: thread (warp w, lane l) holds site x0 + 32 w + l
-      const int x = x0 + 32 * warp + lane;
+      // epilogue: thread (warp w, lane l) holds site x0 + 32 (w % 4) + l; the
+      // warpgroup w / 4 reads accumulator columns 16 (w / 4) .. + 15
+      const int x = x0 + 32 * (warp & 3) + lane, half = warp >> 2;
       const int64_t site = shot * LL + (int64_t)y * L + x;
-      float v[32];
-      tc_ld32(tmem + (uint32_t)(acc * 32) + ((uint32_t)(32 * warp) << 16), v);
+      float v[16];
+      tc_ld16(tmem + (uint32_t)(acc * 32 + 16 * half) + ((uint32_t)(32 * (warp & 3)) << 16), v);
       if (MODE == kActs) {
-        uint32_t w[16];
+        uint32_t w[8];
 #pragma unroll
-        for (int c = 0; c < 16; ++c)
-          w[c] = pack_bf16(fmaxf(v[2 * c] + sbias[2 * c], 0.f),
-                           fmaxf(v[2 * c + 1] + sbias[2 * c + 1], 0.f));
-        uint4* o = reinterpret_cast<uint4*>(out + site * 32);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          o[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
-      } else {
+        for (int c = 0; c < 8; ++c)
+          w[c] = pack_bf16(fmaxf(v[2 * c] + sbias[16 * half + 2 * c], 0.f),
+                           fmaxf(v[2 * c + 1] + sbias[16 * half + 2 * c + 1], 0.f));
+        uint4* o = reinterpret_cast<uint4*>(out + site * 32 + 16 * half);
+        o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+      } else if (half == 0) {
         const float z[4] = {v[0] + sbias[0], v[1] + sbias[1], v[2] + sbias[2], v[3] + sbias[3]};
         if (MODE == kLogits) {
           float* lb = logits + shot * 4 * LL + (int64_t)y * L + x;
