@@ -182,3 +182,69 @@ def forward_fp8(anyon: np.ndarray, params: np.ndarray, act_scales) -> np.ndarray
         if i < len(layers) - 1:
             x = np.maximum(x, 0.0)
     return x
+
+
+# ------------------------------------------------------------- training
+
+LABEL_SMOOTHING = 0.1
+
+
+def loss_and_grads(anyons: np.ndarray, labels: np.ndarray, params: np.ndarray):
+    """Mean smoothed cross-entropy over the labelled sites of a batch and its
+    gradient with respect to the flat parameters, in float64 without
+    quantisation.  anyons: uint8 [B][L][L]; labels: uint8 [B][L][L] (0..3
+    direction, 4 no move, 255 ignored).  The fifth class has logit 0; the
+    target puts 1 - eps + eps/5 on the label and eps/5 elsewhere.
+
+    Backward pass of the four circular 3x3 convolutions written out: for
+    out = conv(x, W) + b, dW[o][c][ky][kx] = sum_s dout[o][s] x[c][s + (ky-1, kx-1)],
+    db[o] = sum_s dout[o][s], dx[c][s] = sum_{o,ky,kx} W[o][c][ky][kx]
+    dout[o][s - (ky-1, kx-1)]; ReLU passes the gradient where its output is
+    positive."""
+    layers = unpack(params)
+    B = anyons.shape[0]
+    grads = [(np.zeros_like(W), np.zeros_like(b)) for W, b in layers]
+    loss = 0.0
+    n = int(np.sum(labels != 255))
+    if n == 0:
+        return 0.0, np.zeros(param_count())
+    q_off = LABEL_SMOOTHING / 5.0
+    q_on = 1.0 - LABEL_SMOOTHING + q_off
+    for bi in range(B):
+        a = anyons[bi]
+        xs = [np.stack([a.astype(np.float64), np.ones_like(a, dtype=np.float64)])]
+        for i, (W, b) in enumerate(layers):
+            y = conv3x3_circular(xs[-1], W, b)
+            xs.append(np.maximum(y, 0.0) if i < len(layers) - 1 else y)
+        z = xs[-1]                                   # [4][L][L]
+        lab = labels[bi]
+        zz = np.concatenate([z, np.zeros((1,) + z.shape[1:])])   # fifth class
+        m = zz.max(axis=0)
+        lse = m + np.log(np.exp(zz - m).sum(axis=0))
+        p = np.exp(zz - lse)
+        q = np.full_like(zz, q_off)
+        valid = lab != 255
+        for k in range(5):
+            q[k][lab == k] = q_on
+        loss += float(np.sum((q * (lse - zz))[:, valid]))
+        dz = ((p - q)[:4]) * valid / n
+        d = dz
+        for i in range(len(layers) - 1, -1, -1):
+            W, b = layers[i]
+            x = xs[i]
+            gW, gb = grads[i]
+            for ky in range(3):
+                for kx in range(3):
+                    shifted = np.roll(x, shift=(1 - ky, 1 - kx), axis=(1, 2))
+                    gW[:, :, ky, kx] += np.einsum("oyx,cyx->oc", d, shifted)
+            gb += d.sum(axis=(1, 2))
+            if i == 0:
+                break
+            dx = np.zeros_like(x)
+            for ky in range(3):
+                for kx in range(3):
+                    contrib = np.einsum("oc,oyx->cyx", W[:, :, ky, kx], d)
+                    dx += np.roll(contrib, shift=(ky - 1, kx - 1), axis=(1, 2))
+            d = dx * (x > 0)
+    flat = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
+    return loss / n, flat

@@ -278,3 +278,53 @@ def test_forward_fp8_close_to_bf16_form():
     z8 = onet.forward_fp8(anyon, params, scales)
     assert np.max(np.abs(z8 - zb)) < 0.2 * max(1.0, np.max(np.abs(zb)))
     assert np.max(np.abs(z8 - zb)) > 0  # the FP8 points do change the result
+
+
+# ---------------------------------------------------------------- training
+
+def test_loss_and_grads_match_torch_autograd():
+    r = np.random.default_rng(12)
+    B, L = 2, 7
+    anyons = (r.random((B, L, L)) < 0.25).astype(np.uint8)
+    labels = np.where(anyons == 1, r.integers(0, 5, (B, L, L)), 255).astype(np.uint8)
+    params = rng_params(13, scale=0.2)
+    loss, g = onet.loss_and_grads(anyons, labels, params)
+    p = torch.tensor(params.astype(np.float64), requires_grad=True)
+    x = torch.from_numpy(np.stack([anyons.astype(np.float64), np.ones((B, L, L))], axis=1))
+    o = 0
+    for i, (co, ci) in enumerate(onet.LAYERS):
+        W = p[o:o + co * ci * 9].reshape(co, ci, 3, 3)
+        o += co * ci * 9
+        b = p[o:o + co]
+        o += co
+        x = torch.nn.functional.conv2d(torch.nn.functional.pad(x, (1, 1, 1, 1), mode="circular"),
+                                       W, b)
+        if i < 3:
+            x = torch.relu(x)
+    z = torch.cat([x, torch.zeros(B, 1, L, L, dtype=torch.float64)], dim=1)   # [B][5][L][L]
+    lab = torch.from_numpy(labels.astype(np.int64))
+    valid = lab != 255
+    eps = onet.LABEL_SMOOTHING
+    logp = torch.log_softmax(z, dim=1)
+    onehot = torch.nn.functional.one_hot(torch.where(valid, lab, 0), 5).permute(0, 3, 1, 2)
+    q = eps / 5 + (1 - eps) * onehot.double()
+    tl = -(q * logp).sum(dim=1)[valid].mean()
+    tl.backward()
+    assert loss == pytest.approx(float(tl), rel=1e-12)
+    np.testing.assert_allclose(g, p.grad.numpy(), rtol=1e-9, atol=1e-12)
+
+
+def test_loss_and_grads_finite_differences():
+    r = np.random.default_rng(14)
+    B, L = 1, 5
+    anyons = (r.random((B, L, L)) < 0.3).astype(np.uint8)
+    labels = np.where(anyons == 1, r.integers(0, 5, (B, L, L)), 255).astype(np.uint8)
+    params = rng_params(15, scale=0.2).astype(np.float64)
+    _, g = onet.loss_and_grads(anyons, labels, params)
+    for k in r.choice(onet.param_count(), 12, replace=False):
+        h = 1e-5
+        pp, pm = params.copy(), params.copy()
+        pp[k] += h
+        pm[k] -= h
+        num = (onet.loss_and_grads(anyons, labels, pp)[0] - onet.loss_and_grads(anyons, labels, pm)[0]) / (2 * h)
+        assert num == pytest.approx(g[k], rel=1e-4, abs=1e-9), k
