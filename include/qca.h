@@ -343,11 +343,21 @@ int qca_net_set_params(qca_net_t net, const float* host_params, int64_t count);
  * advances across calls on the same handle).  Loss: mean softmax
  * cross-entropy over the anyon sites against the first-step labels above,
  * smoothed by 0.1 (that mass spread evenly over the five classes).
- * Forward and backward run in fp32 on the device.  out_losses (HOST, may be
+ * Forward, input gradients and weight gradients run as bf16 tensor-core
+ * implicit GEMMs with fp32 accumulation and fp32 master weights.  out_losses (HOST, may be
  * NULL) receives one loss per iteration.  4 <= L <= 128, batch * L * L <=
  * 2^24.  Allocates its buffers for the duration of the call; synchronous. */
 int qca_net_train(qca_net_t net, int L, int64_t iterations, int batch, double p_lo, double p_hi,
                   uint64_t seed, float lr, float* out_losses);
+
+/* One forward and backward pass of the training loss on given noise
+ * realisations (device uint8 [batch][2][L][L], labels from the automaton's
+ * first step as for qca_net_train) without updating the weights: host_grads
+ * (HOST, count = qca_net_param_count() floats) receives the gradient in the
+ * parameter layout, *host_loss (may be NULL) the loss.  Same arithmetic as a
+ * training step.  4 <= L <= 128; synchronous. */
+int qca_net_gradients(qca_net_t net, const uint8_t* noise, int L, int batch, float* host_grads,
+                      int64_t count, float* host_loss);
 
 /* First-step labels of noise realisations: noise uint8 [shots][2][L][L],
  * out_labels uint8 [shots][L][L] (values as above), scratch >= 2 * shots * L^2

@@ -94,6 +94,7 @@ def lib():
             "qca_net_set_params": ([vp, vp, i64], i32),
             "qca_net_train": ([vp, i32, i64, i32, ctypes.c_double, ctypes.c_double, u64,
                                ctypes.c_float, vp], i32),
+            "qca_net_gradients": ([vp, vp, i32, i32, vp, i64, vp], i32),
             "qca_net_labels_async": ([vp, i32, i64, vp, vp, vp], i32),
             "qca_net_chunk_shots": ([i32], i64),
             "qca_net_calibrate_fp8": ([vp, vp, i32, i64, vp], i32),
@@ -543,6 +544,20 @@ class Net:
     def status(self):
         """Raises QcaError if a tensor-core wait timed out since the last call."""
         _check(lib().qca_net_status(self.handle))
+
+    def gradients(self, errors):
+        """(loss, flat fp32 gradient) of the training loss on these noise
+        realisations (cuda uint8 [batch][2][L][L]); the weights are unchanged."""
+        import numpy as np
+        torch = _torch()
+        batch, L = errors.shape[0], errors.shape[-1]
+        _dev_u8(torch, errors, (batch, 2, L, L), "errors")
+        g = np.zeros(self.param_count(), dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(lib().qca_net_gradients(self.handle, ctypes.c_void_p(errors.data_ptr()), L, batch,
+                                       g.ctypes.data_as(ctypes.c_void_p), g.size,
+                                       ctypes.byref(loss)))
+        return loss.value, g
 
     def logits(self, errors, stream=None):
         """fp32 [shots][4][L][L] logits of the noise realisations' syndromes."""

@@ -14,11 +14,13 @@
 // the cone distances <= 3), kept when its neighbour in that direction moves
 // back (the pair annihilates in that step); other anyons get label 4 (none).
 //
-// Inference: layer 1 on CUDA cores (2 input channels), layers 2-4 as
-// implicit-GEMM convolutions on the tensor cores (mma.sync m16n8k16, bf16
-// operands, fp32 accumulation), activations bf16 in NHWC layout.
-// Training: fp32 kernels on the CUDA cores (forward, softmax cross-entropy,
-// backward data/weights, Adam).
+// Inference: layers 2-4 as implicit-GEMM convolutions on the tensor cores,
+// bf16 operands and fp32 accumulation: tcgen05 with the accumulator in tensor
+// memory where L is a multiple of 128 (layer 1 then a table of the 512 3 x 3
+// anyon patterns), mma.sync elsewhere (layer 1 on the CUDA cores);
+// activations bf16 in NHWC layout.
+// Training: bf16 tensor-core implicit GEMMs with fp32 accumulation and fp32
+// master weights (forward, input gradients, weight gradients), Adam.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <math.h>
@@ -159,49 +161,6 @@ __global__ void train_sample_kernel(int L, int B, int64_t it, uint64_t seed, uin
   }
 }
 
-// input layer activations: channel 0 = anyon, channel 1 = 1 (fp32 NCHW)
-__global__ void input_f32_kernel(const uint8_t* __restrict__ sig, int L, int B,
-                                 float* __restrict__ x) {
-  const int LL = L * L;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B * LL; i += gridDim.x * blockDim.x) {
-    const int b = i / LL, r = i - b * LL;
-    x[(size_t)b * 2 * LL + r] = sig[i] ? 1.f : 0.f;
-    x[(size_t)b * 2 * LL + LL + r] = 1.f;
-  }
-}
-
-// out[b][co][y][x] = bias[co] + sum W[co][ci][ky][kx] in[b][ci][y+ky-1][x+kx-1]
-template <int CI, int CO, bool RELU>
-__global__ void conv_fwd_f32(const float* __restrict__ in, const float* __restrict__ W,
-                             const float* __restrict__ bias, int L, int B,
-                             float* __restrict__ out) {
-  __shared__ float sW[CO * CI * 9];
-  __shared__ float sb[CO];
-  for (int i = threadIdx.x; i < CO * CI * 9; i += blockDim.x) sW[i] = W[i];
-  for (int i = threadIdx.x; i < CO; i += blockDim.x) sb[i] = bias[i];
-  __syncthreads();
-  const int LL = L * L;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B * LL; i += gridDim.x * blockDim.x) {
-    const int b = i / LL, r = i - b * LL, x = r % L, y = r / L;
-    float acc[CO];
-#pragma unroll
-    for (int co = 0; co < CO; ++co) acc[co] = sb[co];
-    const float* ib = in + (size_t)b * CI * LL;
-    for (int ky = 0; ky < 3; ++ky)
-      for (int kx = 0; kx < 3; ++kx) {
-        const int nb = wrapL(y + ky - 1, L) * L + wrapL(x + kx - 1, L);
-        for (int ci = 0; ci < CI; ++ci) {
-          const float v = ib[(size_t)ci * LL + nb];
-#pragma unroll
-          for (int co = 0; co < CO; ++co) acc[co] += sW[((co * CI + ci) * 3 + ky) * 3 + kx] * v;
-        }
-      }
-    float* ob = out + (size_t)b * CO * LL;
-#pragma unroll
-    for (int co = 0; co < CO; ++co) ob[(size_t)co * LL + r] = RELU ? fmaxf(acc[co], 0.f) : acc[co];
-  }
-}
-
 __global__ void count_labelled_kernel(const uint8_t* __restrict__ lab, int n,
                                       unsigned int* __restrict__ count) {
   unsigned int c = 0;
@@ -216,135 +175,6 @@ __global__ void count_labelled_kernel(const uint8_t* __restrict__ lab, int n,
 // log((1 - eps + eps/5) / (eps/5)), about 3.8 at eps = 0.1), which keeps the
 // activations, and so the size of one bf16 rounding step in them, small.
 constexpr float kLabelSmoothing = 0.1f;
-
-// Softmax over (z0..z3, 0) at labelled sites, the fifth class ("no move")
-// with its logit fixed at 0; target q = smoothed one-hot of the label;
-// dz = (p - q) / n_labelled, loss = mean cross-entropy -sum q log p.
-__global__ void loss_grad_kernel(const float* __restrict__ z, const uint8_t* __restrict__ lab,
-                                 int L, int B, const unsigned int* __restrict__ count,
-                                 float* __restrict__ dz, float* __restrict__ loss) {
-  const int LL = L * L;
-  const float inv_n = 1.f / (float)(*count > 0 ? *count : 1u);
-  const float q_off = kLabelSmoothing / 5.f, q_on = 1.f - kLabelSmoothing + q_off;
-  float local = 0.f;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B * LL; i += gridDim.x * blockDim.x) {
-    const int b = i / LL, r = i - b * LL;
-    const float* zb = z + (size_t)b * 4 * LL;
-    float* db = dz + (size_t)b * 4 * LL;
-    const int t = lab[i];
-    if (t == 255) {
-      for (int k = 0; k < 4; ++k) db[(size_t)k * LL + r] = 0.f;
-      continue;
-    }
-    float v[5] = {zb[r], zb[LL + r], zb[2 * LL + r], zb[3 * LL + r], 0.f};
-    float mx = v[0];
-    for (int k = 1; k < 5; ++k) mx = fmaxf(mx, v[k]);
-    float sum = 0.f;
-    for (int k = 0; k < 5; ++k) sum += expf(v[k] - mx);
-    const float lse = mx + logf(sum);
-    for (int k = 0; k < 5; ++k) {
-      const float q = (t == k) ? q_on : q_off;
-      const float pk = expf(v[k] - lse);
-      if (k < 4) db[(size_t)k * LL + r] = (pk - q) * inv_n;
-      local += q * (lse - v[k]);
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xFFFFFFFFu, local, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(loss, local * inv_n);
-}
-
-// din[b][ci][y][x] = sum W[co][ci][ky][kx] dout[b][co][y-ky+1][x-kx+1], times the
-// ReLU mask of the forward input (act > 0) when MASK
-template <int CI, int CO, bool MASK>
-__global__ void conv_bwd_data_f32(const float* __restrict__ dout, const float* __restrict__ W,
-                                  const float* __restrict__ act, int L, int B,
-                                  float* __restrict__ din) {
-  __shared__ float sW[CO * CI * 9];
-  for (int i = threadIdx.x; i < CO * CI * 9; i += blockDim.x) sW[i] = W[i];
-  __syncthreads();
-  const int LL = L * L;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B * LL; i += gridDim.x * blockDim.x) {
-    const int b = i / LL, r = i - b * LL, x = r % L, y = r / L;
-    float acc[CI];
-#pragma unroll
-    for (int ci = 0; ci < CI; ++ci) acc[ci] = 0.f;
-    const float* db = dout + (size_t)b * CO * LL;
-    for (int ky = 0; ky < 3; ++ky)
-      for (int kx = 0; kx < 3; ++kx) {
-        const int nb = wrapL(y - ky + 1, L) * L + wrapL(x - kx + 1, L);
-        for (int co = 0; co < CO; ++co) {
-          const float g = db[(size_t)co * LL + nb];
-#pragma unroll
-          for (int ci = 0; ci < CI; ++ci) acc[ci] += sW[((co * CI + ci) * 3 + ky) * 3 + kx] * g;
-        }
-      }
-    float* ob = din + (size_t)b * CI * LL;
-    const float* ab = act + (size_t)b * CI * LL;
-#pragma unroll
-    for (int ci = 0; ci < CI; ++ci)
-      ob[(size_t)ci * LL + r] = (MASK && ab[(size_t)ci * LL + r] <= 0.f) ? 0.f : acc[ci];
-  }
-}
-
-// dW[co][ci][ky][kx] += sum_sites dout[co][s] in[ci][s + (ky-1, kx-1)], db[co] += sum dout
-// One CTA per chunk of sites; thread t owns entries t, t + blockDim, ...
-template <int CI, int CO>
-__global__ void conv_bwd_weight_f32(const float* __restrict__ in, const float* __restrict__ dout,
-                                    int L, int B, int chunk, float* __restrict__ dW,
-                                    float* __restrict__ dbias) {
-  constexpr int NE = CO * CI * 9;
-  constexpr int T = 32;  // sites staged per round (rows padded to T + 1 words)
-  __shared__ float sin[9][CI][T + 1];
-  __shared__ float sd[CO][T + 1];
-  const int LL = L * L, total = B * LL;
-  const int s0 = blockIdx.x * chunk, s1 = min(total, s0 + chunk);
-  constexpr int PER = (NE + 255) / 256;
-  float acc[PER];
-#pragma unroll
-  for (int k = 0; k < PER; ++k) acc[k] = 0.f;
-  float accb = 0.f;
-  for (int base = s0; base < s1; base += T) {
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < T * (CO + 9 * CI); idx += blockDim.x) {
-      const int t = idx % T, q = idx / T;
-      const int s = base + t;
-      float v = 0.f;
-      if (s < s1) {
-        const int b = s / LL, r = s - b * LL, x = r % L, y = r / L;
-        if (q < CO) {
-          v = dout[((size_t)b * CO + q) * LL + r];
-        } else {
-          const int qq = q - CO, tap = qq / CI, ci = qq - tap * CI;
-          const int nb = wrapL(y + tap / 3 - 1, L) * L + wrapL(x + tap % 3 - 1, L);
-          v = in[((size_t)b * CI + ci) * LL + nb];
-        }
-      }
-      if (q < CO)
-        sd[q][t] = v;
-      else
-        sin[(q - CO) / CI][(q - CO) % CI][t] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int e = threadIdx.x + k * 256;
-      if (e >= NE) break;
-      const int co = e / (CI * 9), rem = e - co * CI * 9, ci = rem / 9, tap = rem - ci * 9;
-      float a = 0.f;
-#pragma unroll 8
-      for (int t = 0; t < T; ++t) a += sd[co][t] * sin[tap][ci][t];
-      acc[k] += a;
-    }
-    if (threadIdx.x < CO)
-      for (int t = 0; t < T; ++t) accb += sd[threadIdx.x][t];
-  }
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int e = threadIdx.x + k * 256;
-    if (e < NE) atomicAdd(&dW[e], acc[k]);
-  }
-  if (threadIdx.x < CO) atomicAdd(&dbias[threadIdx.x], accb);
-}
 
 // Adam (Kingma & Ba, ICLR 2015) with bias corrections c1 = 1 / (1 - b1^t),
 // c2 = 1 / (1 - b2^t) computed on the host; epsilon 1e-8.
@@ -453,21 +283,25 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 //   kActs:      bias + ReLU, bf16 NHWC activations to `out`;
 //   kLogits:    fp32 logits [shot][4][L][L] (channels < 4) to `logits`;
 //   kProposals: per anyon (sig != 0) the channel of the largest logit if it is
-//               positive, else 4; non-anyons 4; one byte per site to `prop`.
-enum ConvMode { kActs = 0, kLogits = 1, kProposals = 2 };
+//               positive, else 4; non-anyons 4; one byte per site to `prop`;
+//   kGradMasked (training, backward data): no bias; the sum times the ReLU
+//               mask (act > 0) of the layer input `act`, bf16 NHWC to `out`.
+enum ConvMode { kActs = 0, kLogits = 1, kProposals = 2, kGradMasked = 3 };
 constexpr int kWPitch = 20;
 
 template <int NT, int MODE>
 __global__ void __launch_bounds__(128) conv_mma_kernel(
     const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Wg,
     const float* __restrict__ bias, int L, int64_t shots, __nv_bfloat16* __restrict__ out,
-    float* __restrict__ logits, const uint8_t* __restrict__ sig, uint8_t* __restrict__ prop) {
+    float* __restrict__ logits, const uint8_t* __restrict__ sig, uint8_t* __restrict__ prop,
+    const __nv_bfloat16* __restrict__ act) {
   constexpr int CO = 8 * NT;
   __shared__ uint32_t sW[9 * CO * kWPitch];
   __shared__ float sb[CO];
   for (int i = threadIdx.x; i < 9 * CO * 16; i += blockDim.x)
     sW[(i / 16) * kWPitch + (i % 16)] = reinterpret_cast<const uint32_t*>(Wg)[i];
-  for (int i = threadIdx.x; i < CO; i += blockDim.x) sb[i] = (MODE == kActs || i < 4) ? bias[i] : 0.f;
+  for (int i = threadIdx.x; i < CO; i += blockDim.x)
+    sb[i] = MODE == kGradMasked ? 0.f : ((MODE == kActs || i < 4) ? bias[i] : 0.f);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
@@ -545,6 +379,10 @@ __global__ void __launch_bounds__(128) conv_mma_kernel(
           float* lb = logits + shot[h] * 4 * LL + r;
           if (c0 < 4) lb[(int64_t)c0 * LL] = v0;
           if (c0 + 1 < 4) lb[(int64_t)(c0 + 1) * LL] = v1;
+        } else if (MODE == kGradMasked) {
+          const __nv_bfloat162 m = reinterpret_cast<const __nv_bfloat162*>(act)[site[h] * 16 + c0 / 2];
+          reinterpret_cast<uint32_t*>(out)[site[h] * 16 + c0 / 2] =
+              pack_bf16(__bfloat162float(m.x) > 0.f ? v0 : 0.f, __bfloat162float(m.y) > 0.f ? v1 : 0.f);
         } else {
           reinterpret_cast<uint32_t*>(out)[site[h] * 16 + c0 / 2] =
               pack_bf16(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
@@ -1147,6 +985,190 @@ __global__ void combine_kernel(uint8_t* __restrict__ C, const uint8_t* __restric
   for (int64_t i = i0; i < n; i += stride) C[i] ^= N[i] ^ R[i];
 }
 
+// ------------------------------------------------ training (tensor cores) --
+//
+// One training step in bf16 with fp32 accumulation and fp32 master weights:
+// forward through layer1_kernel and conv_mma_kernel (the inference kernels),
+// the loss gradient as bf16 NHWC, then per layer the weight gradient
+// (wgrad_mma_kernel: dW[co][ci][tap] = sum_s dout[s][co] in[s + tap][ci] as a
+// GEMM with M = output channels, N = (tap, input channel), K = sites, on
+// mma.sync m16n8k16), the bias gradient, and the input gradient
+// (conv_mma_kernel in kGradMasked mode: the same 3x3 convolution with the
+// weights transposed in channels and mirrored in taps, times the ReLU mask).
+
+// Backward-data weights: Wt[l][tap][ci][co] = W_l[co][ci][8 - tap] for the
+// layers 2, 3, 4 (layer 4's co >= 4 zero), bf16.
+__global__ void prepare_bwd_weights_kernel(const float* __restrict__ P,
+                                           __nv_bfloat16* __restrict__ Wt) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * 9 * 32 * 32;
+       i += gridDim.x * blockDim.x) {
+    const int l = i / (9 * 32 * 32), j = i % (9 * 32 * 32);
+    const int tap = j / (32 * 32), ci = (j / 32) % 32, co = j % 32;
+    const int CO = l < 2 ? 32 : 4;
+    const int off = l == 0 ? kW1 : (l == 1 ? kW2 : kW3);
+    const float w = co < CO ? P[off + (co * 32 + ci) * 9 + (8 - tap)] : 0.f;
+    Wt[i] = __float2bfloat16_rn(w);
+  }
+}
+
+// network input as bf16 NHWC with 32 channels: (anyon, 1, 0, ..., 0)
+__global__ void x0_nhwc_kernel(const uint8_t* __restrict__ sig, int64_t S,
+                               __nv_bfloat16* __restrict__ x0) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint4* o = reinterpret_cast<uint4*>(x0 + i * 32);
+    o[0] = make_uint4(pack_bf16(sig[i] ? 1.f : 0.f, 1.f), 0, 0, 0);
+    o[1] = o[2] = o[3] = make_uint4(0, 0, 0, 0);
+  }
+}
+
+// Softmax over (z0..z3, 0) at labelled sites, the fifth class ("no move")
+// with its logit fixed at 0; target q = smoothed one-hot of the label;
+// dz = (p - q) / n_labelled as bf16 NHWC with 32 channels (4 used), loss =
+// mean cross-entropy -sum q log p.
+__global__ void loss_grad_nhwc_kernel(const float* __restrict__ z, const uint8_t* __restrict__ lab,
+                                      int L, int B, const unsigned int* __restrict__ count,
+                                      __nv_bfloat16* __restrict__ dz, float* __restrict__ loss) {
+  const int LL = L * L;
+  const float inv_n = 1.f / (float)(*count > 0 ? *count : 1u);
+  const float q_off = kLabelSmoothing / 5.f, q_on = 1.f - kLabelSmoothing + q_off;
+  float local = 0.f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B * LL; i += gridDim.x * blockDim.x) {
+    const int b = i / LL, r = i - b * LL;
+    const float* zb = z + (size_t)b * 4 * LL;
+    uint4* o = reinterpret_cast<uint4*>(dz + (size_t)i * 32);
+    const int t = lab[i];
+    float g[4] = {0.f, 0.f, 0.f, 0.f};
+    if (t != 255) {
+      float v[5] = {zb[r], zb[LL + r], zb[2 * LL + r], zb[3 * LL + r], 0.f};
+      float mx = v[0];
+      for (int k = 1; k < 5; ++k) mx = fmaxf(mx, v[k]);
+      float sum = 0.f;
+      for (int k = 0; k < 5; ++k) sum += expf(v[k] - mx);
+      const float lse = mx + logf(sum);
+      for (int k = 0; k < 5; ++k) {
+        const float q = (t == k) ? q_on : q_off;
+        if (k < 4) g[k] = (expf(v[k] - lse) - q) * inv_n;
+        local += q * (lse - v[k]);
+      }
+    }
+    o[0] = make_uint4(pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), 0, 0);
+    o[1] = o[2] = o[3] = make_uint4(0, 0, 0, 0);
+  }
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xFFFFFFFFu, local, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, local * inv_n);
+}
+
+// per-channel sum of a bf16 NHWC [S][32] gradient into db[0 .. CO)
+template <int CO>
+__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ d, int64_t S,
+                                 float* __restrict__ db) {
+  __shared__ float red[8][32];
+  const int c = threadIdx.x & 31, row = threadIdx.x >> 5;
+  float acc = 0.f;
+  for (int64_t s = blockIdx.x * 8 + row; s < S; s += (int64_t)gridDim.x * 8)
+    acc += __bfloat162float(d[s * 32 + c]);
+  red[row][c] = acc;
+  __syncthreads();
+  if (row == 0) {
+    float v = 0.f;
+    for (int r = 0; r < 8; ++r) v += red[r][c];
+    if (c < CO) atomicAdd(&db[c], v);
+  }
+}
+
+constexpr int kWgChunk = 64;   // sites staged per round
+constexpr int kWgPitch = 36;   // words per staged row (64 sites = 32 words, padded)
+
+// dW[co][ci][tap] += sum over the CTA's sites s of dout[s][co] in[nb(s, tap)][ci]
+// (nb: the circular neighbour of s at tap offset (ky - 1, kx - 1)); dout and in
+// bf16 NHWC [S][32]; only co < CO_REAL, ci < CI_REAL are written (param layout
+// [co][CI_REAL][9]).  256 threads: warp w owns output channels 16 (w / 4) ..
+// +15 and the n-tiles 9 (w % 4) .. +8 of the 36 (tap, 8-channel block) tiles.
+template <int CO_REAL, int CI_REAL>
+__global__ void __launch_bounds__(256) wgrad_mma_kernel(const __nv_bfloat16* __restrict__ dout,
+                                                        const __nv_bfloat16* __restrict__ in,
+                                                        int L, int64_t S, int64_t chunk,
+                                                        float* __restrict__ dW) {
+  __shared__ uint32_t sD[32 * kWgPitch];       // [co][site pair]
+  __shared__ uint32_t sI[9 * 32 * kWgPitch];   // [tap][ci][site pair]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int mt = warp >> 2, nt0 = (warp & 3) * 9;
+  const int64_t LL = (int64_t)L * L;
+  const int64_t s_begin = blockIdx.x * chunk, s_end = min(S, s_begin + chunk);
+  float acc[9][4];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.f;
+  __nv_bfloat16* sDh = reinterpret_cast<__nv_bfloat16*>(sD);
+  __nv_bfloat16* sIh = reinterpret_cast<__nv_bfloat16*>(sI);
+  for (int64_t base = s_begin; base < s_end; base += kWgChunk) {
+    __syncthreads();
+    // stage: thread (site j, octet o) transposes 8 channels of dout and of the
+    // nine neighbours of site base + j
+    {
+      const int j = tid >> 2, o = tid & 3;
+      const int64_t s = base + j;
+      const bool ok = s < s_end;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (ok) v = *reinterpret_cast<const uint4*>(dout + s * 32 + o * 8);
+      const __nv_bfloat16* vh = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) sDh[(o * 8 + k) * (2 * kWgPitch) + j] = vh[k];
+      int64_t shot = 0;
+      int x = 0, y = 0;
+      if (ok) {
+        shot = s / LL;
+        const int r = (int)(s - shot * LL);
+        x = r % L;
+        y = r / L;
+      }
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        uint4 u = make_uint4(0, 0, 0, 0);
+        if (ok) {
+          const int xx = wrapL(x + tap % 3 - 1, L), yy = wrapL(y + tap / 3 - 1, L);
+          u = *reinterpret_cast<const uint4*>(in + (shot * LL + (int64_t)yy * L + xx) * 32 + o * 8);
+        }
+        const __nv_bfloat16* uh = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sIh[((tap * 32) + o * 8 + k) * (2 * kWgPitch) + j] = uh[k];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < kWgChunk / 16; ++ks) {
+      uint32_t a[4];
+      const uint32_t* ar = sD + (mt * 16 + g) * kWgPitch + ks * 8 + t;
+      a[0] = ar[0];
+      a[1] = ar[8 * kWgPitch];
+      a[2] = ar[4];
+      a[3] = ar[8 * kWgPitch + 4];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const int ntile = nt0 + k, tap = ntile >> 2, ci = (ntile & 3) * 8 + g;
+        const uint32_t* br = sI + (tap * 32 + ci) * kWgPitch + ks * 8 + t;
+        mma_bf16(acc[k], a, br[0], br[4]);
+      }
+    }
+  }
+  // rows g, g + 8 (output channels), columns 2t, 2t + 1 (input channels) of each tile
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int ntile = nt0 + k, tap = ntile >> 2, cb = (ntile & 3) * 8 + 2 * t;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int co = mt * 16 + g + 8 * h;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int ci = cb + e;
+        if (co < CO_REAL && ci < CI_REAL)
+          atomicAdd(&dW[(co * CI_REAL + ci) * 9 + tap], acc[k][2 * h + e]);
+      }
+    }
+  }
+}
+
 int grid_for(int64_t items, int threads) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -1272,6 +1294,96 @@ int qca_net_set_params(qca_net_t n, const float* host, int64_t count) {
                    "qca_net_set_params");
 }
 
+}  // extern "C"
+
+namespace {
+
+// Device buffers of one training batch of S sites.
+struct TrainBufs {
+  int64_t S = 0;
+  uint8_t* bytes = nullptr;        // sig, dir, lab
+  __nv_bfloat16* h = nullptr;      // x0, a1, a2, a3, dz, g1, g2: bf16 NHWC [S][32] each
+  float* z = nullptr;              // logits fp32 [B][4][L][L]
+  __nv_bfloat16* wt = nullptr;     // backward-data weights [3][9][32][32]
+  uint8_t* sig() const { return bytes; }
+  uint8_t* dir() const { return bytes + S; }
+  uint8_t* lab() const { return bytes + 2 * S; }
+  __nv_bfloat16* act(int k) const { return h + (size_t)k * S * 32; }
+  int alloc(int64_t sites) {
+    S = sites;
+    cudaError_t e = cudaMalloc(&bytes, 3 * S);
+    if (e == cudaSuccess) e = cudaMalloc(&h, sizeof(__nv_bfloat16) * 7 * 32 * S);
+    if (e == cudaSuccess) e = cudaMalloc(&z, sizeof(float) * 4 * S);
+    if (e == cudaSuccess) e = cudaMalloc(&wt, sizeof(__nv_bfloat16) * 3 * 9 * 32 * 32);
+    return cuda_fail(e, "training buffers");
+  }
+  ~TrainBufs() {
+    cudaFree(bytes);
+    cudaFree(h);
+    cudaFree(z);
+    cudaFree(wt);
+  }
+};
+
+// Forward and backward of one batch whose syndromes (bufs.sig) and labels
+// (bufs.lab) are in place: n->grads receives the gradient of the mean
+// smoothed cross-entropy over the labelled sites, *loss that loss.
+int train_forward_backward(qca_net_s* n, const TrainBufs& b, int L, int batch,
+                           const unsigned int* count, float* loss) {
+  const int64_t S = b.S;
+  const int gS = grid_for(S, 256);
+  const int gm = grid_for((S + 15) / 16 * 32, 128);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t chunk = (S + 2 * (int64_t)sms - 1) / (2 * (int64_t)sms);
+  chunk = ((chunk + kWgChunk - 1) / kWgChunk) * kWgChunk;
+  const int gW = (int)((S + chunk - 1) / chunk);
+  __nv_bfloat16 *x0 = b.act(0), *a1 = b.act(1), *a2 = b.act(2), *a3 = b.act(3), *dz = b.act(4),
+                *g1 = b.act(5), *g2 = b.act(6);
+  // weights of this step: bf16 forward copies, mirrored backward copies
+  prepare_weights_kernel<<<64, 256>>>(n->params, n->wb, n->w1);
+  prepare_bwd_weights_kernel<<<64, 256>>>(n->params, b.wt);
+  n->prepared = false;  // the inference table follows the weights on the next inference call
+  // forward
+  x0_nhwc_kernel<<<gS, 256>>>(b.sig(), S, x0);
+  layer1_kernel<<<gS, 256>>>(b.sig(), L, batch, n->w1, n->params, a1);
+  conv_mma_kernel<4, kActs><<<gm, 128>>>(a1, n->wb, n->params + kB1, L, batch, a2, nullptr, nullptr,
+                                         nullptr, nullptr);
+  conv_mma_kernel<4, kActs><<<gm, 128>>>(a2, n->wb + 9 * 32 * 32, n->params + kB2, L, batch, a3,
+                                         nullptr, nullptr, nullptr, nullptr);
+  conv_mma_kernel<1, kLogits><<<gm, 128>>>(a3, n->wb + 2 * 9 * 32 * 32, n->params + kB3, L, batch,
+                                           nullptr, b.z, nullptr, nullptr, nullptr);
+  loss_grad_nhwc_kernel<<<gS, 256>>>(b.z, b.lab(), L, batch, count, dz, loss);
+  // backward: layer 4, 3, 2 (weights, bias, masked input gradient), layer 1
+  cudaMemsetAsync(n->grads, 0, sizeof(float) * kParams);
+  float* G = n->grads;
+  wgrad_mma_kernel<4, 32><<<gW, 256>>>(dz, a3, L, S, chunk, G + kW3);
+  bias_grad_kernel<4><<<gS, 256>>>(dz, S, G + kB3);
+  conv_mma_kernel<4, kGradMasked><<<gm, 128>>>(dz, b.wt + 2 * 9 * 32 * 32, nullptr, L, batch, g1,
+                                               nullptr, nullptr, nullptr, a3);
+  wgrad_mma_kernel<32, 32><<<gW, 256>>>(g1, a2, L, S, chunk, G + kW2);
+  bias_grad_kernel<32><<<gS, 256>>>(g1, S, G + kB2);
+  conv_mma_kernel<4, kGradMasked><<<gm, 128>>>(g1, b.wt + 9 * 32 * 32, nullptr, L, batch, g2,
+                                               nullptr, nullptr, nullptr, a2);
+  wgrad_mma_kernel<32, 32><<<gW, 256>>>(g2, a1, L, S, chunk, G + kW1);
+  bias_grad_kernel<32><<<gS, 256>>>(g2, S, G + kB1);
+  conv_mma_kernel<4, kGradMasked><<<gm, 128>>>(g2, b.wt, nullptr, L, batch, g1, nullptr, nullptr,
+                                               nullptr, a1);
+  wgrad_mma_kernel<32, 2><<<gW, 256>>>(g1, x0, L, S, chunk, G + kW0);
+  bias_grad_kernel<32><<<gS, 256>>>(g1, S, G + kB0);
+  return cuda_fail(cudaGetLastError(), "training kernels");
+}
+
+uint64_t train_thr(double p) {
+  const double v = ldexp(p, 64);
+  return v >= 18446744073709549568.0 ? ~0ull : (uint64_t)v;
+}
+
+}  // namespace
+
+extern "C" {
+
 int qca_net_train(qca_net_t n, int L, int64_t iterations, int batch, double p_lo, double p_hi,
                   uint64_t seed, float lr, float* out_losses) {
   if (!n || L < 4 || L > 128 || iterations < 0 || iterations > (1 << 24) || batch < 1 ||
@@ -1282,69 +1394,30 @@ int qca_net_train(qca_net_t n, int L, int64_t iterations, int batch, double p_lo
   }
   if (iterations == 0) return QCA_OK;
   const int64_t S = (int64_t)batch * L * L;
-  // bytes: sig, dir, lab; floats: x0 (2), a1, a2, a3 (32), z, dz (4), ga, gb (32); per-iteration
-  // loss and labelled-site count
-  uint8_t* bytes = nullptr;
-  float* fl = nullptr;
+  TrainBufs b;
+  int rc = b.alloc(S);
+  if (rc) return rc;
   float* losses = nullptr;
   unsigned int* counts = nullptr;
-  cudaError_t e = cudaMalloc(&bytes, 3 * S);
-  if (e == cudaSuccess) e = cudaMalloc(&fl, sizeof(float) * S * (2 + 32 * 3 + 4 + 4 + 32 * 2));
-  if (e == cudaSuccess) e = cudaMalloc(&losses, sizeof(float) * iterations);
+  cudaError_t e = cudaMalloc(&losses, sizeof(float) * iterations);
   if (e == cudaSuccess) e = cudaMalloc(&counts, sizeof(unsigned int) * iterations);
   if (e == cudaSuccess) e = cudaMemset(losses, 0, sizeof(float) * iterations);
   if (e == cudaSuccess) e = cudaMemset(counts, 0, sizeof(unsigned int) * iterations);
   if (e != cudaSuccess) {
-    cudaFree(bytes);
-    cudaFree(fl);
     cudaFree(losses);
     cudaFree(counts);
     return cuda_fail(e, "qca_net_train allocation");
   }
-  uint8_t *sig = bytes, *dir = bytes + S, *lab = bytes + 2 * S;
-  float* x0 = fl;
-  float* a1 = x0 + 2 * S;
-  float* a2 = a1 + 32 * S;
-  float* a3 = a2 + 32 * S;
-  float* z = a3 + 32 * S;
-  float* dz = z + 4 * S;
-  float* ga = dz + 4 * S;
-  float* gb = ga + 32 * S;
-  auto thr_of = [](double p) -> uint64_t {
-    const double v = ldexp(p, 64);
-    return v >= 18446744073709549568.0 ? ~0ull : (uint64_t)v;
-  };
-  const uint64_t t_lo = thr_of(p_lo), t_span = thr_of(p_hi - p_lo);
+  const uint64_t t_lo = train_thr(p_lo), t_span = train_thr(p_hi - p_lo);
   const int gS = grid_for(S, 256);
-  // weight-gradient CTAs: about two per SM, each over a contiguous run of sites
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t chunk64 = (S + 2 * (int64_t)(sms > 0 ? sms : 1) - 1) / (2 * (int64_t)(sms > 0 ? sms : 1));
-  chunk64 = ((chunk64 + 31) / 32) * 32;
-  const int chunk = (int)(chunk64 < 256 ? 256 : chunk64);
-  const int gW = (int)((S + chunk - 1) / chunk);
   const float b1 = 0.9f, b2 = 0.999f;
-  int rc = QCA_OK;
-  for (int64_t it = 0; it < iterations; ++it) {
-    train_sample_kernel<<<gS, 256>>>(L, batch, n->train_shots, seed, t_lo, t_span, sig);
-    first_dir_kernel<<<gS, 256>>>(sig, L, batch, dir);
-    mutual_label_kernel<<<gS, 256>>>(dir, L, batch, lab);
-    count_labelled_kernel<<<gS, 256>>>(lab, (int)S, counts + it);
-    input_f32_kernel<<<gS, 256>>>(sig, L, batch, x0);
-    conv_fwd_f32<2, 32, true><<<gS, 256>>>(x0, n->params + kW0, n->params + kB0, L, batch, a1);
-    conv_fwd_f32<32, 32, true><<<gS, 256>>>(a1, n->params + kW1, n->params + kB1, L, batch, a2);
-    conv_fwd_f32<32, 32, true><<<gS, 256>>>(a2, n->params + kW2, n->params + kB2, L, batch, a3);
-    conv_fwd_f32<32, 4, false><<<gS, 256>>>(a3, n->params + kW3, n->params + kB3, L, batch, z);
-    cudaMemsetAsync(n->grads, 0, sizeof(float) * kParams);
-    loss_grad_kernel<<<gS, 256>>>(z, lab, L, batch, counts + it, dz, losses + it);
-    conv_bwd_weight_f32<32, 4><<<gW, 256>>>(a3, dz, L, batch, chunk, n->grads + kW3, n->grads + kB3);
-    conv_bwd_data_f32<32, 4, true><<<gS, 256>>>(dz, n->params + kW3, a3, L, batch, ga);
-    conv_bwd_weight_f32<32, 32><<<gW, 256>>>(a2, ga, L, batch, chunk, n->grads + kW2, n->grads + kB2);
-    conv_bwd_data_f32<32, 32, true><<<gS, 256>>>(ga, n->params + kW2, a2, L, batch, gb);
-    conv_bwd_weight_f32<32, 32><<<gW, 256>>>(a1, gb, L, batch, chunk, n->grads + kW1, n->grads + kB1);
-    conv_bwd_data_f32<32, 32, true><<<gS, 256>>>(gb, n->params + kW1, a1, L, batch, ga);
-    conv_bwd_weight_f32<2, 32><<<gW, 256>>>(x0, ga, L, batch, chunk, n->grads + kW0, n->grads + kB0);
+  for (int64_t it = 0; it < iterations && rc == QCA_OK; ++it) {
+    train_sample_kernel<<<gS, 256>>>(L, batch, n->train_shots, seed, t_lo, t_span, b.sig());
+    first_dir_kernel<<<gS, 256>>>(b.sig(), L, batch, b.dir());
+    mutual_label_kernel<<<gS, 256>>>(b.dir(), L, batch, b.lab());
+    count_labelled_kernel<<<gS, 256>>>(b.lab(), (int)S, counts + it);
+    rc = train_forward_backward(n, b, L, batch, counts + it, losses + it);
+    if (rc) break;
     n->adam_t += 1;
     const float c1 = 1.f / (1.f - powf(b1, (float)n->adam_t));
     const float c2 = 1.f / (1.f - powf(b2, (float)n->adam_t));
@@ -1352,21 +1425,55 @@ int qca_net_train(qca_net_t n, int L, int64_t iterations, int batch, double p_lo
                                                 b2, c1, c2);
     n->train_shots += batch;
     e = cudaGetLastError();
-    if (e != cudaSuccess) {
-      rc = cuda_fail(e, "training kernels");
-      break;
-    }
+    if (e != cudaSuccess) rc = cuda_fail(e, "training kernels");
   }
   if (rc == QCA_OK) rc = cuda_fail(cudaDeviceSynchronize(), "qca_net_train");
   if (rc == QCA_OK && out_losses)
     rc = cuda_fail(cudaMemcpy(out_losses, losses, sizeof(float) * iterations, cudaMemcpyDeviceToHost),
                    "training loss copy");
-  cudaFree(bytes);
-  cudaFree(fl);
   cudaFree(losses);
   cudaFree(counts);
   n->prepared = false;
   n->prepared8 = false;
+  return rc;
+}
+
+int qca_net_gradients(qca_net_t n, const uint8_t* noise, int L, int batch, float* host_grads,
+                      int64_t count, float* host_loss) {
+  if (!n || !noise || !host_grads || count != kParams || L < 4 || L > 128 || batch < 1 ||
+      (int64_t)batch * L * L > (1 << 24)) {
+    set_error("qca_net_gradients: bad arguments (count must be %d, 4 <= L <= 128)", kParams);
+    return QCA_ERR_ARG;
+  }
+  const int64_t S = (int64_t)batch * L * L;
+  TrainBufs b;
+  int rc = b.alloc(S);
+  if (rc) return rc;
+  float* dl = nullptr;
+  unsigned int* cnt = nullptr;
+  cudaError_t e = cudaMalloc(&dl, sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&cnt, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(dl, 0, sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(cnt, 0, sizeof(unsigned int));
+  if (e != cudaSuccess) {
+    cudaFree(dl);
+    cudaFree(cnt);
+    return cuda_fail(e, "qca_net_gradients allocation");
+  }
+  const int gS = grid_for(S, 256);
+  syndrome_kernel<<<gS, 256>>>(noise, L, batch, b.sig());
+  first_dir_kernel<<<gS, 256>>>(b.sig(), L, batch, b.dir());
+  mutual_label_kernel<<<gS, 256>>>(b.dir(), L, batch, b.lab());
+  count_labelled_kernel<<<gS, 256>>>(b.lab(), (int)S, cnt);
+  rc = train_forward_backward(n, b, L, batch, cnt, dl);
+  if (rc == QCA_OK) rc = cuda_fail(cudaDeviceSynchronize(), "qca_net_gradients");
+  if (rc == QCA_OK)
+    rc = cuda_fail(cudaMemcpy(host_grads, n->grads, sizeof(float) * kParams, cudaMemcpyDeviceToHost),
+                   "gradient copy");
+  if (rc == QCA_OK && host_loss)
+    rc = cuda_fail(cudaMemcpy(host_loss, dl, sizeof(float), cudaMemcpyDeviceToHost), "loss copy");
+  cudaFree(dl);
+  cudaFree(cnt);
   return rc;
 }
 
@@ -1515,17 +1622,17 @@ int net_run(qca_net_s* n, const uint8_t* noise, int L, int64_t shots, float* log
     }
     layer1_kernel<<<grid_for(S, 256), 256, 0, st>>>(sig, L, m, n->w1, n->params, actA);
     conv_mma_kernel<4, kActs><<<gm, 128, 0, st>>>(actA, n->wb, n->params + kB1, L, m, actB,
-                                                  nullptr, nullptr, nullptr);
+                                                  nullptr, nullptr, nullptr, nullptr);
     conv_mma_kernel<4, kActs><<<gm, 128, 0, st>>>(actB, n->wb + 9 * 32 * 32, n->params + kB2, L, m,
-                                                  actA, nullptr, nullptr, nullptr);
+                                                  actA, nullptr, nullptr, nullptr, nullptr);
     if (logits) {
       conv_mma_kernel<1, kLogits><<<gm, 128, 0, st>>>(actA, n->wb + 2 * 9 * 32 * 32,
                                                       n->params + kB3, L, m, nullptr,
-                                                      logits + c0s * 4 * LL, nullptr, nullptr);
+                                                      logits + c0s * 4 * LL, nullptr, nullptr, nullptr);
     } else {
       conv_mma_kernel<1, kProposals><<<gm, 128, 0, st>>>(actA, n->wb + 2 * 9 * 32 * 32,
                                                          n->params + kB3, L, m, nullptr, nullptr,
-                                                         sig, prop);
+                                                         sig, prop, nullptr);
       pairing_kernel<<<grid_for(S, 256), 256, 0, st>>>(Nc, prop, L, m, resid + c0s * 2 * LL,
                                                        c0 ? c0 + c0s * 2 * LL : nullptr);
     }
@@ -1656,10 +1763,10 @@ int qca_net_calibrate_fp8(qca_net_t n, const uint8_t* noise, int L, int64_t shot
   layer1_kernel<<<grid_for(S, 256), 256, 0, st>>>(sig, L, m, n->w1, n->params, actA);
   amax_bf16_kernel<<<ga, 256, 0, st>>>(actA, S * 32, amax + 0);
   conv_mma_kernel<4, kActs><<<gm, 128, 0, st>>>(actA, n->wb, n->params + kB1, L, m, actB, nullptr,
-                                                nullptr, nullptr);
+                                                nullptr, nullptr, nullptr);
   amax_bf16_kernel<<<ga, 256, 0, st>>>(actB, S * 32, amax + 1);
   conv_mma_kernel<4, kActs><<<gm, 128, 0, st>>>(actB, n->wb + 9 * 32 * 32, n->params + kB2, L, m,
-                                                actA, nullptr, nullptr, nullptr);
+                                                actA, nullptr, nullptr, nullptr, nullptr);
   amax_bf16_kernel<<<ga, 256, 0, st>>>(actA, S * 32, amax + 2);
   unsigned int h[3] = {0, 0, 0};
   e = cudaGetLastError();

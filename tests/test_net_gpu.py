@@ -290,6 +290,7 @@ def test_tcgen05_logits_match_fp64_and_mma_path(trained):
     # flips occur, so the bar is 99.99 % of logits within 1e-2 and none beyond
     # 0.03; the small lattices above hold every logit to 1e-2.
     net, _ = trained
+    net.set_precision("bf16")   # the FP8 fixture may still be active in this module
     L, shots = 128, 2
     N = oracle.sample_errors(L, shots, 0.05, seed=51)
     Nd = dev(N)
@@ -309,6 +310,7 @@ def test_tcgen05_logits_match_fp64_and_mma_path(trained):
 
 def test_tcgen05_pairing_bit_exact_and_decode(trained):
     net, _ = trained
+    net.set_precision("bf16")
     net.set_tensor_path(True)
     L, shots = 256, 3
     N = oracle.sample_errors(L, shots, 0.05, seed=52)
@@ -325,3 +327,33 @@ def test_tcgen05_pairing_bit_exact_and_decode(trained):
     Co, so, fo = oracle.decode_shot(R[0], max_steps=4096)
     np.testing.assert_array_equal(C[0].cpu().numpy(), Co ^ C0[0])
     assert (int(steps[0]), int(fail[0])) == (so, fo)
+
+
+# ------------------------------------------------- training on tensor cores
+
+def test_gradients_match_fp64_reference():
+    # one training step's gradient (bf16 operands, fp32 accumulation) against
+    # the FP64 reference of the same loss: the bf16 rounding of weights and
+    # activations bounds the agreement to about 1e-2 relative per layer
+    net = qca.Net(seed=4)
+    try:
+        L, B = 16, 6
+        N = oracle.sample_errors(L, B, 0.06, seed=61)
+        loss, g = net.gradients(dev(N))
+        params = net.get_params()
+        A = anyon_maps(N)
+        lab = np.stack([onet.first_step_labels(A[b]) for b in range(B)])
+        loss_ref, g_ref = onet.loss_and_grads(A, lab, params)
+        assert loss == pytest.approx(loss_ref, rel=2e-2)
+        o = 0
+        for co, ci in onet.LAYERS:
+            for n_ in (co * ci * 9, co):
+                a, b = g[o:o + n_].astype(np.float64), g_ref[o:o + n_]
+                rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+                cos = float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
+                assert rel < 5e-2 and cos > 0.998, (co, ci, n_, rel, cos)
+                o += n_
+        # the weights did not move
+        np.testing.assert_array_equal(net.get_params(), params)
+    finally:
+        net.close()
