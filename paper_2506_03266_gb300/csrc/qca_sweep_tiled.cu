@@ -127,6 +127,14 @@ __device__ __forceinline__ uint32_t bits4(const uint32_t* row, int W, int pos) {
   return (uint32_t)(two >> sh) & 0xFu;
 }
 
+// Six bits of a bitmap row starting at bit position pos (wrapping at the row end).
+__device__ __forceinline__ uint32_t bits6(const uint32_t* row, int W, int pos) {
+  const int q = pos >> 5, sh = pos & 31;
+  const int q1 = (q + 1 == W) ? 0 : q + 1;
+  const uint64_t two = ((uint64_t)row[q1] << 32) | row[q];
+  return (uint32_t)(two >> sh) & 0x3Fu;
+}
+
 // 4 bits -> 4 bytes of 0xFF / 0x00 (bit k -> byte k).
 __device__ __forceinline__ uint32_t nib_mask(uint32_t nib) {
   return ((nib * 0x00204081u) & 0x01010101u) * 0xFFu;
@@ -338,31 +346,44 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
           D[(size_t)(kTB + r) * W + w] = d2;
           D[(size_t)(2 * kTB + r) * W + w] = d3;
         }
-        // transverse window min over 7 rows, rolling down the band
+        // transverse window min over 7 rows, rolling down the band: with pair
+        // mins q(j) = min(row j, row j + 1), min(rows r .. r + 6) =
+        // min(q(r), q(r + 2), q(r + 4), row r + 6)  (4 mins per half-word)
         for (int kc = tid; kc < cols; kc += nt) {
           const uint32_t* col = reinterpret_cast<const uint32_t*>(Bk) + kc;
-          uint32_t hi[7], lo[7];
+          uint32_t qh[5], ql[5], rh, rl;
+          {
+            uint32_t h[6], l[6];
 #pragma unroll
-          for (int j = 0; j < 6; ++j) {
-            const uint32_t w = col[(size_t)j * cols];
-            hi[j] = w & 0xFF00FF00u;
-            lo[j] = w & 0x00FF00FFu;
+            for (int j = 0; j < 6; ++j) {
+              const uint32_t w = col[(size_t)j * cols];
+              h[j] = w & 0xFF00FF00u;
+              l[j] = w & 0x00FF00FFu;
+            }
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+              qh[j] = __vminu2(h[j], h[j + 1]);
+              ql[j] = __vminu2(l[j], l[j + 1]);
+            }
+            rh = h[5];
+            rl = l[5];
           }
 #pragma unroll 4
           for (int r = 0; r < kTB; ++r) {
             const uint32_t w = col[(size_t)(r + 6) * cols];
-            hi[6] = w & 0xFF00FF00u;
-            lo[6] = w & 0x00FF00FFu;
-            uint32_t mh = __vminu2(__vminu2(__vminu2(hi[0], hi[1]), __vminu2(hi[2], hi[3])),
-                                   __vminu2(__vminu2(hi[4], hi[5]), hi[6]));
-            uint32_t ml = __vminu2(__vminu2(__vminu2(lo[0], lo[1]), __vminu2(lo[2], lo[3])),
-                                   __vminu2(__vminu2(lo[4], lo[5]), lo[6]));
+            const uint32_t h6 = w & 0xFF00FF00u, l6 = w & 0x00FF00FFu;
+            const uint32_t mh = __vminu2(__vminu2(qh[0], qh[2]), __vminu2(qh[4], h6));
+            const uint32_t ml = __vminu2(__vminu2(ql[0], ql[2]), __vminu2(ql[4], l6));
             M[(size_t)r * cols + kc] = mh | ml;
 #pragma unroll
-            for (int j = 0; j < 6; ++j) {
-              hi[j] = hi[j + 1];
-              lo[j] = lo[j + 1];
+            for (int j = 0; j < 4; ++j) {
+              qh[j] = qh[j + 1];
+              ql[j] = ql[j + 1];
             }
+            qh[4] = __vminu2(rh, h6);
+            ql[4] = __vminu2(rl, l6);
+            rh = h6;
+            rl = l6;
           }
         }
         __syncthreads();
@@ -382,15 +403,23 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
             s = __funnelshift_r(Mr[kc], Mr[kp], 24);
           }
           uint32_t v = vmin4(s, 0xFCFCFCFCu) + 0x03030303u;
-          // terms: the smallest d wins (d = 3 first, overwritten by smaller d)
-          uint32_t T = 0xFFFFFFFFu;
+          // terms: the smallest d wins (d = 3 first, overwritten by smaller d).
+          // The d <= 3 cones of the word's four sites read positions
+          // 4 kc - 3 .. 4 kc + 2 (m^+) or 4 kc + 1 .. 4 kc + 6 (m^-) of the
+          // dilated rows, and D_3 contains D_2 and D_1: if those six bits of
+          // D_3 are clear there is no term.
+          const uint32_t* D3 = D + (size_t)(2 * kTB + r) * W;
+          if (bits6(D3, W, twrap(4 * kc + (plus ? -3 : 1), L))) {
+            uint32_t T = 0xFFFFFFFFu;
 #pragma unroll
-          for (int d = 3; d >= 1; --d) {
-            const int pos = twrap(4 * kc + (plus ? -d : d), L);
-            const uint32_t m = nib_mask(bits4(D + (size_t)((d - 1) * kTB + r) * W, W, pos));
-            T = (T & ~m) | ((v1 + (uint32_t)(d - 1) * 0x01010101u) & m);
+            for (int d = 3; d >= 1; --d) {
+              const int pos = twrap(4 * kc + (plus ? -d : d), L);
+              const uint32_t m = nib_mask(bits4(D + (size_t)((d - 1) * kTB + r) * W, W, pos));
+              T = (T & ~m) | ((v1 + (uint32_t)(d - 1) * 0x01010101u) & m);
+            }
+            v = vmin4(v, T);
           }
-          out[(size_t)r * cols + kc] = vmin4(v, T);
+          out[(size_t)r * cols + kc] = v;
         }
         __syncthreads();  // M, D and the band buffer are free again
       }
