@@ -783,6 +783,89 @@ def run_variant(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_sweep(args, rank, world, local):
+    """The plain decoder over the grid L in {32, 64, 128, 256} x p in {0.01,
+    0.02, 0.04, 0.06, 0.08}, 100 000 shots per point (noise coupled across p:
+    one seed), budget 4096: p_log with its sigma, mean and p99 steps to an
+    empty syndrome, and site-updates/s per point, each point timed with CUDA
+    events after one warm decode."""
+    import numpy as np
+    import torch
+
+    import paper_2506_03266_gb300 as qca
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    qca.build()
+    qca.lib()
+    shots = args.shots
+    shot0, _ = shard(rank, shots)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    points, tot_ms, tot_shots, tot_su = [], 0.0, 0, 0.0
+    grid_L = [int(x) for x in args.grid_L.split(",")]
+    grid_p = [float(x) for x in args.grid_p.split(",")]
+    for L in grid_L:
+        for p in grid_p:
+            N = qca.sample_errors(L, shots, p, seed=0, shot0=shot0)
+            out = (torch.empty_like(N), torch.empty(shots, dtype=torch.int32, device="cuda"),
+                   torch.empty(shots, dtype=torch.uint8, device="cuda"))
+            for _ in range(max(1, args.warmup)):
+                qca.decode_batch(N, MAX_STEPS, out=out)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            qca.decode_batch(N, MAX_STEPS, out=out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = reduce_time_max(a.elapsed_time(b), dist, "cuda")
+            st = out[1].cpu().numpy().astype(np.int64)
+            fl = out[2].cpu().numpy()
+            pl = float((fl > 0).mean())
+            su = float(st.sum()) * L * L
+            points.append({"L": L, "p": p, "p_log": pl,
+                           "p_log_sigma": float(np.sqrt(pl * (1 - pl) / shots)),
+                           "p_log_cut": float((fl == 1).mean()),
+                           "budget_exhausted": int((fl == 2).sum()),
+                           "mean_steps": float(st.mean()), "p99_steps": float(np.percentile(st, 99)),
+                           "shot_decodes_per_s": world * shots / (ms / 1e3),
+                           "site_updates_per_s": world * su / (ms / 1e3), "ms": ms})
+            tot_ms += ms
+            tot_shots += shots
+            tot_su += su
+            del N, out
+    clk = clocks.stop()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": f"shot-decodes/s of the plain automaton over the L x p grid ({len(points)} points)",
+        "value": world * tot_shots / (tot_ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": 1,
+        "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "site_updates_per_s": world * tot_su / (tot_ms / 1e3),
+        "config": {"workload": (f"plain automaton, L in {{{args.grid_L}}} x p in "
+                                f"{{{args.grid_p}}}, {shots} shots per point and GPU, "
+                                f"seed 0, budget {MAX_STEPS}; one timed decode per point"),
+                   "shots_per_point": shots,
+                   "l2": "each point's input is read once per decode; L >= 64 inputs exceed L2"},
+        "points": points,
+        "roofline": {"bound": "alu",
+                     "achieved": ALU_OPS_PER_SITE_UPDATE * tot_su / (tot_ms / 1e3) / 1e9,
+                     "peak": ALU_PEAK_LANE_OPS / 1e9, "unit": "Glane-op/s",
+                     "frac": ALU_OPS_PER_SITE_UPDATE * tot_su / (tot_ms / 1e3) / ALU_PEAK_LANE_OPS,
+                     "traffic": None},
+        "clocks": clk, "gpu_launches": len(points), "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def ctypes_ptr(t):
     import ctypes
     return ctypes.c_void_p(t.data_ptr())
@@ -818,11 +901,17 @@ def main():
     ap.add_argument("--no-net", action="store_true",
                     help="skip the net + automaton comparison of the default workload")
     ap.add_argument("--workload", default="uniform",
-                    choices=["uniform", "uneven", "net", "large", "1d", "open", "desync"],
+                    choices=["uniform", "uneven", "net", "large", "1d", "open", "desync",
+                             "sweep"],
                     help="uniform: the L=256 headline; uneven: 200 000 shots of mixed L; "
                          "net: learned pre-decoder + automaton at L=128, p=0.04; "
                          "large: L=1024 plain vs FP8 net + automaton; "
-                         "1d: the repetition-code automaton; open / desync: the 2D variants")
+                         "1d: the repetition-code automaton; open / desync: the 2D variants; "
+                         "sweep: the plain decoder over L in {32..256} x p in {0.01..0.08}")
+    ap.add_argument("--grid-L", default="32,64,128,256",
+                    help="sweep workload: comma-separated lattice sizes")
+    ap.add_argument("--grid-p", default="0.01,0.02,0.04,0.06,0.08",
+                    help="sweep workload: comma-separated error rates")
     ap.add_argument("--train-syndromes", type=int, default=1_000_000,
                     help="net workload: automaton-labelled training syndromes (untimed)")
     ap.add_argument("--autotune", action="store_true",
@@ -847,6 +936,9 @@ def main():
         return
     if args.workload == "1d":
         run_1d(args, rank, world, local)
+        return
+    if args.workload == "sweep":
+        run_sweep(args, rank, world, local)
         return
     if args.workload in ("open", "desync"):
         run_variant(args, rank, world, local)
