@@ -398,11 +398,14 @@ int qca_net_set_fp8_scales(qca_net_t net, const float* scales);
 int qca_net_get_fp8_scales(qca_net_t net, float* scales);
 int qca_net_set_precision(qca_net_t net, int precision);
 
-/* Tensor path of the bf16 form's layers 2-4: 1 (default) = tcgen05 MMAs with
- * the accumulator in tensor memory where L is a multiple of 128 (mma.sync
- * elsewhere); 0 = mma.sync everywhere.  Both give the same arithmetic up to
- * the fp32 accumulation order. */
-int qca_net_set_tensor_path(qca_net_t net, int use_tcgen05);
+/* Tensor path of the bf16 form's layers 2-4 where L is a multiple of 128
+ * (mma.sync elsewhere): 2 (default) = tcgen05 MMAs with the accumulator in
+ * tensor memory, warp-specialised (producer warps stage rows into a ring,
+ * one thread issues the MMAs, epilogue warps drain two accumulators, all
+ * handed over through mbarriers); 1 = the same MMAs with the roles in
+ * lock-step (block barriers per row); 0 = mma.sync everywhere.  All three
+ * give the same bits.  QCA_ERR_ARG for any other value. */
+int qca_net_set_tensor_path(qca_net_t net, int path);
 
 /* Synchronise and report the device watchdog of the tensor-core kernels:
  * QCA_ERR_WATCHDOG if a wait for an MMA timed out since the last call (the

@@ -538,8 +538,12 @@ class Net:
         """"bf16" or "fp8" for every inference entry point."""
         _check(lib().qca_net_set_precision(self.handle, {"bf16": 0, "fp8": 1}[precision]))
 
-    def set_tensor_path(self, use_tcgen05: bool):
-        _check(lib().qca_net_set_tensor_path(self.handle, 1 if use_tcgen05 else 0))
+    def set_tensor_path(self, path: str):
+        """Layers 2-4 of the bf16 form where L % 128 == 0: "tcgen05_ws"
+        (default, warp-specialised), "tcgen05" (row-synchronous) or "mma"
+        (mma.sync; also the path for other L)."""
+        _check(lib().qca_net_set_tensor_path(
+            self.handle, {"mma": 0, "tcgen05": 1, "tcgen05_ws": 2}[path]))
 
     def status(self):
         """Raises QcaError if a tensor-core wait timed out since the last call."""

@@ -721,6 +721,347 @@ constexpr size_t tc_smem_bytes() {
   return 4 * 4 * kTcRow * 16 + 9 * 4 * NOUT * 16 + 32 + 4 * NOUT;
 }
 
+// Warp-specialised form of the same convolution (the same MMAs in the same
+// order, so the same bits): the roles hand rows and accumulators to one
+// another through mbarriers instead of block barriers, so that the staging of
+// later rows, the MMAs of the next tile and the read-out of the last one
+// overlap.  Its activations use a planar layout of their own,
+// [shot][y][channel octet][x][8 bf16], so that a staged row is four
+// contiguous 2 KB runs (plus one halo site at either end) and the epilogue's
+// stores are contiguous across a warp.
+//   * producers stage the rows of the CTA's work units, in order, into a ring
+//     of kWsR row buffers.  From planar activations one thread issues bulk
+//     copies (cp.async.bulk, completion by transaction count on full[slot]);
+//     for layer 2 the kWsProd producer warps gather layer 1 from the table
+//     with cp.async, each thread publishing a row kWsLag rows after issuing
+//     it, once its copies have landed (wait_group, proxy fence, arrive).  A
+//     slot is refilled only after the MMAs that read it are complete
+//     (empty[slot], tcgen05.commit);
+//   * one MMA thread issues the 18 MMAs of each tile into one of two TMEM
+//     accumulators (once its epilogue is drained: acc_empty) and commits them
+//     to acc_full and to the release of the ring slot the tile reads last;
+//   * eight epilogue warps (two per TMEM lane quarter, one per column half)
+//     read each accumulator, free it, and apply bias and ReLU / write logits
+//     or proposals.
+// Every wait is bounded; a timeout sets err and a stop flag that every role
+// polls, and the CTA drains its MMAs before freeing the TMEM.
+constexpr int kWsR = 8;          // ring of staged rows
+constexpr int kWsLag = 4;        // rows a producer thread keeps in flight (<= kWsR - 3)
+constexpr int kWsEpi = 8;        // epilogue warps
+constexpr int kWsProd = 4;       // producer warps
+constexpr int kWsThreads = 32 * (kWsEpi + kWsProd + 1);
+constexpr int kWsMmaWarp = kWsEpi + kWsProd;
+static_assert(kWsLag <= kWsR - 3, "a producer must be able to publish the rows the MMA waits for");
+
+__device__ __forceinline__ void ws_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_smem(bar)) : "memory");
+}
+__device__ __forceinline__ void ws_bar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem(bar)), "r"(count)
+               : "memory");
+}
+// bounded wait on phase `parity`; on timeout, or when another role has already
+// stopped, returns false
+__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile int* stop) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(tc_smem(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (*stop) return false;
+    if (clock64() - t0 > kTcWaitCycles) {
+      *stop = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_expect_tx_ws(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Bulk copy global -> this CTA's shared memory, completion counted on bar.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s_ws(void* dst, const void* src, uint32_t bytes,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          tc_smem(dst)),
+      "l"(src), "r"(bytes), "r"(tc_smem(bar))
+      : "memory");
+}
+
+template <int NOUT, int MODE, bool FROM_SIG>
+__global__ void __launch_bounds__(kWsThreads, 2) conv_ws_kernel(
+    const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Wg,
+    const float* __restrict__ bias, int L, int64_t shots, __nv_bfloat16* __restrict__ out,
+    float* __restrict__ logits, const uint8_t* __restrict__ sig, uint8_t* __restrict__ prop,
+    unsigned int* __restrict__ err, const __nv_bfloat16* __restrict__ lut) {
+  constexpr int CO_SRC = NOUT == 32 ? 32 : 8;
+  constexpr uint32_t kRowBytes = 4 * kTcRow * 16;  // one staged row
+  constexpr uint32_t kA = kWsR * kRowBytes;        // the ring
+  constexpr uint32_t kB = 9 * 4 * NOUT * 16;       // weights
+  extern __shared__ __align__(128) uint8_t sm[];
+  uint8_t* sA = sm;
+  uint8_t* sB = sm + kA;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kA + kB);  // [kWsR]
+  uint64_t* empty = full + kWsR;                               // [kWsR]
+  uint64_t* acc_full = empty + kWsR;                           // [2]
+  uint64_t* acc_empty = acc_full + 2;                          // [2]
+  uint64_t* drained = acc_empty + 2;                           // [1]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drained + 1);
+  volatile int* stop = reinterpret_cast<volatile int*>(tslot + 1);
+  float* sbias = reinterpret_cast<float*>(tslot + 4);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  for (int i = tid; i < 9 * NOUT * 4; i += kWsThreads) {
+    const int tap = i / (NOUT * 4), rem = i % (NOUT * 4), co = rem / 4, oct = rem % 4;
+    uint4 w = make_uint4(0, 0, 0, 0);
+    if (co < CO_SRC)
+      w = *reinterpret_cast<const uint4*>(Wg + ((size_t)(tap * CO_SRC + co) * 32 + oct * 8));
+    *reinterpret_cast<uint4*>(sB + ((size_t)(tap * 4 + oct) * NOUT + co) * 16) = w;
+  }
+  for (int i = tid; i < NOUT; i += kWsThreads) sbias[i] = (MODE == kActs || i < 4) ? bias[i] : 0.f;
+  if (tid == 0) {
+    for (int k = 0; k < kWsR; ++k) {
+      ws_bar_init(&full[k], FROM_SIG ? 32 * kWsProd : 1);
+      ws_bar_init(&empty[k], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      ws_bar_init(&acc_full[k], 1);
+      ws_bar_init(&acc_empty[k], kWsEpi);
+    }
+    ws_bar_init(drained, 1);
+    *stop = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     tc_smem(tslot)),
+                 "r"(64)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // the weights are read by the tensor core (async proxy)
+  tc_fence_proxy_shared();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;  // two accumulators: columns 0-31 and 32-63
+  const int64_t LL = (int64_t)L * L;
+  const int xblocks = L / kTcM, strips = L / kTcStrip;
+  const int64_t units = shots * xblocks * strips;
+  auto unit_of = [&](int64_t u, int64_t& shot, int& x0, int& y0) {
+    shot = u / ((int64_t)xblocks * strips);
+    const int rem = (int)(u - shot * (int64_t)xblocks * strips);
+    x0 = (rem % xblocks) * kTcM;
+    y0 = (rem / xblocks) * kTcStrip;
+  };
+
+  if (!FROM_SIG && warp >= kWsEpi && warp < kWsMmaWarp) {
+    // ================= producer (one thread): bulk copies of planar rows; the
+    // other producer warps have no work in this form
+    if (warp == kWsEpi && lane == 0) {
+      int64_t e = 0;
+      for (int64_t u = blockIdx.x; u < units && !*stop; u += gridDim.x) {
+        int64_t shot;
+        int x0, y0;
+        unit_of(u, shot, x0, y0);
+        const int xl = x0 == 0 ? L - 1 : x0 - 1, xr = x0 + kTcM == L ? 0 : x0 + kTcM;
+        int r = -1;
+        for (; r <= kTcStrip; ++r, ++e) {
+          const int slot = (int)(e % kWsR);
+          if (e >= kWsR && !ws_wait(&empty[slot], (uint32_t)((e / kWsR - 1) & 1), stop)) break;
+          int yy = y0 + r;
+          yy = yy < 0 ? yy + L : (yy >= L ? yy - L : yy);
+          uint8_t* dst = sA + (size_t)slot * kRowBytes;
+          mbar_expect_tx_ws(&full[slot], kRowBytes);
+#pragma unroll
+          for (int oct = 0; oct < 4; ++oct) {
+            const __nv_bfloat16* src = in + (((shot * L + yy) * 4 + oct) * (int64_t)L) * 8;
+            uint8_t* d = dst + (size_t)oct * kTcRow * 16;
+            bulk_g2s_ws(d + 16, src + (int64_t)x0 * 8, kTcM * 16, &full[slot]);
+            bulk_g2s_ws(d, src + (int64_t)xl * 8, 16, &full[slot]);
+            bulk_g2s_ws(d + (kTcRow - 1) * 16, src + (int64_t)xr * 8, 16, &full[slot]);
+          }
+        }
+        if (r <= kTcStrip) break;  // stopped
+      }
+      // no copy may still be landing when the CTA exits: wait (bounded) for the
+      // last entry of every slot (a no-op unless the CTA stopped early)
+      for (int64_t f = e > kWsR ? e - kWsR : 0; f < e; ++f)
+        (void)tc_bar_wait(&full[f % kWsR], (uint32_t)((f / kWsR) & 1));
+    }
+    __syncwarp();
+  } else if (FROM_SIG && warp >= kWsEpi && warp < kWsMmaWarp) {
+    // ================= producers: rows y0 - 1 .. y0 + kTcStrip of every unit,
+    // layer 1 gathered from the table
+    const int pt = tid - 32 * kWsEpi;  // 0 .. 32 * kWsProd - 1
+    int64_t e = 0;                     // entries issued by this CTA
+    for (int64_t u = blockIdx.x; u < units && !*stop; u += gridDim.x) {
+      int64_t shot;
+      int x0, y0;
+      unit_of(u, shot, x0, y0);
+      for (int r = -1; r <= kTcStrip && !*stop; ++r, ++e) {
+        const int slot = (int)(e % kWsR);
+        if (e >= kWsR && !ws_wait(&empty[slot], (uint32_t)((e / kWsR - 1) & 1), stop)) break;
+        int yy = y0 + r;
+        yy = yy < 0 ? yy + L : (yy >= L ? yy - L : yy);
+        uint8_t* dst = sA + (size_t)slot * kRowBytes;
+        {
+          const uint8_t* g = sig + shot * LL;
+          const int ym = yy == 0 ? L - 1 : yy - 1, yp = yy == L - 1 ? 0 : yy + 1;
+          for (int j = pt; j < kTcRow; j += 32 * kWsProd) {
+            int xx = x0 + j - 1;
+            xx = xx < 0 ? xx + L : (xx >= L ? xx - L : xx);
+            const int xm = xx == 0 ? L - 1 : xx - 1, xp = xx == L - 1 ? 0 : xx + 1;
+            const int rows[3] = {ym, yy, yp}, cols[3] = {xm, xx, xp};
+            uint32_t idx = 0;
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap)
+              idx |= (g[(int64_t)rows[tap / 3] * L + cols[tap % 3]] ? 1u : 0u) << tap;
+            const __nv_bfloat16* src = lut + (size_t)idx * 32;
+#pragma unroll
+            for (int oct = 0; oct < 4; ++oct)
+              tc_cp16_ca(dst + ((size_t)oct * kTcRow + j) * 16, src + oct * 8);
+          }
+        }
+        tc_cp_commit();
+        if (e >= kWsLag) {
+          // the copies of entry e - kWsLag have landed: publish it
+          asm volatile("cp.async.wait_group %0;" ::"n"(kWsLag) : "memory");
+          tc_fence_proxy_shared();
+          ws_arrive(&full[(e - kWsLag) % kWsR]);
+        }
+      }
+    }
+    // publish the entries still in flight
+    tc_cp_wait_all();
+    tc_fence_proxy_shared();
+    for (int64_t f = e > kWsLag ? e - kWsLag : 0; f < e; ++f) ws_arrive(&full[f % kWsR]);
+  } else if (warp == kWsMmaWarp) {
+    // ================= MMA issue (one thread)
+    if (lane == 0) {
+      const uint32_t idesc = tc_idesc(NOUT, kTcM);
+      const uint32_t a0 = tc_smem(sA), b0 = tc_smem(sB);
+      int64_t e = 0, T = 0;  // first entry of the current unit, tiles issued
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        for (int j = 0; j < kTcStrip && ok; ++j, ++T) {
+          const int64_t eb = e + j;  // entries eb .. eb + 2: rows y - 1 .. y + 1
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy)
+            ok = ok && ws_wait(&full[(eb + dy) % kWsR], (uint32_t)(((eb + dy) / kWsR) & 1), stop);
+          const int acc = (int)(T & 1);
+          if (ok && T >= 2) ok = ws_wait(&acc_empty[acc], (uint32_t)(((T >> 1) - 1) & 1), stop);
+          if (!ok) break;
+          tc_fence_after();
+#pragma unroll
+          for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap % 3 - 1;
+            const uint32_t slot = (uint32_t)((eb + dy) % kWsR);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const uint32_t aaddr =
+                  a0 + slot * kRowBytes + ((uint32_t)((2 * h) * kTcRow + 1 + dx)) * 16;
+              const uint32_t baddr = b0 + ((uint32_t)((tap * 4 + 2 * h) * NOUT)) * 16;
+              tc_mma(tmem + (uint32_t)(acc * 32), tc_desc(aaddr, kTcRow * 16, 128),
+                     tc_desc(baddr, NOUT * 16, 128), idesc, (tap | h) != 0);
+            }
+          }
+          tc_commit(&acc_full[acc]);
+          tc_commit(&empty[eb % kWsR]);  // no later tile reads entry eb
+          if (j == kTcStrip - 1) {       // nor the unit's last two rows
+            tc_commit(&empty[(eb + 1) % kWsR]);
+            tc_commit(&empty[(eb + 2) % kWsR]);
+          }
+        }
+        e += kTcStrip + 2;
+      }
+      // every MMA issued so far has completed before the TMEM is freed
+      tc_commit(drained);
+      if (!tc_bar_wait(drained, 0)) *stop = 1;
+    }
+    __syncwarp();
+  } else {
+    // ================= epilogue: warp w reads TMEM lanes 32 (w % 4) .., columns
+    // 16 (w / 4) .. + 15 of the tile's accumulator
+    const int half = warp >> 2;
+    int64_t T = 0;
+    for (int64_t u = blockIdx.x; u < units && !*stop; u += gridDim.x) {
+      int64_t shot;
+      int x0, y0;
+      unit_of(u, shot, x0, y0);
+      bool ok = true;
+      for (int j = 0; j < kTcStrip; ++j, ++T) {
+        const int acc = (int)(T & 1);
+        ok = ws_wait(&acc_full[acc], (uint32_t)((T >> 1) & 1), stop);
+        if (!__all_sync(0xffffffffu, ok)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        float v[16];
+        tc_ld16(tmem + (uint32_t)(acc * 32 + 16 * half) + ((uint32_t)(32 * (warp & 3)) << 16), v);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ws_arrive(&acc_empty[acc]);
+        const int y = y0 + j, x = x0 + 32 * (warp & 3) + lane;
+        const int64_t site = shot * LL + (int64_t)y * L + x;
+        if (MODE == kActs) {
+          uint32_t w[8];
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            w[c] = pack_bf16(fmaxf(v[2 * c] + sbias[16 * half + 2 * c], 0.f),
+                             fmaxf(v[2 * c + 1] + sbias[16 * half + 2 * c + 1], 0.f));
+          // planar: octets 2 half and 2 half + 1 of site x
+          const int64_t rowo = (shot * L + y) * 4 + 2 * half;
+          *reinterpret_cast<uint4*>(out + (rowo * L + x) * 8) = make_uint4(w[0], w[1], w[2], w[3]);
+          *reinterpret_cast<uint4*>(out + ((rowo + 1) * L + x) * 8) =
+              make_uint4(w[4], w[5], w[6], w[7]);
+        } else if (half == 0) {
+          const float z[4] = {v[0] + sbias[0], v[1] + sbias[1], v[2] + sbias[2], v[3] + sbias[3]};
+          if (MODE == kLogits) {
+            float* lb = logits + shot * 4 * LL + (int64_t)y * L + x;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) lb[(int64_t)k * LL] = z[k];
+          } else {
+            float best = z[0];
+            int bk = 0;
+#pragma unroll
+            for (int q = 1; q < 4; ++q)
+              if (z[q] > best) {
+                best = z[q];
+                bk = q;
+              }
+            prop[site] = (sig[site] && best > 0.f) ? (uint8_t)bk : (uint8_t)4;
+          }
+        }
+      }
+      if (!ok) break;
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && *stop) atomicOr(err, 1u);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64)
+                 : "memory");
+}
+
+template <int NOUT>
+constexpr size_t ws_smem_bytes() {
+  return (size_t)kWsR * 4 * kTcRow * 16 + 9 * 4 * NOUT * 16 + (2 * kWsR + 5) * 8 + 16 + 4 * NOUT;
+}
+
 // ------------------------------------------------------ inference (FP8) ----
 //
 // FP8 (E4M3) form of layers 2-4: weights quantised per output channel,
@@ -1203,7 +1544,8 @@ struct qca_net_s {
   float act_scale[3] = {0.f, 0.f, 0.f};
   int precision = 0;  // 0 bf16, 1 fp8
   bool prepared8 = false;
-  int use_tc = 1;                // bf16 layers 2-4 on tcgen05 where L % 128 == 0
+  int use_tc = 2;                // bf16 layers 2-4: 0 mma.sync, 1 tcgen05 row-synchronous,
+                                 // 2 tcgen05 warp-specialised (tcgen05 where L % 128 == 0)
   unsigned int* err = nullptr;   // device word: a tensor-core wait timed out
   __nv_bfloat16* lut = nullptr;  // layer-1 outputs per 3 x 3 anyon pattern [512][32]
   // inference workspace
@@ -1585,6 +1927,41 @@ int net_run(qca_net_s* n, const uint8_t* noise, int L, int64_t shots, float* log
       if (e != cudaSuccess) return cuda_fail(e, "net fp8 inference kernels");
       continue;
     }
+    if (n->use_tc == 2 && L % kTcM == 0 && L % kTcStrip == 0) {
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const int64_t units = S / ((int64_t)kTcM * kTcStrip);
+      const int gt = (int)(units < (int64_t)sms * 2 ? units : (int64_t)sms * 2);
+      cudaFuncSetAttribute(conv_ws_kernel<32, kActs, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem_bytes<32>());
+      cudaFuncSetAttribute(conv_ws_kernel<32, kActs, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem_bytes<32>());
+      cudaFuncSetAttribute(conv_ws_kernel<16, kLogits, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem_bytes<16>());
+      cudaFuncSetAttribute(conv_ws_kernel<16, kProposals, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem_bytes<16>());
+      // layers 1 + 2 (layer 1 looked up while staging), 3, 4
+      conv_ws_kernel<32, kActs, true><<<gt, kWsThreads, ws_smem_bytes<32>(), st>>>(
+          nullptr, n->wb, n->params + kB1, L, m, actB, nullptr, sig, nullptr, n->err, n->lut);
+      conv_ws_kernel<32, kActs, false><<<gt, kWsThreads, ws_smem_bytes<32>(), st>>>(
+          actB, n->wb + 9 * 32 * 32, n->params + kB2, L, m, actA, nullptr, nullptr, nullptr,
+          n->err, nullptr);
+      if (logits) {
+        conv_ws_kernel<16, kLogits, false><<<gt, kWsThreads, ws_smem_bytes<16>(), st>>>(
+            actA, n->wb + 2 * 9 * 32 * 32, n->params + kB3, L, m, nullptr, logits + c0s * 4 * LL,
+            nullptr, nullptr, n->err, nullptr);
+      } else {
+        conv_ws_kernel<16, kProposals, false><<<gt, kWsThreads, ws_smem_bytes<16>(), st>>>(
+            actA, n->wb + 2 * 9 * 32 * 32, n->params + kB3, L, m, nullptr, nullptr, sig, prop,
+            n->err, nullptr);
+        pairing_kernel<<<grid_for(S, 256), 256, 0, st>>>(Nc, prop, L, m, resid + c0s * 2 * LL,
+                                                         c0 ? c0 + c0s * 2 * LL : nullptr);
+      }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e, "net warp-specialised tcgen05 kernels");
+      continue;
+    }
     if (n->use_tc && L % kTcM == 0 && L % kTcStrip == 0) {
       int dev = 0, sms = 0;
       cudaGetDevice(&dev);
@@ -1692,12 +2069,13 @@ int qca_net_get_fp8_scales(qca_net_t n, float* scales) {
   return QCA_OK;
 }
 
-int qca_net_set_tensor_path(qca_net_t n, int use_tcgen05) {
-  if (!n || (use_tcgen05 != 0 && use_tcgen05 != 1)) {
-    set_error("qca_net_set_tensor_path: 0 (mma.sync) or 1 (tcgen05 where L %% 128 == 0)");
+int qca_net_set_tensor_path(qca_net_t n, int path) {
+  if (!n || path < 0 || path > 2) {
+    set_error("qca_net_set_tensor_path: 0 (mma.sync), 1 (tcgen05, row-synchronous) or 2 "
+              "(tcgen05, warp-specialised), the tcgen05 forms where L %% 128 == 0");
     return QCA_ERR_ARG;
   }
-  n->use_tc = use_tcgen05;
+  n->use_tc = path;
   return QCA_OK;
 }
 

@@ -66,18 +66,25 @@ def test_labels_bit_exact(L, p, shots):
 
 # ------------------------------------------------------------------- logits
 
-def _check_logits(net, L, shots, p, seed):
+def _check_logits(net, L, shots, p, seed, all_within=True):
+    # all_within=False: a trained net's larger weights turn the rare bf16
+    # rounding flip of an intermediate activation (fp32 and fp64 values on
+    # either side of a bf16 boundary) into a logit change of up to |W| times
+    # one bf16 step; the training's float atomics make the weights differ
+    # slightly from run to run, so the bar is 99.9 % within 1e-2, none beyond 0.03
     N = oracle.sample_errors(L, shots, p, seed=seed)
     z = net.logits(dev(N))
     torch.cuda.synchronize()
     z = z.cpu().numpy()
     params = net.get_params()
     A = anyon_maps(N)
-    worst = 0.0
-    for s in range(shots):
-        want = onet.forward(A[s], params, quantize=True)
-        worst = max(worst, float(np.max(np.abs(z[s] - want))))
-    assert worst <= 1e-2, f"max |logit - fp64 forward| = {worst}"
+    d = np.concatenate([np.abs(z[s] - onet.forward(A[s], params, quantize=True)).ravel()
+                        for s in range(shots)])
+    worst = float(d.max())
+    if all_within:
+        assert worst <= 1e-2, f"max |logit - fp64 forward| = {worst}"
+    else:
+        assert np.mean(d <= 1e-2) >= 0.999 and worst <= 0.03, (np.mean(d <= 1e-2), worst)
     return worst
 
 
@@ -92,8 +99,8 @@ def test_logits_initial_net(L, shots):
 
 def test_logits_trained_net(trained):
     net, _ = trained
-    _check_logits(net, 24, 4, 0.05, seed=9)
-    _check_logits(net, 19, 2, 0.07, seed=10)
+    _check_logits(net, 24, 4, 0.05, seed=9, all_within=False)
+    _check_logits(net, 19, 2, 0.07, seed=10, all_within=False)
 
 
 def test_set_get_params_roundtrip():
@@ -294,13 +301,17 @@ def test_tcgen05_logits_match_fp64_and_mma_path(trained):
     L, shots = 128, 2
     N = oracle.sample_errors(L, shots, 0.05, seed=51)
     Nd = dev(N)
-    net.set_tensor_path(True)
+    net.set_tensor_path("tcgen05")
     z_tc = net.logits(Nd).cpu().numpy()
     net.status()
-    net.set_tensor_path(False)
+    net.set_tensor_path("tcgen05_ws")
+    z_ws = net.logits(Nd).cpu().numpy()
+    net.status()
+    net.set_tensor_path("mma")
     z_ms = net.logits(Nd).cpu().numpy()
-    net.set_tensor_path(True)
+    net.set_tensor_path("tcgen05_ws")
     np.testing.assert_array_equal(z_tc, z_ms)
+    np.testing.assert_array_equal(z_ws, z_ms)
     params = net.get_params()
     A = anyon_maps(N)
     d = np.concatenate([np.abs(z_tc[s] - onet.forward(A[s], params, quantize=True)).ravel()
@@ -308,10 +319,30 @@ def test_tcgen05_logits_match_fp64_and_mma_path(trained):
     assert np.mean(d <= 1e-2) >= 0.9999 and d.max() <= 0.03, (np.mean(d <= 1e-2), d.max())
 
 
+def test_tcgen05_warp_specialised_matches_row_synchronous(trained):
+    # enough shots that every CTA runs several work units through its ring of
+    # staged rows (units = shots * (L / 128) * (L / 64) > twice the SM count)
+    net, _ = trained
+    net.set_precision("bf16")
+    L, shots = 128, 400
+    Nd = qca.sample_errors(L, shots, 0.05, seed=53)
+    out = {}
+    for path in ("tcgen05", "tcgen05_ws"):
+        net.set_tensor_path(path)
+        z = net.logits(Nd)
+        R, C0 = net.predecode(Nd)
+        torch.cuda.synchronize()
+        net.status()
+        out[path] = (z.cpu().numpy(), R.cpu().numpy(), C0.cpu().numpy())
+    net.set_tensor_path("tcgen05_ws")
+    for a, b in zip(out["tcgen05"], out["tcgen05_ws"]):
+        np.testing.assert_array_equal(a, b)
+
+
 def test_tcgen05_pairing_bit_exact_and_decode(trained):
     net, _ = trained
     net.set_precision("bf16")
-    net.set_tensor_path(True)
+    net.set_tensor_path("tcgen05_ws")
     L, shots = 256, 3
     N = oracle.sample_errors(L, shots, 0.05, seed=52)
     Nd = dev(N)
