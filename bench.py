@@ -36,7 +36,7 @@ MAX_STEPS = 4096
 METRIC = "shot-decodes/s and site-updates/s at L=256,p=0.05 (plain vs net+CA, same p_log)"
 UNIT = "shot-decodes/s"
 
-# Integer-ALU roofline of the sweep (derivation in the design doc): the fused
+# Integer-ALU roofline of the sweep: the fused
 # v = 3 message update costs 16 min/compare lane-ops per site-update (4 fields x
 # (3 two-input mins of the width-7 cone window + 1 clamp)); the ALU pipe issues
 # 64 32-bit instructions / clk / SM (measured with a microbenchmark on GB300:
@@ -591,8 +591,8 @@ def run_large(args, rank, world, local):
         dist.destroy_process_group()
 
 
-# Shared-memory bytes the 1D kernel reads and writes per site-update (derivation
-# in the design doc): two fields x (up to 3 syndrome bytes, 1 old value, 1 new
+# Shared-memory bytes the 1D kernel reads and writes per site-update: two
+# fields x (up to 3 syndrome bytes, 1 old value, 1 new
 # value), the move pass (syndrome, fields, move byte), feedback (two move
 # bytes, correction read/write), syndrome update (two correction bytes,
 # syndrome read/write) and the flag clear (correction read/write).

@@ -112,11 +112,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
-// Byte-wise unsigned min on the native 16x2 min (each byte alone in a lane).
-__device__ __forceinline__ uint32_t vmin4(uint32_t a, uint32_t b) {
-  return __vminu2(a & 0xFF00FF00u, b & 0xFF00FF00u) | __vminu2(a & 0x00FF00FFu, b & 0x00FF00FFu);
-}
-
 __device__ __forceinline__ int twrap(int i, int L) { return i < 0 ? i + L : (i >= L ? i - L : i); }
 
 // Four bits of a bitmap row starting at bit position pos (wrapping at the row end).
@@ -258,8 +253,10 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
       // sigma (Def. synch_ccqs: parity of the four links incident to r)
       uint32_t* Sx = sigf(0);
       int cnt = 0;
-      for (int i = tid; i < RL * W; i += nt) {
-        const int y = r0 + i / W, x0 = (i % W) * 32;
+      // a warp per row, a lane per word (W <= 32)
+      for (int rr = warp; rr < RL; rr += nw) {
+        if (lane >= W) continue;
+        const int y = r0 + rr, x0 = lane * 32;
         uint32_t bits = 0;
         if (a.from_sigma) {
           const uint8_t* row = N + (size_t)y * L + x0;
@@ -281,7 +278,7 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
           const uint32_t left = N[(size_t)y * L + twrap(x0 - 1, L)] & 1u;  // e_x(r - x^)
           bits = bx ^ ((bx << 1) | left) ^ by ^ byd;
         }
-        Sx[(size_t)y * W + (i % W)] = bits;
+        Sx[(size_t)y * W + lane] = bits;
         cnt += __popc(bits);
       }
       fence_proxy_async_global();
@@ -336,8 +333,9 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
         const uint8_t* Bk = band + (size_t)buf * kTRows * L;
         const uint32_t* Sb = sband + (size_t)buf * kTRows * W;
         // dilated syndrome rows D_d(R) = OR_{|j| <= d} sigma(R + j), d = 1, 2, 3
-        for (int idx = tid; idx < kTB * W; idx += nt) {
-          const int r = idx / W, w = idx - r * W;
+        for (int r = warp; r < kTB; r += nw) {
+          const int w = lane;
+          if (w >= W) continue;
           const uint32_t* c = Sb + (size_t)(r + 3) * W + w;
           const uint32_t d1 = c[-W] | c[0] | c[W];
           const uint32_t d2 = d1 | c[-2 * W] | c[2 * W];
@@ -374,7 +372,10 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
             const uint32_t h6 = w & 0xFF00FF00u, l6 = w & 0x00FF00FFu;
             const uint32_t mh = __vminu2(__vminu2(qh[0], qh[2]), __vminu2(qh[4], h6));
             const uint32_t ml = __vminu2(__vminu2(ql[0], ql[2]), __vminu2(ql[4], l6));
-            M[(size_t)r * cols + kc] = mh | ml;
+            // +3 saturating at 0xFF while each byte sits alone in a 16-bit lane:
+            // clamp at 0xFC, then add (no carry leaves the lane)
+            M[(size_t)r * cols + kc] = (__vminu2(mh, 0xFC00FC00u) + 0x03000300u) |
+                                       (__vminu2(ml, 0x00FC00FCu) + 0x00030003u);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               qh[j] = qh[j + 1];
@@ -387,12 +388,13 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
           }
         }
         __syncthreads();
-        // shift by 3 sites along the byte axis, +3 (saturating), anyon terms
+        // shift by 3 sites along the byte axis, anyon terms
         const bool plus = (p % 2) == 0;  // m^{+a} reads from r - 3 a^
         uint32_t* out = reinterpret_cast<uint32_t*>(plane(dst, p)) + (size_t)R0 * cols;
         const uint32_t v1 = (uint32_t)(g.off) * 0x01010101u;
-        for (int idx = tid; idx < kTB * cols; idx += nt) {
-          const int r = idx / cols, kc = idx - r * cols;
+        // items idx = r * cols + kc (r < kTB), stepped by nt without division
+        int r = tid / cols, kc = tid - r * cols;
+        while (r < kTB) {
           const uint32_t* Mr = M + (size_t)r * cols;
           uint32_t s;
           if (plus) {
@@ -402,24 +404,31 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
             const int kp = kc + 1 == cols ? 0 : kc + 1;
             s = __funnelshift_r(Mr[kc], Mr[kp], 24);
           }
-          uint32_t v = vmin4(s, 0xFCFCFCFCu) + 0x03030303u;
-          // terms: the smallest d wins (d = 3 first, overwritten by smaller d).
+          uint32_t v = s;
+          // terms: the smallest d wins (d = 3 first, overwritten by smaller d),
+          // and every term lies below every propagated value, so it replaces it.
           // The d <= 3 cones of the word's four sites read positions
           // 4 kc - 3 .. 4 kc + 2 (m^+) or 4 kc + 1 .. 4 kc + 6 (m^-) of the
           // dilated rows, and D_3 contains D_2 and D_1: if those six bits of
           // D_3 are clear there is no term.
           const uint32_t* D3 = D + (size_t)(2 * kTB + r) * W;
           if (bits6(D3, W, twrap(4 * kc + (plus ? -3 : 1), L))) {
-            uint32_t T = 0xFFFFFFFFu;
+            uint32_t T = 0u, any = 0u;
 #pragma unroll
             for (int d = 3; d >= 1; --d) {
               const int pos = twrap(4 * kc + (plus ? -d : d), L);
               const uint32_t m = nib_mask(bits4(D + (size_t)((d - 1) * kTB + r) * W, W, pos));
               T = (T & ~m) | ((v1 + (uint32_t)(d - 1) * 0x01010101u) & m);
+              any |= m;
             }
-            v = vmin4(v, T);
+            v = (v & ~any) | (T & any);
           }
           out[(size_t)r * cols + kc] = v;
+          kc += nt;
+          while (kc >= cols) {
+            kc -= cols;
+            ++r;
+          }
         }
         __syncthreads();  // M, D and the band buffer are free again
       }
@@ -436,8 +445,9 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
         const uint32_t* Sx = sigf(0);
         uint64_t kstep = 0;
         if (a.move_thr) kstep = move_step_key(a.move_key, a.shot_offset + shot, t);
-        for (int i = tid; i < RL * W; i += nt) {
-          const int y = r0 + i / W, wq = i % W;
+        for (int rr = warp; rr < RL; rr += nw) {
+          const int y = r0 + rr, wq = lane;
+          if (wq >= W) continue;
           uint32_t bits = Sx[(size_t)y * W + wq];
           while (bits) {
             // up to four anyons of the word at a time: all sixteen field loads
@@ -489,8 +499,9 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
           const uint32_t* Fa = flip(par, fr, fr == 0 ? 0 : 1);  // links along the row
           const uint32_t* Fc = flip(par, fr, fr == 0 ? 1 : 0);  // links across rows
           uint32_t* S = sigf(fr);
-          for (int i = tid; i < RL * W; i += nt) {
-            const int R = r0 + i / W, wq = i % W;
+          for (int rr = warp; rr < RL; rr += nw) {
+            const int R = r0 + rr, wq = lane;
+            if (wq >= W) continue;
             const int Rm = twrap(R - 1, L), wm = wq == 0 ? W - 1 : wq - 1;
             const uint32_t fa = Fa[(size_t)R * W + wq];
             const uint32_t fa_prev = Fa[(size_t)R * W + wm];
@@ -540,7 +551,7 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
     for (int kd = 0; kd < 2; ++kd) {
       const uint32_t* C = Cb + (size_t)kd * L * W;
       for (int i = tid; i < RL * (L / 4); i += nt) {
-        const int y = r0 + i / (L / 4), x = (i % (L / 4)) * 4;
+        const int q = i / cols, y = r0 + q, x = (i - q * cols) * 4;
         const uint32_t nib = (C[(size_t)y * W + (x >> 5)] >> (x & 31)) & 0xFu;
         *reinterpret_cast<uint32_t*>(outC + (size_t)kd * LL + (size_t)y * L + x) =
             (nib * 0x00204081u) & 0x01010101u;
