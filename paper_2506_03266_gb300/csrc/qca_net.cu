@@ -26,6 +26,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "qca_internal.cuh"
@@ -1403,7 +1404,7 @@ __global__ void loss_grad_nhwc_kernel(const float* __restrict__ z, const uint8_t
 // per-channel sum of a bf16 NHWC [S][32] gradient into db[0 .. CO)
 template <int CO>
 __global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ d, int64_t S,
-                                 float* __restrict__ db) {
+                                 float* __restrict__ part) {
   __shared__ float red[8][32];
   const int c = threadIdx.x & 31, row = threadIdx.x >> 5;
   float acc = 0.f;
@@ -1414,7 +1415,19 @@ __global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ d, int64_t S,
   if (row == 0) {
     float v = 0.f;
     for (int r = 0; r < 8; ++r) v += red[r][c];
-    if (c < CO) atomicAdd(&db[c], v);
+    part[(size_t)blockIdx.x * 32 + c] = v;  // this CTA's partial sums, [CTA][32]
+  }
+}
+
+// out[i] = sum over p = 0 .. nparts - 1, in that order, of part[p * stride + i]:
+// the per-CTA partial sums of a gradient added in a fixed order, so that a
+// training run repeats bit for bit.
+__global__ void reduce_parts_kernel(const float* __restrict__ part, int nparts, int stride, int n,
+                                    float* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float v = 0.f;
+    for (int q = 0; q < nparts; ++q) v += part[(size_t)q * stride + i];
+    out[i] = v;
   }
 }
 
@@ -1430,7 +1443,7 @@ template <int CO_REAL, int CI_REAL>
 __global__ void __launch_bounds__(256) wgrad_mma_kernel(const __nv_bfloat16* __restrict__ dout,
                                                         const __nv_bfloat16* __restrict__ in,
                                                         int L, int64_t S, int64_t chunk,
-                                                        float* __restrict__ dW) {
+                                                        float* __restrict__ part) {
   __shared__ uint32_t sD[32 * kWgPitch];       // [co][site pair]
   __shared__ uint32_t sI[9 * 32 * kWgPitch];   // [tap][ci][site pair]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1503,8 +1516,9 @@ __global__ void __launch_bounds__(256) wgrad_mma_kernel(const __nv_bfloat16* __r
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int ci = cb + e;
-        if (co < CO_REAL && ci < CI_REAL)
-          atomicAdd(&dW[(co * CI_REAL + ci) * 9 + tap], acc[k][2 * h + e]);
+        if (co < CO_REAL && ci < CI_REAL)  // this CTA's partial sums, [CTA][param]
+          part[(size_t)blockIdx.x * (CO_REAL * CI_REAL * 9) + (co * CI_REAL + ci) * 9 + tap] =
+              acc[k][2 * h + e];
       }
     }
   }
@@ -1641,12 +1655,18 @@ int qca_net_set_params(qca_net_t n, const float* host, int64_t count) {
 namespace {
 
 // Device buffers of one training batch of S sites.
+// Gradient reductions split the sites into at most kGradParts CTAs, a number
+// fixed by the batch size alone (not by the device), and add the CTAs' partial
+// sums in order.
+constexpr int kGradParts = 256;
+
 struct TrainBufs {
   int64_t S = 0;
   uint8_t* bytes = nullptr;        // sig, dir, lab
   __nv_bfloat16* h = nullptr;      // x0, a1, a2, a3, dz, g1, g2: bf16 NHWC [S][32] each
   float* z = nullptr;              // logits fp32 [B][4][L][L]
   __nv_bfloat16* wt = nullptr;     // backward-data weights [3][9][32][32]
+  float* part = nullptr;           // per-CTA gradient partial sums [kGradParts][9216]
   uint8_t* sig() const { return bytes; }
   uint8_t* dir() const { return bytes + S; }
   uint8_t* lab() const { return bytes + 2 * S; }
@@ -1657,6 +1677,7 @@ struct TrainBufs {
     if (e == cudaSuccess) e = cudaMalloc(&h, sizeof(__nv_bfloat16) * 7 * 32 * S);
     if (e == cudaSuccess) e = cudaMalloc(&z, sizeof(float) * 4 * S);
     if (e == cudaSuccess) e = cudaMalloc(&wt, sizeof(__nv_bfloat16) * 3 * 9 * 32 * 32);
+    if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(float) * kGradParts * 9 * 32 * 32);
     return cuda_fail(e, "training buffers");
   }
   ~TrainBufs() {
@@ -1664,6 +1685,7 @@ struct TrainBufs {
     cudaFree(h);
     cudaFree(z);
     cudaFree(wt);
+    cudaFree(part);
   }
 };
 
@@ -1675,12 +1697,15 @@ int train_forward_backward(qca_net_s* n, const TrainBufs& b, int L, int batch,
   const int64_t S = b.S;
   const int gS = grid_for(S, 256);
   const int gm = grid_for((S + 15) / 16 * 32, 128);
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t chunk = (S + 2 * (int64_t)sms - 1) / (2 * (int64_t)sms);
+  // weight gradients: CTAs of `chunk` sites (a multiple of the staging chunk);
+  // bias gradients: gB CTAs; both counts depend on S only
+  int64_t chunk = (S + kGradParts - 1) / kGradParts;
   chunk = ((chunk + kWgChunk - 1) / kWgChunk) * kWgChunk;
   const int gW = (int)((S + chunk - 1) / chunk);
+  const int gB = (int)std::min<int64_t>(kGradParts, (S + 255) / 256);
+  auto reduce = [&](int nparts, int stride, int n, float* out) {
+    reduce_parts_kernel<<<(n + 255) / 256, 256>>>(b.part, nparts, stride, n, out);
+  };
   __nv_bfloat16 *x0 = b.act(0), *a1 = b.act(1), *a2 = b.act(2), *a3 = b.act(3), *dz = b.act(4),
                 *g1 = b.act(5), *g2 = b.act(6);
   // weights of this step: bf16 forward copies, mirrored backward copies
@@ -1698,22 +1723,29 @@ int train_forward_backward(qca_net_s* n, const TrainBufs& b, int L, int batch,
                                            nullptr, b.z, nullptr, nullptr, nullptr);
   loss_grad_nhwc_kernel<<<gS, 256>>>(b.z, b.lab(), L, batch, count, dz, loss);
   // backward: layer 4, 3, 2 (weights, bias, masked input gradient), layer 1
-  cudaMemsetAsync(n->grads, 0, sizeof(float) * kParams);
   float* G = n->grads;
-  wgrad_mma_kernel<4, 32><<<gW, 256>>>(dz, a3, L, S, chunk, G + kW3);
-  bias_grad_kernel<4><<<gS, 256>>>(dz, S, G + kB3);
+  wgrad_mma_kernel<4, 32><<<gW, 256>>>(dz, a3, L, S, chunk, b.part);
+  reduce(gW, 4 * 32 * 9, 4 * 32 * 9, G + kW3);
+  bias_grad_kernel<4><<<gB, 256>>>(dz, S, b.part);
+  reduce(gB, 32, 4, G + kB3);
   conv_mma_kernel<4, kGradMasked><<<gm, 128>>>(dz, b.wt + 2 * 9 * 32 * 32, nullptr, L, batch, g1,
                                                nullptr, nullptr, nullptr, a3);
-  wgrad_mma_kernel<32, 32><<<gW, 256>>>(g1, a2, L, S, chunk, G + kW2);
-  bias_grad_kernel<32><<<gS, 256>>>(g1, S, G + kB2);
+  wgrad_mma_kernel<32, 32><<<gW, 256>>>(g1, a2, L, S, chunk, b.part);
+  reduce(gW, 32 * 32 * 9, 32 * 32 * 9, G + kW2);
+  bias_grad_kernel<32><<<gB, 256>>>(g1, S, b.part);
+  reduce(gB, 32, 32, G + kB2);
   conv_mma_kernel<4, kGradMasked><<<gm, 128>>>(g1, b.wt + 9 * 32 * 32, nullptr, L, batch, g2,
                                                nullptr, nullptr, nullptr, a2);
-  wgrad_mma_kernel<32, 32><<<gW, 256>>>(g2, a1, L, S, chunk, G + kW1);
-  bias_grad_kernel<32><<<gS, 256>>>(g2, S, G + kB1);
+  wgrad_mma_kernel<32, 32><<<gW, 256>>>(g2, a1, L, S, chunk, b.part);
+  reduce(gW, 32 * 32 * 9, 32 * 32 * 9, G + kW1);
+  bias_grad_kernel<32><<<gB, 256>>>(g2, S, b.part);
+  reduce(gB, 32, 32, G + kB1);
   conv_mma_kernel<4, kGradMasked><<<gm, 128>>>(g2, b.wt, nullptr, L, batch, g1, nullptr, nullptr,
                                                nullptr, a1);
-  wgrad_mma_kernel<32, 2><<<gW, 256>>>(g1, x0, L, S, chunk, G + kW0);
-  bias_grad_kernel<32><<<gS, 256>>>(g1, S, G + kB0);
+  wgrad_mma_kernel<32, 2><<<gW, 256>>>(g1, x0, L, S, chunk, b.part);
+  reduce(gW, 32 * 2 * 9, 32 * 2 * 9, G + kW0);
+  bias_grad_kernel<32><<<gB, 256>>>(g1, S, b.part);
+  reduce(gB, 32, 32, G + kB0);
   return cuda_fail(cudaGetLastError(), "training kernels");
 }
 

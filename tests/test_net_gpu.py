@@ -362,6 +362,22 @@ def test_tcgen05_pairing_bit_exact_and_decode(trained):
 
 # ------------------------------------------------- training on tensor cores
 
+def test_training_repeats_bit_for_bit():
+    # the gradient partial sums are added in a fixed order: two runs from the
+    # same initial weights and seed end with the same weights
+    a, b = qca.Net(seed=5), qca.Net(seed=5)
+    try:
+        p0 = a.get_params()
+        for net in (a, b):
+            net.train(L=16, iterations=40, batch=8, p_lo=0.02, p_hi=0.07, seed=3, lr=2e-3)
+        pa, pb = a.get_params(), b.get_params()
+        assert np.any(pa != p0)  # the runs did train
+        np.testing.assert_array_equal(pa, pb)
+    finally:
+        a.close()
+        b.close()
+
+
 def test_gradients_match_fp64_reference():
     # one training step's gradient (bf16 operands, fp32 accumulation) against
     # the FP64 reference of the same loss: the bf16 rounding of weights and
