@@ -592,11 +592,11 @@ def run_large(args, rank, world, local):
 
 
 # Shared-memory bytes the 1D kernel reads and writes per site-update: two
-# fields x (up to 3 syndrome bytes, 1 old value, 1 new
-# value), the move pass (syndrome, fields, move byte), feedback (two move
-# bytes, correction read/write), syndrome update (two correction bytes,
-# syndrome read/write) and the flag clear (correction read/write).
-SMEM_BYTES_PER_SITE_UPDATE_1D = 22
+# fields x (up to 3 syndrome bytes, 1 old value, 1 new value), the move
+# (syndrome byte, move byte; the fields are still in registers), feedback (two
+# move bytes, flip byte, correction read/write) and the syndrome update (two
+# flip bytes, syndrome read/write).
+SMEM_BYTES_PER_SITE_UPDATE_1D = 21
 SMEM_PEAK_BYTES = 152 * 128 * 2.070e9  # 128 B/clk/SM at the maximum SM clock
 
 

@@ -16,6 +16,8 @@
 //      direction with probability p_move;
 //   3. feedback: link <r, r+1> flips iff the anyon at r moves right or the
 //      anyon at r+1 moves left (the OR); C ^= F, sigma updated.
+// A thread decides the moves of its own sites right after their fields, so a
+// step takes three block barriers.
 // After the last step N xor C is constant on the ring; its value is the
 // decoded logical value.
 #include "qca_internal.cuh"
@@ -25,7 +27,7 @@ namespace qca {
 namespace {
 
 constexpr uint64_t kTagNoise1D = 0x4E4F49534531ULL;  // "NOISE1"
-constexpr int k1DThreads = 256;
+constexpr int k1DThreads = 128;
 
 __global__ void sample_1d_kernel(int L, int64_t shot0, int64_t shots, uint64_t thr, uint64_t seed,
                                  uint8_t* __restrict__ out) {
@@ -56,10 +58,19 @@ struct Args1D {
   uint8_t* out_maj;
 };
 
-// i mod L for any i (offsets up to v = 8 can exceed a short ring)
+// i mod L: one correction covers every offset of a ring of at least 8 sites
+// (offsets are at most v = 8); shorter rings take the remainder
 __device__ __forceinline__ int rwrap(int i, int L) {
-  const int r = i % L;
-  return r < 0 ? r + L : r;
+  if (i < 0) {
+    i += L;
+  } else if (i >= L) {
+    i -= L;
+  }
+  if (i < 0 || i >= L) {
+    i %= L;
+    if (i < 0) i += L;
+  }
+  return i;
 }
 
 __global__ void __launch_bounds__(k1DThreads) decode_1d_kernel(Args1D a) {
@@ -69,6 +80,7 @@ __global__ void __launch_bounds__(k1DThreads) decode_1d_kernel(Args1D a) {
   uint8_t* sig = sm + 4 * L;     // 1 = anyon
   uint8_t* C = sig + L;
   uint8_t* mv = C + L;           // per-site move: 0 none, 1 right, 2 left
+  uint8_t* F = mv + L;           // link <r, r + 1> flipped this step
   const int off = 255 - a.m_max, v = a.v;
   const int reach = v < a.m_max ? v : a.m_max;  // terms d <= reach are representable
   for (int64_t shot = blockIdx.x; shot < a.shots; shot += gridDim.x) {
@@ -90,10 +102,14 @@ __global__ void __launch_bounds__(k1DThreads) decode_1d_kernel(Args1D a) {
         flag = 2;
         break;
       }
-      // 1. fused v sub-steps of A^(1)
+      // 1. fused v sub-steps of A^(1) for both fields of the thread's sites,
+      // 2. and at once the move of an anyon there (it reads only its own site)
       const uint8_t* w0 = wbuf + cur * 2 * L;
       uint8_t* w1 = wbuf + (cur ^ 1) * 2 * L;
+      uint64_t kstep = 0;
+      if (a.move_thr) kstep = move_step_key(a.move_key, a.shot_offset + shot, t);
       for (int r = tid; r < L; r += nt) {
+        uint32_t wk[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
           const int s = k == 0 ? 1 : -1;
@@ -108,17 +124,11 @@ __global__ void __launch_bounds__(k1DThreads) decode_1d_kernel(Args1D a) {
             out = old + (uint32_t)v > 0xFEu ? 0xFFu : old + (uint32_t)v;
           }
           w1[k * L + r] = (uint8_t)out;
+          wk[k] = out;
         }
-      }
-      cur ^= 1;
-      __syncthreads();
-      // 2. moves of the anyons
-      uint64_t kstep = 0;
-      if (a.move_thr) kstep = move_step_key(a.move_key, a.shot_offset + shot, t);
-      for (int r = tid; r < L; r += nt) {
         uint8_t m = 0;
         if (sig[r]) {
-          const uint32_t wp = w1[r], wm = w1[L + r];
+          const uint32_t wp = wk[0], wm = wk[1];
           m = wm < wp ? 1 : (wp < wm ? 2 : 0);  // toward the smaller field; 0xFF = none
           if (a.move_thr) {
             const uint64_t u = splitmix64(kstep ^ (uint64_t)r);
@@ -127,24 +137,21 @@ __global__ void __launch_bounds__(k1DThreads) decode_1d_kernel(Args1D a) {
         }
         mv[r] = m;
       }
+      cur ^= 1;
       __syncthreads();
-      // 3. feedback (OR), correction; the new sigma needs the flips of both
-      //    neighbouring links, so flips go to a temporary first (C's high bit)
+      // 3. feedback (OR) and correction
       for (int r = tid; r < L; r += nt) {
-        const int rn = rwrap(r + 1, L);
-        const uint8_t f = (mv[r] == 1 || mv[rn] == 2) ? 1 : 0;
-        C[r] = (uint8_t)((C[r] ^ f) | (f << 1));
+        const uint8_t f = (mv[r] == 1 || mv[rwrap(r + 1, L)] == 2) ? 1 : 0;
+        F[r] = f;
+        C[r] ^= f;
       }
       __syncthreads();
       cnt = 0;
       for (int r = tid; r < L; r += nt) {
-        const uint8_t fl = (C[rwrap(r - 1, L)] >> 1) & 1u, fr = (C[r] >> 1) & 1u;
-        const uint8_t s = sig[r] ^ fl ^ fr;
+        const uint8_t s = sig[r] ^ F[rwrap(r - 1, L)] ^ F[r];
         sig[r] = s;
         cnt += s;
       }
-      __syncthreads();
-      for (int r = tid; r < L; r += nt) C[r] &= 1u;
       any = __syncthreads_count(cnt > 0);
       ++t;
     }
@@ -234,7 +241,7 @@ int qca_decode_1d_batch_async(const uint8_t* noise, int L, int64_t shots, int ma
   a.out_steps = out_steps;
   a.out_flag = out_flag;
   a.out_maj = out_majority_flag;
-  const size_t smem = 7 * (size_t)L;
+  const size_t smem = 8 * (size_t)L;
   cudaError_t e = cudaFuncSetAttribute(decode_1d_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "1D decode smem attribute");
