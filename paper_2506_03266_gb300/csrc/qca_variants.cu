@@ -1,5 +1,6 @@
 // Two variants of the 2D decoder, on a literal per-site sweep with the state in
-// a per-CTA slot of global memory (one CTA per shot, grid-stride over shots):
+// a per-CTA slot (one CTA per shot, grid-stride over shots): shared memory
+// where the 14 L^2 bytes of a shot fit (L <= 85), else global memory:
 //
 //   OPEN   open boundaries (Appendix "Open boundary conditions", Def. "message
 //          passing automaton with open boundaries"): an L x L grid without
@@ -30,6 +31,7 @@ namespace qca {
 namespace {
 
 constexpr int kVThreads = 512;
+constexpr size_t kVSmemSlot = 100 * 1024;  // largest per-shot state kept in shared memory
 constexpr uint64_t kTagDesync = 0x444553594E43ULL;  // "DESYNC"
 
 enum VariantMode { kOpen = 0, kDesync = 1 };
@@ -75,12 +77,14 @@ __device__ __forceinline__ bool open_link(int L, int plane, int x, int y) {
   return plane == 0 ? x <= L - 2 : (x >= 1 && x <= L - 2 && y <= L - 2);
 }
 
+// ws == nullptr: the slot is this CTA's dynamic shared memory (small L)
 template <int MODE>
 __global__ void __launch_bounds__(kVThreads) variant_kernel(VariantArgs a, uint8_t* ws,
                                                            size_t slot_bytes) {
+  extern __shared__ __align__(16) uint8_t vsm[];
   const int L = a.L;
   const int LL = L * L;
-  uint8_t* slot = ws + (size_t)blockIdx.x * slot_bytes;
+  uint8_t* slot = ws ? ws + (size_t)blockIdx.x * slot_bytes : vsm;
   uint8_t* mcur = slot;             // [4][L][L]
   uint8_t* mnxt = mcur + 4 * LL;    // [4][L][L]
   uint8_t* sig = mnxt + 4 * LL;     // [L][L] 1 = anyon
@@ -280,6 +284,20 @@ int launch_variant(int mode, const VariantArgs& a, cudaStream_t stream) {
   }
   const size_t LL = (size_t)a.L * a.L;
   const size_t slot = ((14 * LL) + 255) & ~(size_t)255;
+  if (slot <= kVSmemSlot) {
+    // the whole state of a shot in shared memory: as many CTAs as fit
+    auto kern = mode == kOpen ? variant_kernel<kOpen> : variant_kernel<kDesync>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kVSmemSlot);
+    if (e != cudaSuccess) return cuda_fail(e, "variant smem attribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kVThreads, slot);
+    if (e != cudaSuccess) return cuda_fail(e, "variant occupancy");
+    int64_t grid = (int64_t)(per_sm > 0 ? per_sm : 1) * sms;
+    if (grid > a.shots) grid = a.shots;
+    kern<<<(unsigned)grid, kVThreads, slot, stream>>>(a, nullptr, slot);
+    return cuda_fail(cudaGetLastError(), "variant sweep launch");
+  }
   int64_t slots = (int64_t)sms * 4;
   const int64_t cap = (int64_t)((size_t(2) << 30) / slot);
   if (slots > cap) slots = cap;
