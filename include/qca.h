@@ -208,7 +208,8 @@ int qca_decode_uneven_async(qca_uneven_plan_t plan, const uint8_t* errors, int m
  * band_height: rows of one plane a warp segment sweeps (4, 8, 16 or 32; it sets
  * the threads per CTA and so the CTAs per SM); 0 = built-in heuristic.
  * sparse_divisor: steps with at most L^2 / sparse_divisor anyons write the
- * anyon terms per anyon, busier steps compute them densely; 0 = 64.
+ * anyon terms per anyon, busier steps compute them densely; 0 = the default,
+ * 64 for the one-CTA kernel (L <= 128) and 256 for the two-CTA cluster.
  * An override that does not fit a size is ignored. */
 int qca_set_tuning(int L, int band_height, int sparse_divisor);
 /* Current effective values and the resulting threads per CTA (QCA_ERR_UNSUPPORTED

@@ -799,6 +799,14 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
 int g_tune_H[QCA_MAX_L + 1];
 int g_tune_div[QCA_MAX_L + 1];
 
+// Anyon count (as a divisor of L^2) below which a step writes the anyon terms
+// per anyon: measured best 64 for the one-CTA kernel and 256 for the two-CTA
+// cluster, where the dense pass is split between the CTAs while every CTA
+// scatters every anyon.
+int sparse_divisor_for(int L, int CL) {
+  return g_tune_div[L] > 0 ? g_tune_div[L] : (CL == 2 ? 256 : 64);
+}
+
 bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, size_t& smem) {
   if (L % 4 != 0 || L < 8 || L > 256) return false;
   if (m_max < 3) return false;  // the first-step fill assumes the d <= 3 terms fit below 0xFF
@@ -840,7 +848,7 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
   if ((g.nws + threads - 1) / threads > 4) return false;  // apply_flips handles <= 4 words/thread
   g.off = 255 - m_max;
   g.cap = L * L < kListCap ? L * L : kListCap;
-  g.sparse_max = L * L / (g_tune_div[L] > 0 ? g_tune_div[L] : 64);
+  g.sparse_max = L * L / sparse_divisor_for(L, CL);
   // row pitch: L + 4 bytes (one extra bank per row); L + 8 keeps the 8-byte
   // alignment of the 64-bit accesses used with two words per lane
   g.ls = L + (KW == 2 ? 8 : 4);
@@ -975,7 +983,7 @@ int qca_get_tuning(int L, int* band_height, int* sparse_divisor, int* threads_pe
   size_t smem;
   const bool fast = make_geom(L, 255, CL, KW, g, threads, smem);
   if (band_height) *band_height = fast ? g.H : 0;
-  if (sparse_divisor) *sparse_divisor = g_tune_div[L] > 0 ? g_tune_div[L] : 64;
+  if (sparse_divisor) *sparse_divisor = sparse_divisor_for(L, fast ? CL : 1);
   if (threads_per_cta) *threads_per_cta = fast ? threads : 0;
   return fast ? QCA_OK : QCA_ERR_UNSUPPORTED;
 }
@@ -1017,7 +1025,7 @@ int qca_autotune(int L, int64_t shots, double p, uint64_t seed, int max_steps,
     FastGeom g2;
     size_t sm2;
     if (!make_geom(L, 255, CL2, KW2, g2, th2, sm2) || g2.H != H) continue;  // invalid here
-    for (int div : {128, 64, 32}) {
+    for (int div : {256, 128, 64, 32}) {
       g_tune_div[L] = div;
       // one untimed run, then the median of three timed runs
       rc = qca_decode_batch_async(N, L, shots, max_steps, 0, C, S, F, nullptr, st);
