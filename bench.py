@@ -49,8 +49,8 @@ ALU_PEAK_LANE_OPS = 152 * 64 * 2 * 2.070e9
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 4000 shots,
 # profiles/fast_kernel_L256_p005_full.md), valid only for the kernel source
 # whose SHA-256 prefix is recorded with it; reported as null otherwise.
-TRAFFIC_PER_SHOT = {"sha256_prefix": "a10f7144a4ea9b92", "L": 256, "p": 0.05,
-                    "bytes_per_shot": (525.472768e6 + 479.387392e6) / 4000}
+TRAFFIC_PER_SHOT = {"sha256_prefix": "5df71a97652cf0dd", "L": 256, "p": 0.05,
+                    "bytes_per_shot": (526.072320e6 + 479.626240e6) / 4000}
 
 
 def traffic_per_launch(L, p, shots):

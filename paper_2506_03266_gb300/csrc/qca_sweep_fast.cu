@@ -804,7 +804,8 @@ int g_tune_div[QCA_MAX_L + 1];
 // cluster, where the dense pass is split between the CTAs while every CTA
 // scatters every anyon.
 int sparse_divisor_for(int L, int CL) {
-  return g_tune_div[L] > 0 ? g_tune_div[L] : (CL == 2 ? 256 : 64);
+  if (g_tune_div[L] > 0) return g_tune_div[L];
+  return CL == 2 ? 256 : 64;
 }
 
 bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, size_t& smem) {
@@ -819,21 +820,27 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
   if (g.G > 32) return false;
   g.spw = 32 / g.G;
   // band height: 32, 16, 8 or 4 rows, dividing the CTA's rows, within the
-  // thread limit; at L <= 64 few large bands (many shots per SM), above it
-  // at least 16 warps per CTA
+  // thread limit; the one whose warp count is nearest a target (4 warps up to
+  // L = 64, L / 8 above, at most 16; measured over band heights at L = 24 to
+  // 128), the taller band on a tie
   const int max_warps = (CL == 1) ? 32 : 16;
-  int best_H = 0;
+  const int target = L <= 64 ? 4 : std::min(16, L / 8);
+  int best_H = 0, best_d = 1 << 30;
   for (int H : {4, 8, 16, 32}) {
     if (g.rows_local % H) continue;
     const int segments = 4 * (g.rows_local / H);
     const int warps = (segments + g.spw - 1) / g.spw;
     if (warps > max_warps) continue;
-    if (!best_H) best_H = H;
-    if (warps >= 16 || (L <= 64 && H >= 8)) best_H = H;
-    if (g_tune_H[L] == H) {  // a valid override wins
+    const int d = warps > target ? warps - target : target - warps;
+    if (d <= best_d) {
+      best_d = d;
       best_H = H;
-      break;
     }
+  }
+  for (int H : {4, 8, 16, 32}) {  // a valid override wins
+    if (g_tune_H[L] != H || g.rows_local % H) continue;
+    const int warps = (4 * (g.rows_local / H) + g.spw - 1) / g.spw;
+    if (warps <= max_warps) best_H = H;
   }
   if (!best_H) return false;
   g.H = best_H;
