@@ -77,6 +77,26 @@ __device__ __forceinline__ bool open_link(int L, int plane, int x, int y) {
   return plane == 0 ? x <= L - 2 : (x >= 1 && x <= L - 2 && y <= L - 2);
 }
 
+// (x, y) of site i = threadIdx.x + k blockDim.x, stepped with one carry per
+// iteration instead of a division (blockDim.x % L < L)
+struct SitePos {
+  int x, y, dx, dy, L;
+  __device__ explicit SitePos(int L_) : L(L_) {
+    x = (int)threadIdx.x % L;
+    y = (int)threadIdx.x / L;
+    dx = (int)blockDim.x % L;
+    dy = (int)blockDim.x / L;
+  }
+  __device__ void next() {
+    x += dx;
+    y += dy;
+    if (x >= L) {
+      x -= L;
+      ++y;
+    }
+  }
+};
+
 // ws == nullptr: the slot is this CTA's dynamic shared memory (small L)
 template <int MODE>
 __global__ void __launch_bounds__(kVThreads) variant_kernel(VariantArgs a, uint8_t* ws,
@@ -95,8 +115,9 @@ __global__ void __launch_bounds__(kVThreads) variant_kernel(VariantArgs a, uint8
   for (int64_t shot = blockIdx.x; shot < a.shots; shot += gridDim.x) {
     const uint8_t* N = a.in + shot * 2 * (int64_t)LL;
     int any = 0;
-    for (int i = threadIdx.x; i < LL; i += blockDim.x) {
-      const int x = i % L, y = i / L;
+    SitePos pi(L);
+    for (int i = threadIdx.x; i < LL; i += blockDim.x, pi.next()) {
+      const int x = pi.x, y = pi.y;
       int s;
       if (MODE == kOpen) {
         s = 0;
@@ -126,8 +147,9 @@ __global__ void __launch_bounds__(kVThreads) variant_kernel(VariantArgs a, uint8
       // ---- message sub-steps: v per step (OPEN), one at the firing sites (DESYNC)
       const int subs = MODE == kOpen ? a.v : 1;
       for (int k = 0; k < subs; ++k) {
-        for (int i = threadIdx.x; i < LL; i += blockDim.x) {
-          const int x = i % L, y = i / L;
+        SitePos pm(L);
+        for (int i = threadIdx.x; i < LL; i += blockDim.x, pm.next()) {
+          const int x = pm.x, y = pm.y;
           bool fire = true;
           if (MODE == kDesync) fire = splitmix64(k2 ^ (uint64_t)(2 * (int64_t)i)) < a.thr_msg;
 #pragma unroll
@@ -196,8 +218,9 @@ __global__ void __launch_bounds__(kVThreads) variant_kernel(VariantArgs a, uint8
       }
       __syncthreads();
       // ---- feedback (OR) on the existing links
-      for (int i = threadIdx.x; i < LL; i += blockDim.x) {
-        const int x = i % L, y = i / L;
+      SitePos pf(L);
+      for (int i = threadIdx.x; i < LL; i += blockDim.x, pf.next()) {
+        const int x = pf.x, y = pf.y;
         int fx, fy;
         if (MODE == kOpen) {
           fx = open_link(L, 0, x, y) ? ((dir[i] == 1) | (dir[i + 1] == 2)) : 0;
@@ -213,8 +236,9 @@ __global__ void __launch_bounds__(kVThreads) variant_kernel(VariantArgs a, uint8
       __syncthreads();
       // ---- syndrome update
       any = 0;
-      for (int i = threadIdx.x; i < LL; i += blockDim.x) {
-        const int x = i % L, y = i / L;
+      SitePos ps(L);
+      for (int i = threadIdx.x; i < LL; i += blockDim.x, ps.next()) {
+        const int x = ps.x, y = ps.y;
         int s;
         if (MODE == kOpen) {
           if (x == 0 || x == L - 1) {
