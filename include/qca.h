@@ -294,7 +294,8 @@ int qca_decode_desync_batch_async(const uint8_t* noise, int L, int64_t shots, in
  * Learned pre-decoder in front of the automaton.  The paper has no learned
  * component; this stage is an addition whose only job is to pair off nearby
  * anyons before the automaton (the paper's decoder, unchanged) finishes every
- * shot, so the automaton stays both the fallback and the judge.
+ * shot: every anyon the net leaves is decoded exactly as without it, and the
+ * shot's outcome is the automaton's.
  *
  * The net: four 3x3 convolutions with circular (periodic) padding,
  * 2 -> 32 -> 32 -> 32 -> 4 channels, ReLU between layers.  Input channel 0 is
