@@ -415,6 +415,18 @@ int qca_net_set_tensor_path(qca_net_t net, int path);
  * flag is then cleared), else QCA_OK. */
 int qca_net_status(qca_net_t net);
 
+/* Self-test of the device watchdog (no fault is involved): one thread of a
+ * one-CTA kernel waits on an mbarrier that nothing completes, with the bounded
+ * polling the tensor-core kernels use (about 2 s of SM clock), gives up and
+ * raises the CTA's stop flag; a second warp waiting on another such barrier
+ * must then give up at once.  Outputs (host pointers, each may be NULL): 1 if
+ * the first / second wait gave up, the first wait's duration and the second
+ * waiter's return after the first gave up, in seconds at the device's nominal
+ * clock.  Synchronises the device; QCA_OK unless a CUDA call fails.  The
+ * context stays usable afterwards. */
+int qca_watchdog_selftest(int* first_gave_up, int* second_gave_up, double* first_wait_s,
+                          double* second_lag_s);
+
 /* Net + automaton: pre-decode, run qca_decode_batch_async on the residual
  * N xor C0 (arguments as there), then out_correction = C0 xor C_automaton.
  * out_steps counts the automaton's steps; out_logical_fail is the failure

@@ -103,6 +103,7 @@ def lib():
             "qca_net_set_precision": ([vp, i32], i32),
             "qca_net_set_tensor_path": ([vp, i32], i32),
             "qca_net_status": ([vp], i32),
+            "qca_watchdog_selftest": ([vp, vp, vp, vp], i32),
             "qca_net_logits_async": ([vp, vp, i32, i64, vp, vp], i32),
             "qca_net_predecode_async": ([vp, vp, i32, i64, vp, vp, vp], i32),
             "qca_net_decode_batch_async": ([vp, vp, i32, i64, i32, u64, vp, vp, vp, cfgp, vp,
@@ -609,6 +610,17 @@ class Net:
             ctypes.c_void_p(steps.data_ptr()), ctypes.c_void_p(fail.data_ptr()),
             ctypes.byref(cfg), ctypes.c_void_p(scratch.data_ptr()), _stream(torch, stream)))
         return C, steps, fail
+
+
+def watchdog_selftest():
+    """(first wait gave up, second wait gave up, first wait in s, second
+    waiter's lag in s) of the device watchdog self-test: a bounded wait on a
+    barrier nothing completes gives up and stops a second waiter."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    t1, t2 = ctypes.c_double(), ctypes.c_double()
+    _check(lib().qca_watchdog_selftest(ctypes.byref(a), ctypes.byref(b), ctypes.byref(t1),
+                                       ctypes.byref(t2)))
+    return bool(a.value), bool(b.value), t1.value, t2.value
 
 
 def free_workspace():

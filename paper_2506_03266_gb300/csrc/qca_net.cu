@@ -1063,6 +1063,46 @@ constexpr size_t ws_smem_bytes() {
   return (size_t)kWsR * 4 * kTcRow * 16 + 9 * 4 * NOUT * 16 + (2 * kWsR + 5) * 8 + 16 + 4 * NOUT;
 }
 
+// Self-test of the bounded waits the tensor-core kernels use: thread 0 waits
+// (ws_wait) on an mbarrier that nothing completes, gives up after its bound
+// and raises the stop flag; warp 1 waits on another such barrier and must give
+// up as soon as the flag is raised.  out[0] / out[1]: 1 if the first / second
+// wait gave up; out[2]: the first wait in units of 2^20 SM cycles; out[3]: the
+// second waiter's return after the first gave up, in units of 2^10 cycles.
+__global__ void watchdog_selftest_kernel(unsigned int* out) {
+  __shared__ uint64_t bars[2];
+  __shared__ int stop_s;
+  __shared__ long long t_stop;
+  volatile int* stop = &stop_s;
+  if (threadIdx.x == 0) {
+    ws_bar_init(&bars[0], 1);
+    ws_bar_init(&bars[1], 1);
+    *stop = 0;
+    t_stop = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const long long t0 = clock64();
+    const bool ok = ws_wait(&bars[0], 0, stop);  // raises *stop when it gives up
+    const long long t1 = clock64();
+    t_stop = t1;
+    out[0] = ok ? 0u : 1u;
+    out[2] = (unsigned int)((t1 - t0) >> 20);
+  } else if (threadIdx.x == 32) {
+    out[1] = ws_wait(&bars[1], 0, stop) ? 0u : 1u;
+    const long long t1 = clock64();
+    // t_stop is written just after the flag; wait (bounded) until it is visible
+    volatile long long* ts = &t_stop;
+    for (int k = 0; k < (1 << 20) && *ts == 0; ++k) {
+    }
+    const long long d = t1 - *ts;
+    out[3] = (unsigned int)((d > 0 ? d : 0) >> 10);
+  }
+  // the barriers leave the CTA with their phases incomplete; nothing else
+  // refers to them
+}
+
 // ------------------------------------------------------ inference (FP8) ----
 //
 // FP8 (E4M3) form of layers 2-4: weights quantised per output channel,
@@ -2125,6 +2165,31 @@ int qca_net_status(qca_net_t n) {
     set_error("qca_net_status: a tensor-core wait timed out; the outputs since the last check are unreliable");
     return QCA_ERR_WATCHDOG;
   }
+  return QCA_OK;
+}
+
+int qca_watchdog_selftest(int* first_gave_up, int* second_gave_up, double* first_wait_s,
+                          double* second_lag_s) {
+  unsigned int* d = nullptr;
+  unsigned int h[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaMalloc(&d, sizeof(h));
+  if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(h));
+  if (e == cudaSuccess) {
+    watchdog_selftest_kernel<<<1, 64>>>(d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "qca_watchdog_selftest");
+  int clk_khz = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+  const double hz = clk_khz > 0 ? clk_khz * 1e3 : 0.0;
+  if (first_gave_up) *first_gave_up = (int)h[0];
+  if (second_gave_up) *second_gave_up = (int)h[1];
+  if (first_wait_s) *first_wait_s = hz > 0 ? (double)h[2] * 1048576.0 / hz : -1.0;
+  if (second_lag_s) *second_lag_s = hz > 0 ? (double)h[3] * 1024.0 / hz : -1.0;
   return QCA_OK;
 }
 

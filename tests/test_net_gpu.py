@@ -378,6 +378,20 @@ def test_training_repeats_bit_for_bit():
         b.close()
 
 
+def test_watchdog_gives_up_and_stops_the_other_waiters():
+    # a bounded wait on a barrier that nothing completes gives up after its
+    # bound (about 2 s of SM clock) and raises the stop flag, and a second
+    # waiter leaves at once; the context stays usable (no fault is involved)
+    first, second, t_first, lag = qca.watchdog_selftest()
+    assert first and second
+    assert 0.5 < t_first < 10.0, t_first
+    assert 0.0 <= lag < 0.01, lag
+    N = qca.sample_errors(16, 8, 0.05, seed=1)
+    C, steps, fail = qca.decode_batch(N, max_steps=4096)
+    torch.cuda.synchronize()
+    assert int((fail == 3).sum()) == 0
+
+
 def test_gradients_match_fp64_reference():
     # one training step's gradient (bf16 operands, fp32 accumulation) against
     # the FP64 reference of the same loss: the bf16 rounding of weights and
