@@ -401,13 +401,16 @@ int qca_net_set_fp8_scales(qca_net_t net, const float* scales);
 int qca_net_get_fp8_scales(qca_net_t net, float* scales);
 int qca_net_set_precision(qca_net_t net, int precision);
 
-/* Tensor path of the bf16 form's layers 2-4 where L is a multiple of 128
- * (mma.sync elsewhere): 2 (default) = tcgen05 MMAs with the accumulator in
- * tensor memory, warp-specialised (producer warps stage rows into a ring,
- * one thread issues the MMAs, epilogue warps drain two accumulators, all
- * handed over through mbarriers); 1 = the same MMAs with the roles in
- * lock-step (block barriers per row); 0 = mma.sync everywhere.  All three
- * give the same bits.  QCA_ERR_ARG for any other value. */
+/* Tensor path of layers 2-4 where L is a multiple of 128 (mma.sync elsewhere):
+ * 2 (default) = tcgen05 MMAs with the accumulator in tensor memory,
+ * warp-specialised (producer warps stage rows into a ring, one thread issues
+ * the MMAs, epilogue warps drain two accumulators, all handed over through
+ * mbarriers), kind::f16 for the bf16 form and kind::f8f6f4 for the FP8 form;
+ * 1 = the bf16 form's MMAs with the roles in lock-step (block barriers per
+ * row), the FP8 form on mma.sync; 0 = mma.sync everywhere.  The bf16 form
+ * gives the same bits on every path; the FP8 form's tcgen05 and mma.sync
+ * instructions add the 32 products of a K step in different orders (last-bit
+ * fp32 differences).  QCA_ERR_ARG for any other value. */
 int qca_net_set_tensor_path(qca_net_t net, int path);
 
 /* Synchronise and report the device watchdog of the tensor-core kernels:

@@ -540,9 +540,10 @@ class Net:
         _check(lib().qca_net_set_precision(self.handle, {"bf16": 0, "fp8": 1}[precision]))
 
     def set_tensor_path(self, path: str):
-        """Layers 2-4 of the bf16 form where L % 128 == 0: "tcgen05_ws"
-        (default, warp-specialised), "tcgen05" (row-synchronous) or "mma"
-        (mma.sync; also the path for other L)."""
+        """Layers 2-4 where L % 128 == 0: "tcgen05_ws" (default,
+        warp-specialised; bf16 and FP8 forms), "tcgen05" (row-synchronous,
+        bf16 form; FP8 then on mma.sync) or "mma" (mma.sync; also the path for
+        other L)."""
         _check(lib().qca_net_set_tensor_path(
             self.handle, {"mma": 0, "tcgen05": 1, "tcgen05_ws": 2}[path]))
 

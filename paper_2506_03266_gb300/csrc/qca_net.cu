@@ -1063,6 +1063,316 @@ constexpr size_t ws_smem_bytes() {
   return (size_t)kWsR * 4 * kTcRow * 16 + 9 * 4 * NOUT * 16 + (2 * kWsR + 5) * 8 + 16 + 4 * NOUT;
 }
 
+// two floats -> two E4M3 bytes (lo in the low byte), saturating
+__device__ __forceinline__ uint16_t pack_e4m3x2(float lo, float hi) {
+  return (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(lo, hi), __NV_SATFINITE, __NV_E4M3);
+}
+
+// FP8 (E4M3) form of the warp-specialised convolution (tcgen05.mma
+// kind::f8f6f4).  K = 32 e4m3 values per MMA are two 16-byte planes, the same
+// byte geometry as K = 16 bf16, so the descriptors are those of the bf16 form
+// and a tap is one MMA.  Activations are planar as [shot][y][16-channel group]
+// [x][16 bytes]; the epilogue dequantises with s_in * s_co (the weight
+// scale of its output channel), adds the bias, and requantises to e4m3 with the
+// next layer's scale, as the mma.sync FP8 kernel does.
+__host__ __device__ constexpr uint32_t tc_idesc_e4m3(int N, int M) {
+  // D f32 (bits 4-5 = 1), A and B E4M3 (bits 7-9 and 10-12 = 0), K-major, N >> 3, M >> 4
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma_e4m3(uint32_t tmem, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// layer 1 of the FP8 form for every 3 x 3 anyon pattern: e4m3(relu(.) / s_out),
+// summed in the order of layer1_fp8_kernel; 32 bytes per pattern
+__global__ void layer1_lut8_kernel(const float* __restrict__ W1, const float* __restrict__ P,
+                                   float inv_s_out, uint8_t* __restrict__ lut8) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 512 * 16; i += gridDim.x * blockDim.x) {
+    const int pat = i / 16, co = 2 * (i % 16);
+    float b[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      b[k] = P[kB0 + co + k];
+      for (int tap = 0; tap < 9; ++tap) b[k] += W1[(co + k) * 18 + 9 + tap];
+      for (int tap = 0; tap < 9; ++tap)
+        if ((pat >> tap) & 1) b[k] += W1[(co + k) * 18 + tap];
+    }
+    reinterpret_cast<uint16_t*>(lut8)[i] =
+        pack_e4m3x2(fmaxf(b[0], 0.f) * inv_s_out, fmaxf(b[1], 0.f) * inv_s_out);
+  }
+}
+
+template <int NOUT, int MODE, bool FROM_SIG>
+__global__ void __launch_bounds__(kWsThreads, 2) conv_ws8_kernel(
+    const uint8_t* __restrict__ in, const uint8_t* __restrict__ Wq,
+    const float* __restrict__ wscale, const float* __restrict__ bias, float s_in,
+    float inv_s_out, int L, int64_t shots, uint8_t* __restrict__ out,
+    float* __restrict__ logits, const uint8_t* __restrict__ sig, uint8_t* __restrict__ prop,
+    unsigned int* __restrict__ err, const uint8_t* __restrict__ lut8) {
+  constexpr int CO_SRC = NOUT == 32 ? 32 : 8;
+  constexpr uint32_t kRowBytes = 2 * kTcRow * 16;  // one staged row: two 16-channel planes
+  constexpr uint32_t kA = kWsR * kRowBytes;        // the ring
+  constexpr uint32_t kB = 9 * 2 * NOUT * 16;       // weights
+  extern __shared__ __align__(128) uint8_t sm[];
+  uint8_t* sA = sm;
+  uint8_t* sB = sm + kA;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kA + kB);  // [kWsR]
+  uint64_t* empty = full + kWsR;                               // [kWsR]
+  uint64_t* acc_full = empty + kWsR;                           // [2]
+  uint64_t* acc_empty = acc_full + 2;                          // [2]
+  uint64_t* drained = acc_empty + 2;                           // [1]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drained + 1);
+  volatile int* stop = reinterpret_cast<volatile int*>(tslot + 1);
+  float* sbias = reinterpret_cast<float*>(tslot + 4);
+  float* sscale = sbias + NOUT;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // weights [tap][co][32 ci] bytes -> [tap][group][co][16 bytes]
+  for (int i = tid; i < 9 * NOUT * 2; i += kWsThreads) {
+    const int tap = i / (NOUT * 2), rem = i % (NOUT * 2), co = rem / 2, grp = rem % 2;
+    uint4 w = make_uint4(0, 0, 0, 0);
+    if (co < CO_SRC)
+      w = *reinterpret_cast<const uint4*>(Wq + ((size_t)(tap * CO_SRC + co) * 32 + grp * 16));
+    *reinterpret_cast<uint4*>(sB + ((size_t)(tap * 2 + grp) * NOUT + co) * 16) = w;
+  }
+  for (int i = tid; i < NOUT; i += kWsThreads) {
+    const bool real = MODE == kActs || i < 4;
+    sbias[i] = real ? bias[i] : 0.f;
+    sscale[i] = real ? s_in * wscale[i] : 0.f;
+  }
+  if (tid == 0) {
+    for (int k = 0; k < kWsR; ++k) {
+      ws_bar_init(&full[k], FROM_SIG ? 32 * kWsProd : 1);
+      ws_bar_init(&empty[k], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      ws_bar_init(&acc_full[k], 1);
+      ws_bar_init(&acc_empty[k], kWsEpi);
+    }
+    ws_bar_init(drained, 1);
+    *stop = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     tc_smem(tslot)),
+                 "r"(64)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_proxy_shared();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;  // two accumulators: columns 0-31 and 32-63
+  const int64_t LL = (int64_t)L * L;
+  const int xblocks = L / kTcM, strips = L / kTcStrip;
+  const int64_t units = shots * xblocks * strips;
+  auto unit_of = [&](int64_t u, int64_t& shot, int& x0, int& y0) {
+    shot = u / ((int64_t)xblocks * strips);
+    const int rem = (int)(u - shot * (int64_t)xblocks * strips);
+    x0 = (rem % xblocks) * kTcM;
+    y0 = (rem / xblocks) * kTcStrip;
+  };
+
+  if (!FROM_SIG && warp >= kWsEpi && warp < kWsMmaWarp) {
+    // ================= producer (one thread): bulk copies of planar rows
+    if (warp == kWsEpi && lane == 0) {
+      int64_t e = 0;
+      for (int64_t u = blockIdx.x; u < units && !*stop; u += gridDim.x) {
+        int64_t shot;
+        int x0, y0;
+        unit_of(u, shot, x0, y0);
+        const int xl = x0 == 0 ? L - 1 : x0 - 1, xr = x0 + kTcM == L ? 0 : x0 + kTcM;
+        int r = -1;
+        for (; r <= kTcStrip; ++r, ++e) {
+          const int slot = (int)(e % kWsR);
+          if (e >= kWsR && !ws_wait(&empty[slot], (uint32_t)((e / kWsR - 1) & 1), stop)) break;
+          int yy = y0 + r;
+          yy = yy < 0 ? yy + L : (yy >= L ? yy - L : yy);
+          uint8_t* dst = sA + (size_t)slot * kRowBytes;
+          mbar_expect_tx_ws(&full[slot], kRowBytes);
+#pragma unroll
+          for (int grp = 0; grp < 2; ++grp) {
+            const uint8_t* src = in + (((shot * L + yy) * 2 + grp) * (int64_t)L) * 16;
+            uint8_t* d = dst + (size_t)grp * kTcRow * 16;
+            bulk_g2s_ws(d + 16, src + (int64_t)x0 * 16, kTcM * 16, &full[slot]);
+            bulk_g2s_ws(d, src + (int64_t)xl * 16, 16, &full[slot]);
+            bulk_g2s_ws(d + (kTcRow - 1) * 16, src + (int64_t)xr * 16, 16, &full[slot]);
+          }
+        }
+        if (r <= kTcStrip) break;  // stopped
+      }
+      // no copy may still be landing when the CTA exits
+      for (int64_t f = e > kWsR ? e - kWsR : 0; f < e; ++f)
+        (void)tc_bar_wait(&full[f % kWsR], (uint32_t)((f / kWsR) & 1));
+    }
+    __syncwarp();
+  } else if (FROM_SIG && warp >= kWsEpi && warp < kWsMmaWarp) {
+    // ================= producers: layer 1 gathered from the e4m3 table
+    const int pt = tid - 32 * kWsEpi;
+    int64_t e = 0;
+    for (int64_t u = blockIdx.x; u < units && !*stop; u += gridDim.x) {
+      int64_t shot;
+      int x0, y0;
+      unit_of(u, shot, x0, y0);
+      for (int r = -1; r <= kTcStrip && !*stop; ++r, ++e) {
+        const int slot = (int)(e % kWsR);
+        if (e >= kWsR && !ws_wait(&empty[slot], (uint32_t)((e / kWsR - 1) & 1), stop)) break;
+        int yy = y0 + r;
+        yy = yy < 0 ? yy + L : (yy >= L ? yy - L : yy);
+        uint8_t* dst = sA + (size_t)slot * kRowBytes;
+        const uint8_t* g = sig + shot * LL;
+        const int ym = yy == 0 ? L - 1 : yy - 1, yp = yy == L - 1 ? 0 : yy + 1;
+        for (int j = pt; j < kTcRow; j += 32 * kWsProd) {
+          int xx = x0 + j - 1;
+          xx = xx < 0 ? xx + L : (xx >= L ? xx - L : xx);
+          const int xm = xx == 0 ? L - 1 : xx - 1, xp = xx == L - 1 ? 0 : xx + 1;
+          const int rows[3] = {ym, yy, yp}, cols[3] = {xm, xx, xp};
+          uint32_t idx = 0;
+#pragma unroll
+          for (int tap = 0; tap < 9; ++tap)
+            idx |= (g[(int64_t)rows[tap / 3] * L + cols[tap % 3]] ? 1u : 0u) << tap;
+          const uint8_t* src = lut8 + (size_t)idx * 32;
+          tc_cp16_ca(dst + (size_t)j * 16, src);
+          tc_cp16_ca(dst + ((size_t)kTcRow + j) * 16, src + 16);
+        }
+        tc_cp_commit();
+        if (e >= kWsLag) {
+          asm volatile("cp.async.wait_group %0;" ::"n"(kWsLag) : "memory");
+          tc_fence_proxy_shared();
+          ws_arrive(&full[(e - kWsLag) % kWsR]);
+        }
+      }
+    }
+    tc_cp_wait_all();
+    tc_fence_proxy_shared();
+    for (int64_t f = e > kWsLag ? e - kWsLag : 0; f < e; ++f) ws_arrive(&full[f % kWsR]);
+  } else if (warp == kWsMmaWarp) {
+    // ================= MMA issue (one thread): one K = 32 MMA per tap
+    if (lane == 0) {
+      const uint32_t idesc = tc_idesc_e4m3(NOUT, kTcM);
+      const uint32_t a0 = tc_smem(sA), b0 = tc_smem(sB);
+      int64_t e = 0, T = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        for (int j = 0; j < kTcStrip && ok; ++j, ++T) {
+          const int64_t eb = e + j;
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy)
+            ok = ok && ws_wait(&full[(eb + dy) % kWsR], (uint32_t)(((eb + dy) / kWsR) & 1), stop);
+          const int acc = (int)(T & 1);
+          if (ok && T >= 2) ok = ws_wait(&acc_empty[acc], (uint32_t)(((T >> 1) - 1) & 1), stop);
+          if (!ok) break;
+          tc_fence_after();
+#pragma unroll
+          for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap % 3 - 1;
+            const uint32_t slot = (uint32_t)((eb + dy) % kWsR);
+            const uint32_t aaddr = a0 + slot * kRowBytes + (uint32_t)(1 + dx) * 16;
+            const uint32_t baddr = b0 + (uint32_t)(tap * 2 * NOUT) * 16;
+            tc_mma_e4m3(tmem + (uint32_t)(acc * 32), tc_desc(aaddr, kTcRow * 16, 128),
+                        tc_desc(baddr, NOUT * 16, 128), idesc, tap != 0);
+          }
+          tc_commit(&acc_full[acc]);
+          tc_commit(&empty[eb % kWsR]);
+          if (j == kTcStrip - 1) {
+            tc_commit(&empty[(eb + 1) % kWsR]);
+            tc_commit(&empty[(eb + 2) % kWsR]);
+          }
+        }
+        e += kTcStrip + 2;
+      }
+      tc_commit(drained);
+      if (!tc_bar_wait(drained, 0)) *stop = 1;
+    }
+    __syncwarp();
+  } else {
+    // ================= epilogue: warp w reads TMEM lanes 32 (w % 4) .., columns
+    // 16 (w / 4) .. + 15 (output channels of one 16-channel group)
+    const int half = warp >> 2;
+    int64_t T = 0;
+    for (int64_t u = blockIdx.x; u < units && !*stop; u += gridDim.x) {
+      int64_t shot;
+      int x0, y0;
+      unit_of(u, shot, x0, y0);
+      bool ok = true;
+      for (int j = 0; j < kTcStrip; ++j, ++T) {
+        const int acc = (int)(T & 1);
+        ok = ws_wait(&acc_full[acc], (uint32_t)((T >> 1) & 1), stop);
+        if (!__all_sync(0xffffffffu, ok)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        float v[16];
+        tc_ld16(tmem + (uint32_t)(acc * 32 + 16 * half) + ((uint32_t)(32 * (warp & 3)) << 16), v);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ws_arrive(&acc_empty[acc]);
+        const int y = y0 + j, x = x0 + 32 * (warp & 3) + lane;
+        const int64_t site = shot * LL + (int64_t)y * L + x;
+        if (MODE == kActs) {
+          uint32_t w[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int co = 16 * half + 4 * c;
+            const uint32_t lo =
+                pack_e4m3x2(fmaxf(v[4 * c] * sscale[co] + sbias[co], 0.f) * inv_s_out,
+                            fmaxf(v[4 * c + 1] * sscale[co + 1] + sbias[co + 1], 0.f) * inv_s_out);
+            const uint32_t hi =
+                pack_e4m3x2(fmaxf(v[4 * c + 2] * sscale[co + 2] + sbias[co + 2], 0.f) * inv_s_out,
+                            fmaxf(v[4 * c + 3] * sscale[co + 3] + sbias[co + 3], 0.f) * inv_s_out);
+            w[c] = lo | (hi << 16);
+          }
+          *reinterpret_cast<uint4*>(out + (((shot * L + y) * 2 + half) * (int64_t)L + x) * 16) =
+              make_uint4(w[0], w[1], w[2], w[3]);
+        } else if (half == 0) {
+          float z[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) z[k] = v[k] * sscale[k] + sbias[k];
+          if (MODE == kLogits) {
+            float* lb = logits + shot * 4 * LL + (int64_t)y * L + x;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) lb[(int64_t)k * LL] = z[k];
+          } else {
+            float best = z[0];
+            int bk = 0;
+#pragma unroll
+            for (int q = 1; q < 4; ++q)
+              if (z[q] > best) {
+                best = z[q];
+                bk = q;
+              }
+            prop[site] = (sig[site] && best > 0.f) ? (uint8_t)bk : (uint8_t)4;
+          }
+        }
+      }
+      if (!ok) break;
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && *stop) atomicOr(err, 1u);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64)
+                 : "memory");
+}
+
+template <int NOUT>
+constexpr size_t ws8_smem_bytes() {
+  return (size_t)kWsR * 2 * kTcRow * 16 + 9 * 2 * NOUT * 16 + (2 * kWsR + 5) * 8 + 16 +
+         8 * NOUT;
+}
+
 // Self-test of the bounded waits the tensor-core kernels use: thread 0 waits
 // (ws_wait) on an mbarrier that nothing completes, gives up after its bound
 // and raises the stop flag; warp 1 waits on another such barrier and must give
@@ -1110,10 +1420,6 @@ __global__ void watchdog_selftest_kernel(unsigned int* out) {
 // layer, e4m3(x / s_in), with calibrated scales; products accumulate in fp32 on
 // mma.sync m16n8k32 (e4m3 x e4m3), and the epilogue dequantises with
 // s_in * s_co.  Layer 1 stays on the CUDA cores as in the bf16 form.
-
-__device__ __forceinline__ uint16_t pack_e4m3x2(float lo, float hi) {
-  return (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(lo, hi), __NV_SATFINITE, __NV_E4M3);
-}
 
 // One CTA per (layer, output channel): 32 + 32 + 8 CTAs (layer 4 padded to 8
 // channels with zeros).  Wq layout per layer: [tap][co][ci] bytes.
@@ -1602,6 +1908,7 @@ struct qca_net_s {
                                  // 2 tcgen05 warp-specialised (tcgen05 where L % 128 == 0)
   unsigned int* err = nullptr;   // device word: a tensor-core wait timed out
   __nv_bfloat16* lut = nullptr;  // layer-1 outputs per 3 x 3 anyon pattern [512][32]
+  uint8_t* lut8 = nullptr;        // the same in e4m3 at the layer-1 activation scale
   // inference workspace
   uint8_t* ws = nullptr;
   size_t ws_bytes = 0;
@@ -1641,6 +1948,7 @@ int qca_net_create(uint64_t seed, qca_net_t* out) {
   if (e == cudaSuccess) e = cudaMalloc(&n->wscale, sizeof(float) * 96);
   if (e == cudaSuccess) e = cudaMalloc(&n->err, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&n->lut, sizeof(__nv_bfloat16) * 512 * 32);
+  if (e == cudaSuccess) e = cudaMalloc(&n->lut8, 512 * 32);
   if (e == cudaSuccess) e = cudaMemset(n->err, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemcpy(n->params, h.data(), sizeof(float) * kParams, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(n->m1, 0, sizeof(float) * kParams);
@@ -1665,6 +1973,7 @@ int qca_net_destroy(qca_net_t n) {
   cudaFree(n->wscale);
   cudaFree(n->err);
   cudaFree(n->lut);
+  cudaFree(n->lut8);
   cudaFree(n->ws);
   delete n;
   return QCA_OK;
@@ -1971,6 +2280,48 @@ int net_run(qca_net_s* n, const uint8_t* noise, int L, int64_t shots, float* log
     syndrome_kernel<<<grid_for(S, 256), 256, 0, st>>>(Nc, L, m, sig);
     const int64_t tiles = (S + 15) / 16;
     const int gm = grid_for(tiles * 32, 128);
+    if (n->precision == 1 && n->use_tc == 2 && L % kTcM == 0 && L % kTcStrip == 0) {
+      // FP8 form on tcgen05 (kind::f8f6f4), warp-specialised; planar e4m3
+      // activations, 32 bytes per site, in the bf16 buffers
+      uint8_t* a8A = reinterpret_cast<uint8_t*>(actA);
+      uint8_t* a8B = a8A + S * 32;
+      const float* sa = n->act_scale;
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const int64_t units = S / ((int64_t)kTcM * kTcStrip);
+      const int gt = (int)(units < (int64_t)sms * 2 ? units : (int64_t)sms * 2);
+      if (c0s == 0) layer1_lut8_kernel<<<32, 256, 0, st>>>(n->w1, n->params, 1.f / sa[0], n->lut8);
+      cudaFuncSetAttribute(conv_ws8_kernel<32, kActs, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws8_smem_bytes<32>());
+      cudaFuncSetAttribute(conv_ws8_kernel<32, kActs, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws8_smem_bytes<32>());
+      cudaFuncSetAttribute(conv_ws8_kernel<16, kLogits, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws8_smem_bytes<16>());
+      cudaFuncSetAttribute(conv_ws8_kernel<16, kProposals, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws8_smem_bytes<16>());
+      // layers 1 + 2 (layer 1 looked up while staging), 3, 4
+      conv_ws8_kernel<32, kActs, true><<<gt, kWsThreads, ws8_smem_bytes<32>(), st>>>(
+          nullptr, n->wq, n->wscale, n->params + kB1, sa[0], 1.f / sa[1], L, m, a8B, nullptr, sig,
+          nullptr, n->err, n->lut8);
+      conv_ws8_kernel<32, kActs, false><<<gt, kWsThreads, ws8_smem_bytes<32>(), st>>>(
+          a8B, n->wq + 9 * 32 * 32, n->wscale + 32, n->params + kB2, sa[1], 1.f / sa[2], L, m,
+          a8A, nullptr, nullptr, nullptr, n->err, nullptr);
+      if (logits) {
+        conv_ws8_kernel<16, kLogits, false><<<gt, kWsThreads, ws8_smem_bytes<16>(), st>>>(
+            a8A, n->wq + 2 * 9 * 32 * 32, n->wscale + 64, n->params + kB3, sa[2], 0.f, L, m,
+            nullptr, logits + c0s * 4 * LL, nullptr, nullptr, n->err, nullptr);
+      } else {
+        conv_ws8_kernel<16, kProposals, false><<<gt, kWsThreads, ws8_smem_bytes<16>(), st>>>(
+            a8A, n->wq + 2 * 9 * 32 * 32, n->wscale + 64, n->params + kB3, sa[2], 0.f, L, m,
+            nullptr, nullptr, sig, prop, n->err, nullptr);
+        pairing_kernel<<<grid_for(S, 256), 256, 0, st>>>(Nc, prop, L, m, resid + c0s * 2 * LL,
+                                                         c0 ? c0 + c0s * 2 * LL : nullptr);
+      }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e, "net fp8 tcgen05 inference kernels");
+      continue;
+    }
     if (n->precision == 1) {
       // FP8 form: e4m3 activations, 32 bytes per site, in the bf16 buffers
       uint8_t* a8A = reinterpret_cast<uint8_t*>(actA);

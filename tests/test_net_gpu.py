@@ -274,6 +274,50 @@ def test_fp8_pairing_bit_exact(trained_fp8):
     np.testing.assert_array_equal(R, N ^ C0)
 
 
+def test_fp8_tcgen05_matches_mma_path_and_fp64(trained_fp8):
+    # L % 128 == 0: the FP8 layers run as tcgen05 kind::f8f6f4 MMAs (one K = 32
+    # MMA per tap); against the mma.sync m16n8k32 path and the FP64 reference.
+    # The two instructions add the 32 products of a K step in different orders,
+    # so fp32 results differ in their last bits (measured: 4 % of the logits,
+    # by at most 1.5e-6); where that moves an intermediate activation across an
+    # E4M3 rounding boundary (rare), a logit moves by up to |W| times one step.
+    net, scales = trained_fp8
+    L, shots = 128, 2
+    N = oracle.sample_errors(L, shots, 0.05, seed=61)
+    Nd = dev(N)
+    net.set_tensor_path("tcgen05_ws")
+    z_tc = net.logits(Nd).cpu().numpy()
+    net.status()
+    net.set_tensor_path("mma")
+    z_ms = net.logits(Nd).cpu().numpy()
+    net.set_tensor_path("tcgen05_ws")
+    dm = np.abs(z_tc - z_ms).ravel()
+    assert np.mean(dm <= 1e-5) >= 0.999 and dm.max() <= 0.25, (np.mean(dm <= 1e-5), dm.max())
+    params = net.get_params()
+    A = anyon_maps(N)
+    d = np.concatenate([np.abs(z_tc[s] - onet.forward_fp8(A[s], params, scales)).ravel()
+                        for s in range(shots)])
+    assert np.mean(d <= 1e-2) >= 0.999 and d.max() <= 0.25, (np.mean(d <= 1e-2), d.max())
+
+
+def test_fp8_tcgen05_pairing_bit_exact(trained_fp8):
+    net, _ = trained_fp8
+    net.set_tensor_path("tcgen05_ws")
+    L, shots = 256, 2
+    N = oracle.sample_errors(L, shots, 0.05, seed=62)
+    Nd = dev(N)
+    z = net.logits(Nd).cpu().numpy()
+    R, C0 = net.predecode(Nd)
+    torch.cuda.synchronize()
+    net.status()
+    R, C0 = R.cpu().numpy(), C0.cpu().numpy()
+    A = anyon_maps(N)
+    for s in range(shots):
+        want = onet.pairing_links(A[s], onet.proposals(A[s], z[s]))
+        np.testing.assert_array_equal(C0[s], want, err_msg=f"shot {s}")
+    np.testing.assert_array_equal(R, N ^ C0)
+
+
 def test_fp8_net_plus_automaton_plog_within_2sigma(trained_fp8):
     net, _ = trained_fp8
     L, shots = 32, 40000
