@@ -1417,9 +1417,11 @@ __global__ void watchdog_selftest_kernel(unsigned int* out) {
 //
 // FP8 (E4M3) form of layers 2-4: weights quantised per output channel,
 // e4m3(W / s_co) with s_co = amax_co / 448; each layer's input quantised per
-// layer, e4m3(x / s_in), with calibrated scales; products accumulate in fp32 on
-// mma.sync m16n8k32 (e4m3 x e4m3), and the epilogue dequantises with
-// s_in * s_co.  Layer 1 stays on the CUDA cores as in the bf16 form.
+// layer, e4m3(x / s_in), with calibrated scales; products accumulate in fp32,
+// and the epilogue dequantises with s_in * s_co.  This section holds the
+// mma.sync m16n8k32 (e4m3 x e4m3) kernels used where L is not a multiple of
+// 128, with layer 1 on the CUDA cores; conv_ws8_kernel above is the tcgen05
+// form for the other sizes.
 
 // One CTA per (layer, output channel): 32 + 32 + 8 CTAs (layer 4 padded to 8
 // channels with zeros).  Wq layout per layer: [tap][co][ci] bytes.
