@@ -1070,6 +1070,30 @@ def main():
                             "seconds": train_s, "final_loss": float(np.mean(losses[-50:]))},
                   "note": "bf16 pre-decoder (tensor cores) + the exact automaton on the residual; "
                           "timed after the plain steps, outside the timed region"}
+        # the same net in its FP8 (E4M3) form: activation scales calibrated on 16
+        # other shots of the workload (untimed), then one warm and one timed decode
+        cal = qca.sample_errors(L, 16, args.p, seed=2)
+        scales = net.calibrate_fp8(cal)
+        net.set_precision("fp8")
+        net.decode_batch(N, MAX_STEPS, out=nout, scratch=scratch)
+        barrier()
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_ev.record(stream)
+        net.decode_batch(N, MAX_STEPS, out=nout, scratch=scratch)
+        b_ev.record(stream)
+        barrier()
+        net8_ms = reduce_time_max(a_ev.elapsed_time(b_ev), dist, "cuda")
+        net.status()
+        f8 = nout[2].cpu().numpy()
+        p8 = float((f8 > 0).mean())
+        sig8 = float(np.sqrt((p8 * (1 - p8) + pp * (1 - pp)) / max(shots, 1)))
+        net_ca["fp8"] = {"shot_decodes_per_s": world * shots / (net8_ms / 1e3),
+                         "ms_per_step": net8_ms, "p_log": p8,
+                         "same_p_log_within_2sigma": bool(abs(p8 - pp) <= 2 * sig8),
+                         "mean_steps": float(nout[1].float().mean()),
+                         "activation_scales": [float(x) for x in scales],
+                         "note": "FP8 (E4M3) form of the same net, tcgen05 kind::f8f6f4"}
+        net.set_precision("bf16")
         net.close()
         del scratch, nout
 
