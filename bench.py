@@ -45,6 +45,16 @@ UNIT = "shot-decodes/s"
 ALU_OPS_PER_SITE_UPDATE = 16
 ALU_PEAK_LANE_OPS = 152 * 64 * 2 * 2.070e9
 
+# Shared-memory roofline of the same sweep (the second fraction): with the
+# width-7 window in registers, a step reads and writes each of a site's four
+# field bytes once, 8 B per site-update, against 128 B/clk/SM.
+SMEM_BYTES_PER_SITE_UPDATE = 8
+SMEM_PEAK = 152 * 128 * 2.070e9
+
+# A message grows by at most v = 3 per step, so the m_max = 255 cap can only act
+# on shots that run longer than this many steps.
+CAP_REACH_STEPS = (255 + 2) // 3
+
 # DRAM traffic of the dominant kernel per decoded shot at L = 256, p = 0.05
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 4000 shots,
 # profiles/fast_kernel_L256_p005_full.md), valid only for the kernel source
@@ -201,6 +211,7 @@ def run_reference(args, rank):
         "data": "synthetic", "site_updates_per_s": statistics.mean(sites),
         "config": workload_config(args),
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "per_core": val / cores,
                          "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -950,6 +961,7 @@ def main():
         cores = os.cpu_count() or 1
         r = cpu_oracle_rate(args.L, args.p, 0, 15.0, cores)
         cpu = {"value": r["shot_rate"], "unit": UNIT, "cores": cores, "kind": "oracle",
+               "per_core": r["shot_rate"] / cores,
                "sample": (f"{r['shots']} consecutive shots (from shot 0) of the same workload "
                           f"decoded by the CPU oracle in {r['elapsed']:.1f} s on {cores} "
                           f"processes; site-updates/s {r['site_update_rate']:.3e}")}
@@ -1114,11 +1126,18 @@ def main():
                     "budget_exhausted": int((fail_h == 2).sum()),
                     "mean_steps": float(steps_h.float().mean()),
                     "p99_steps": float(torch.quantile(steps_h.float(), 0.99)),
-                    "max_steps_seen": int(steps_h.max())},
+                    "max_steps_seen": int(steps_h.max()),
+                    "shots_beyond_cap_reach": int((steps_h > CAP_REACH_STEPS).sum())},
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": ALU_PEAK_LANE_OPS / 1e9,
                      "unit": "Glane-op/s", "frac": achieved / ALU_PEAK_LANE_OPS,
                      "traffic": traffic_per_launch(L, args.p, shots),
                      "kernel_ms": statistics.mean(kernel_ms)},
+        "roofline_smem": {"bound": "smem",
+                          "achieved": SMEM_BYTES_PER_SITE_UPDATE * site_updates / kernel_s / 1e9,
+                          "peak": SMEM_PEAK / 1e9, "unit": "GB/s",
+                          "frac": SMEM_BYTES_PER_SITE_UPDATE * site_updates / kernel_s / SMEM_PEAK,
+                          "note": "second fraction of the same kernel: 8 B of shared memory "
+                                  "per site-update; the ALU fraction is the higher, binding one"},
         "clocks": clk,
         "gpu_launches": launches,
         "e2e": e2e,
