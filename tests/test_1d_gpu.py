@@ -74,3 +74,23 @@ def test_large_ring_and_full_batch_properties():
         Co, so, fo, mo = oracle.decode_shot_1d(Nh[i])
         assert (int(s[i]), int(f[i]), int(m[i])) == (so, fo, mo)
         np.testing.assert_array_equal(C[i].cpu().numpy(), Co)
+
+
+def fractal_noise(n, k, m):
+    # the gerrymandering pattern of Sec. 5.3: link i of the ring of n^m links
+    # is flipped iff every base-n digit of i is below k
+    x = np.arange(n ** m)
+    keep = np.ones(n ** m, bool)
+    for _ in range(m):
+        keep &= (x % n) < k
+        x //= n
+    return keep.astype(np.uint8)
+
+
+@pytest.mark.parametrize("n,k,m,v", [(6, 5, 3, 3), (5, 4, 4, 4), (5, 4, 4, 3), (6, 5, 4, 3)])
+def test_gerrymander_patterns_bit_exact(n, k, m, v):
+    # structured inputs from the paper: driven to the flipped logical state
+    # (6, 5, 3 at v = 3; 5, 4, 4 at v = 4), decoded correctly (5, 4, 4 at
+    # v = 3), and a pair stranded beyond the 8-bit messages' reach (6, 5, 4)
+    N = fractal_noise(n, k, m)[None, :]
+    check(N, max_steps=2000, v=v, label=f"fractal n={n} m={m} v={v}")

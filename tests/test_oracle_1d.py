@@ -174,3 +174,60 @@ def test_sampler_rate_and_counter_structure():
     assert abs(N.mean() - 0.2) < 0.01
     sub = oracle.sample_errors_1d(64, 10, 0.2, seed=5, shot0=37)
     np.testing.assert_array_equal(sub, N[37:47])
+
+
+# ---------------------------------------------------------- gerrymandering
+
+def fractal_noise(n, k, m):
+    """The substitution S_{n,k}(X) = X^{(x) k} (x) 1^{(x) (n-k)} iterated m times
+    on one X (the gerrymandering construction of Sec. 5.3): link i of the ring
+    of n^m links is flipped iff every base-n digit of i is below k (k^m flips)."""
+    x = np.arange(n ** m)
+    keep = np.ones(n ** m, bool)
+    for _ in range(m):
+        keep &= (x % n) < k
+        x //= n
+    return keep.astype(np.uint8)
+
+
+UNCAPPED = 1 << 30  # the numerics of Sec. 7 set no cap on the messages
+
+
+def test_gerrymander_flips_the_logical_state_in_about_035_L():
+    # Sec. 5.3: with n = 6 (k = 5) and v = 3 the decoder drives the fractal
+    # pattern to the flipped logical state, although from m = 4 on the pattern
+    # flips a minority of the links (5^m < 6^m / 2): a logical failure by the
+    # majority criterion too; its decoding time approaches 0.35 L as L grows
+    ratios = []
+    for m in (2, 3, 4, 5):
+        N = fractal_noise(6, 5, m)
+        L = N.size
+        C, steps, flag, maj = oracle.decode_shot_1d(N, v=3, m_max=UNCAPPED, max_steps=200000)
+        R = N ^ C
+        assert R.min() == R.max() == 1 and flag == 1, (m, steps, flag)
+        assert maj == (1 if 2 * int(N.sum()) < L else 0), (m, maj)
+        ratios.append(steps / L)
+    assert all(a < b for a, b in zip(ratios, ratios[1:])), ratios
+    assert 0.33 <= ratios[-1] <= 0.36, ratios
+
+
+def test_gerrymander_with_n5_needs_v5():
+    # Sec. 5.3: for n = 5 the pattern is driven to the flipped state only if
+    # v >= 5 (at m = 6, L = 15625; smaller m still flip at v = 4)
+    N = fractal_noise(5, 4, 6)
+    outcomes = {v: oracle.decode_shot_1d(N, v=v, m_max=UNCAPPED, max_steps=200000)[2]
+                for v in (3, 4, 5)}
+    assert outcomes == {3: 0, 4: 0, 5: 1}, outcomes
+
+
+def test_gerrymander_under_the_message_cap_strands_a_pair():
+    # with 8-bit messages (m_max = 255) the m = 4 pattern leaves one pair 440
+    # links apart, beyond any message's reach: it never moves again (R5, R10)
+    N = fractal_noise(6, 5, 4)
+    C, steps, flag, _ = oracle.decode_shot_1d(N, v=3, m_max=255, max_steps=2000)
+    assert (steps, flag) == (2000, 2)
+    R = N ^ C
+    anyons = np.nonzero(R ^ np.roll(R, 1))[0]
+    assert anyons.size == 2
+    gap = int(anyons[1] - anyons[0])
+    assert min(gap, N.size - gap) > 255
