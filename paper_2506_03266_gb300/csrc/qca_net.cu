@@ -731,7 +731,7 @@ constexpr size_t tc_smem_bytes() {
 // contiguous 2 KB runs (plus one halo site at either end) and the epilogue's
 // stores are contiguous across a warp.
 //   * producers stage the rows of the CTA's work units, in order, into a ring
-//     of kWsR row buffers.  From planar activations one thread issues bulk
+//     of row buffers (WsShape).  From planar activations one thread issues bulk
 //     copies (cp.async.bulk, completion by transaction count on full[slot]);
 //     for layer 2 the kWsProd producer warps gather layer 1 from the table
 //     with cp.async, each thread publishing a row kWsLag rows after issuing
@@ -746,13 +746,22 @@ constexpr size_t tc_smem_bytes() {
 //     or proposals.
 // Every wait is bounded; a timeout sets err and a stop flag that every role
 // polls, and the CTA drains its MMAs before freeing the TMEM.
-constexpr int kWsR = 8;          // ring of staged rows
-constexpr int kWsLag = 4;        // rows a producer thread keeps in flight (<= kWsR - 3)
+// Ring of staged rows and resident CTAs per SM, per form: the layer that
+// gathers layer 1 from the table (FROM_SIG) keeps more of the SM's L1 for the
+// table with two CTAs and a ring of 8; the bulk-copied layers run three CTAs
+// with a ring of 6 (registers, shared and tensor memory all fit)
+template <bool FROM_SIG>
+struct WsShape {
+  static constexpr int R = FROM_SIG ? 8 : 6;
+  static constexpr int ctas = FROM_SIG ? 2 : 3;
+};
+constexpr int kWsLag = 4;        // rows a producer thread keeps in flight (<= ring - 3)
 constexpr int kWsEpi = 8;        // epilogue warps
 constexpr int kWsProd = 4;       // producer warps
 constexpr int kWsThreads = 32 * (kWsEpi + kWsProd + 1);
 constexpr int kWsMmaWarp = kWsEpi + kWsProd;
-static_assert(kWsLag <= kWsR - 3, "a producer must be able to publish the rows the MMA waits for");
+static_assert(kWsLag <= WsShape<true>::R - 3,
+              "a producer must be able to publish the rows the MMA waits for");
 
 __device__ __forceinline__ void ws_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_smem(bar)) : "memory");
@@ -799,21 +808,22 @@ __device__ __forceinline__ void bulk_g2s_ws(void* dst, const void* src, uint32_t
 }
 
 template <int NOUT, int MODE, bool FROM_SIG>
-__global__ void __launch_bounds__(kWsThreads, 2) conv_ws_kernel(
+__global__ void __launch_bounds__(kWsThreads, WsShape<FROM_SIG>::ctas) conv_ws_kernel(
     const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Wg,
     const float* __restrict__ bias, int L, int64_t shots, __nv_bfloat16* __restrict__ out,
     float* __restrict__ logits, const uint8_t* __restrict__ sig, uint8_t* __restrict__ prop,
     unsigned int* __restrict__ err, const __nv_bfloat16* __restrict__ lut) {
   constexpr int CO_SRC = NOUT == 32 ? 32 : 8;
+  constexpr int kR = WsShape<FROM_SIG>::R;         // staged rows in the ring
   constexpr uint32_t kRowBytes = 4 * kTcRow * 16;  // one staged row
-  constexpr uint32_t kA = kWsR * kRowBytes;        // the ring
+  constexpr uint32_t kA = kR * kRowBytes;          // the ring
   constexpr uint32_t kB = 9 * 4 * NOUT * 16;       // weights
   extern __shared__ __align__(128) uint8_t sm[];
   uint8_t* sA = sm;
   uint8_t* sB = sm + kA;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kA + kB);  // [kWsR]
-  uint64_t* empty = full + kWsR;                               // [kWsR]
-  uint64_t* acc_full = empty + kWsR;                           // [2]
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kA + kB);  // [kR]
+  uint64_t* empty = full + kR;                               // [kR]
+  uint64_t* acc_full = empty + kR;                           // [2]
   uint64_t* acc_empty = acc_full + 2;                          // [2]
   uint64_t* drained = acc_empty + 2;                           // [1]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drained + 1);
@@ -830,7 +840,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws_kernel(
   }
   for (int i = tid; i < NOUT; i += kWsThreads) sbias[i] = (MODE == kActs || i < 4) ? bias[i] : 0.f;
   if (tid == 0) {
-    for (int k = 0; k < kWsR; ++k) {
+    for (int k = 0; k < kR; ++k) {
       ws_bar_init(&full[k], FROM_SIG ? 32 * kWsProd : 1);
       ws_bar_init(&empty[k], 1);
     }
@@ -877,8 +887,8 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws_kernel(
         const int xl = x0 == 0 ? L - 1 : x0 - 1, xr = x0 + kTcM == L ? 0 : x0 + kTcM;
         int r = -1;
         for (; r <= kTcStrip; ++r, ++e) {
-          const int slot = (int)(e % kWsR);
-          if (e >= kWsR && !ws_wait(&empty[slot], (uint32_t)((e / kWsR - 1) & 1), stop)) break;
+          const int slot = (int)(e % kR);
+          if (e >= kR && !ws_wait(&empty[slot], (uint32_t)((e / kR - 1) & 1), stop)) break;
           int yy = y0 + r;
           yy = yy < 0 ? yy + L : (yy >= L ? yy - L : yy);
           uint8_t* dst = sA + (size_t)slot * kRowBytes;
@@ -896,8 +906,8 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws_kernel(
       }
       // no copy may still be landing when the CTA exits: wait (bounded) for the
       // last entry of every slot (a no-op unless the CTA stopped early)
-      for (int64_t f = e > kWsR ? e - kWsR : 0; f < e; ++f)
-        (void)tc_bar_wait(&full[f % kWsR], (uint32_t)((f / kWsR) & 1));
+      for (int64_t f = e > kR ? e - kR : 0; f < e; ++f)
+        (void)tc_bar_wait(&full[f % kR], (uint32_t)((f / kR) & 1));
     }
     __syncwarp();
   } else if (FROM_SIG && warp >= kWsEpi && warp < kWsMmaWarp) {
@@ -910,8 +920,8 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws_kernel(
       int x0, y0;
       unit_of(u, shot, x0, y0);
       for (int r = -1; r <= kTcStrip && !*stop; ++r, ++e) {
-        const int slot = (int)(e % kWsR);
-        if (e >= kWsR && !ws_wait(&empty[slot], (uint32_t)((e / kWsR - 1) & 1), stop)) break;
+        const int slot = (int)(e % kR);
+        if (e >= kR && !ws_wait(&empty[slot], (uint32_t)((e / kR - 1) & 1), stop)) break;
         int yy = y0 + r;
         yy = yy < 0 ? yy + L : (yy >= L ? yy - L : yy);
         uint8_t* dst = sA + (size_t)slot * kRowBytes;
@@ -938,14 +948,14 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws_kernel(
           // the copies of entry e - kWsLag have landed: publish it
           asm volatile("cp.async.wait_group %0;" ::"n"(kWsLag) : "memory");
           tc_fence_proxy_shared();
-          ws_arrive(&full[(e - kWsLag) % kWsR]);
+          ws_arrive(&full[(e - kWsLag) % kR]);
         }
       }
     }
     // publish the entries still in flight
     tc_cp_wait_all();
     tc_fence_proxy_shared();
-    for (int64_t f = e > kWsLag ? e - kWsLag : 0; f < e; ++f) ws_arrive(&full[f % kWsR]);
+    for (int64_t f = e > kWsLag ? e - kWsLag : 0; f < e; ++f) ws_arrive(&full[f % kR]);
   } else if (warp == kWsMmaWarp) {
     // ================= MMA issue (one thread)
     if (lane == 0) {
@@ -958,7 +968,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws_kernel(
           const int64_t eb = e + j;  // entries eb .. eb + 2: rows y - 1 .. y + 1
 #pragma unroll
           for (int dy = 0; dy < 3; ++dy)
-            ok = ok && ws_wait(&full[(eb + dy) % kWsR], (uint32_t)(((eb + dy) / kWsR) & 1), stop);
+            ok = ok && ws_wait(&full[(eb + dy) % kR], (uint32_t)(((eb + dy) / kR) & 1), stop);
           const int acc = (int)(T & 1);
           if (ok && T >= 2) ok = ws_wait(&acc_empty[acc], (uint32_t)(((T >> 1) - 1) & 1), stop);
           if (!ok) break;
@@ -966,7 +976,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws_kernel(
 #pragma unroll
           for (int tap = 0; tap < 9; ++tap) {
             const int dy = tap / 3, dx = tap % 3 - 1;
-            const uint32_t slot = (uint32_t)((eb + dy) % kWsR);
+            const uint32_t slot = (uint32_t)((eb + dy) % kR);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               const uint32_t aaddr =
@@ -977,10 +987,10 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws_kernel(
             }
           }
           tc_commit(&acc_full[acc]);
-          tc_commit(&empty[eb % kWsR]);  // no later tile reads entry eb
+          tc_commit(&empty[eb % kR]);  // no later tile reads entry eb
           if (j == kTcStrip - 1) {       // nor the unit's last two rows
-            tc_commit(&empty[(eb + 1) % kWsR]);
-            tc_commit(&empty[(eb + 2) % kWsR]);
+            tc_commit(&empty[(eb + 1) % kR]);
+            tc_commit(&empty[(eb + 2) % kR]);
           }
         }
         e += kTcStrip + 2;
@@ -1058,9 +1068,10 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws_kernel(
                  : "memory");
 }
 
-template <int NOUT>
+template <int NOUT, bool FROM_SIG>
 constexpr size_t ws_smem_bytes() {
-  return (size_t)kWsR * 4 * kTcRow * 16 + 9 * 4 * NOUT * 16 + (2 * kWsR + 5) * 8 + 16 + 4 * NOUT;
+  constexpr int R = WsShape<FROM_SIG>::R;
+  return (size_t)R * 4 * kTcRow * 16 + 9 * 4 * NOUT * 16 + (2 * R + 5) * 8 + 16 + 4 * NOUT;
 }
 
 // two floats -> two E4M3 bytes (lo in the low byte), saturating
@@ -1109,22 +1120,23 @@ __global__ void layer1_lut8_kernel(const float* __restrict__ W1, const float* __
 }
 
 template <int NOUT, int MODE, bool FROM_SIG>
-__global__ void __launch_bounds__(kWsThreads, 2) conv_ws8_kernel(
+__global__ void __launch_bounds__(kWsThreads, WsShape<FROM_SIG>::ctas) conv_ws8_kernel(
     const uint8_t* __restrict__ in, const uint8_t* __restrict__ Wq,
     const float* __restrict__ wscale, const float* __restrict__ bias, float s_in,
     float inv_s_out, int L, int64_t shots, uint8_t* __restrict__ out,
     float* __restrict__ logits, const uint8_t* __restrict__ sig, uint8_t* __restrict__ prop,
     unsigned int* __restrict__ err, const uint8_t* __restrict__ lut8) {
   constexpr int CO_SRC = NOUT == 32 ? 32 : 8;
+  constexpr int kR = WsShape<FROM_SIG>::R;         // staged rows in the ring
   constexpr uint32_t kRowBytes = 2 * kTcRow * 16;  // one staged row: two 16-channel planes
-  constexpr uint32_t kA = kWsR * kRowBytes;        // the ring
+  constexpr uint32_t kA = kR * kRowBytes;          // the ring
   constexpr uint32_t kB = 9 * 2 * NOUT * 16;       // weights
   extern __shared__ __align__(128) uint8_t sm[];
   uint8_t* sA = sm;
   uint8_t* sB = sm + kA;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kA + kB);  // [kWsR]
-  uint64_t* empty = full + kWsR;                               // [kWsR]
-  uint64_t* acc_full = empty + kWsR;                           // [2]
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kA + kB);  // [kR]
+  uint64_t* empty = full + kR;                               // [kR]
+  uint64_t* acc_full = empty + kR;                           // [2]
   uint64_t* acc_empty = acc_full + 2;                          // [2]
   uint64_t* drained = acc_empty + 2;                           // [1]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drained + 1);
@@ -1147,7 +1159,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws8_kernel(
     sscale[i] = real ? s_in * wscale[i] : 0.f;
   }
   if (tid == 0) {
-    for (int k = 0; k < kWsR; ++k) {
+    for (int k = 0; k < kR; ++k) {
       ws_bar_init(&full[k], FROM_SIG ? 32 * kWsProd : 1);
       ws_bar_init(&empty[k], 1);
     }
@@ -1192,8 +1204,8 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws8_kernel(
         const int xl = x0 == 0 ? L - 1 : x0 - 1, xr = x0 + kTcM == L ? 0 : x0 + kTcM;
         int r = -1;
         for (; r <= kTcStrip; ++r, ++e) {
-          const int slot = (int)(e % kWsR);
-          if (e >= kWsR && !ws_wait(&empty[slot], (uint32_t)((e / kWsR - 1) & 1), stop)) break;
+          const int slot = (int)(e % kR);
+          if (e >= kR && !ws_wait(&empty[slot], (uint32_t)((e / kR - 1) & 1), stop)) break;
           int yy = y0 + r;
           yy = yy < 0 ? yy + L : (yy >= L ? yy - L : yy);
           uint8_t* dst = sA + (size_t)slot * kRowBytes;
@@ -1210,8 +1222,8 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws8_kernel(
         if (r <= kTcStrip) break;  // stopped
       }
       // no copy may still be landing when the CTA exits
-      for (int64_t f = e > kWsR ? e - kWsR : 0; f < e; ++f)
-        (void)tc_bar_wait(&full[f % kWsR], (uint32_t)((f / kWsR) & 1));
+      for (int64_t f = e > kR ? e - kR : 0; f < e; ++f)
+        (void)tc_bar_wait(&full[f % kR], (uint32_t)((f / kR) & 1));
     }
     __syncwarp();
   } else if (FROM_SIG && warp >= kWsEpi && warp < kWsMmaWarp) {
@@ -1223,8 +1235,8 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws8_kernel(
       int x0, y0;
       unit_of(u, shot, x0, y0);
       for (int r = -1; r <= kTcStrip && !*stop; ++r, ++e) {
-        const int slot = (int)(e % kWsR);
-        if (e >= kWsR && !ws_wait(&empty[slot], (uint32_t)((e / kWsR - 1) & 1), stop)) break;
+        const int slot = (int)(e % kR);
+        if (e >= kR && !ws_wait(&empty[slot], (uint32_t)((e / kR - 1) & 1), stop)) break;
         int yy = y0 + r;
         yy = yy < 0 ? yy + L : (yy >= L ? yy - L : yy);
         uint8_t* dst = sA + (size_t)slot * kRowBytes;
@@ -1247,13 +1259,13 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws8_kernel(
         if (e >= kWsLag) {
           asm volatile("cp.async.wait_group %0;" ::"n"(kWsLag) : "memory");
           tc_fence_proxy_shared();
-          ws_arrive(&full[(e - kWsLag) % kWsR]);
+          ws_arrive(&full[(e - kWsLag) % kR]);
         }
       }
     }
     tc_cp_wait_all();
     tc_fence_proxy_shared();
-    for (int64_t f = e > kWsLag ? e - kWsLag : 0; f < e; ++f) ws_arrive(&full[f % kWsR]);
+    for (int64_t f = e > kWsLag ? e - kWsLag : 0; f < e; ++f) ws_arrive(&full[f % kR]);
   } else if (warp == kWsMmaWarp) {
     // ================= MMA issue (one thread): one K = 32 MMA per tap
     if (lane == 0) {
@@ -1266,7 +1278,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws8_kernel(
           const int64_t eb = e + j;
 #pragma unroll
           for (int dy = 0; dy < 3; ++dy)
-            ok = ok && ws_wait(&full[(eb + dy) % kWsR], (uint32_t)(((eb + dy) / kWsR) & 1), stop);
+            ok = ok && ws_wait(&full[(eb + dy) % kR], (uint32_t)(((eb + dy) / kR) & 1), stop);
           const int acc = (int)(T & 1);
           if (ok && T >= 2) ok = ws_wait(&acc_empty[acc], (uint32_t)(((T >> 1) - 1) & 1), stop);
           if (!ok) break;
@@ -1274,17 +1286,17 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws8_kernel(
 #pragma unroll
           for (int tap = 0; tap < 9; ++tap) {
             const int dy = tap / 3, dx = tap % 3 - 1;
-            const uint32_t slot = (uint32_t)((eb + dy) % kWsR);
+            const uint32_t slot = (uint32_t)((eb + dy) % kR);
             const uint32_t aaddr = a0 + slot * kRowBytes + (uint32_t)(1 + dx) * 16;
             const uint32_t baddr = b0 + (uint32_t)(tap * 2 * NOUT) * 16;
             tc_mma_e4m3(tmem + (uint32_t)(acc * 32), tc_desc(aaddr, kTcRow * 16, 128),
                         tc_desc(baddr, NOUT * 16, 128), idesc, tap != 0);
           }
           tc_commit(&acc_full[acc]);
-          tc_commit(&empty[eb % kWsR]);
+          tc_commit(&empty[eb % kR]);
           if (j == kTcStrip - 1) {
-            tc_commit(&empty[(eb + 1) % kWsR]);
-            tc_commit(&empty[(eb + 2) % kWsR]);
+            tc_commit(&empty[(eb + 1) % kR]);
+            tc_commit(&empty[(eb + 2) % kR]);
           }
         }
         e += kTcStrip + 2;
@@ -1367,10 +1379,10 @@ __global__ void __launch_bounds__(kWsThreads, 2) conv_ws8_kernel(
                  : "memory");
 }
 
-template <int NOUT>
+template <int NOUT, bool FROM_SIG>
 constexpr size_t ws8_smem_bytes() {
-  return (size_t)kWsR * 2 * kTcRow * 16 + 9 * 2 * NOUT * 16 + (2 * kWsR + 5) * 8 + 16 +
-         8 * NOUT;
+  constexpr int R = WsShape<FROM_SIG>::R;
+  return (size_t)R * 2 * kTcRow * 16 + 9 * 2 * NOUT * 16 + (2 * R + 5) * 8 + 16 + 8 * NOUT;
 }
 
 // Self-test of the bounded waits the tensor-core kernels use: thread 0 waits
@@ -2292,29 +2304,35 @@ int net_run(qca_net_s* n, const uint8_t* noise, int L, int64_t shots, float* log
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       const int64_t units = S / ((int64_t)kTcM * kTcStrip);
-      const int gt = (int)(units < (int64_t)sms * 2 ? units : (int64_t)sms * 2);
+      auto grid_of = [&](int ctas) {
+        return (int)(units < (int64_t)sms * ctas ? units : (int64_t)sms * ctas);
+      };
+      const int gs = grid_of(WsShape<true>::ctas), gt = grid_of(WsShape<false>::ctas);
       if (c0s == 0) layer1_lut8_kernel<<<32, 256, 0, st>>>(n->w1, n->params, 1.f / sa[0], n->lut8);
-      cudaFuncSetAttribute(conv_ws8_kernel<32, kActs, true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws8_smem_bytes<32>());
+      cudaFuncSetAttribute(conv_ws8_kernel<32, kActs, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ws8_smem_bytes<32, true>());
       cudaFuncSetAttribute(conv_ws8_kernel<32, kActs, false>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws8_smem_bytes<32>());
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ws8_smem_bytes<32, false>());
       cudaFuncSetAttribute(conv_ws8_kernel<16, kLogits, false>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws8_smem_bytes<16>());
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ws8_smem_bytes<16, false>());
       cudaFuncSetAttribute(conv_ws8_kernel<16, kProposals, false>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws8_smem_bytes<16>());
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ws8_smem_bytes<16, false>());
       // layers 1 + 2 (layer 1 looked up while staging), 3, 4
-      conv_ws8_kernel<32, kActs, true><<<gt, kWsThreads, ws8_smem_bytes<32>(), st>>>(
+      conv_ws8_kernel<32, kActs, true><<<gs, kWsThreads, ws8_smem_bytes<32, true>(), st>>>(
           nullptr, n->wq, n->wscale, n->params + kB1, sa[0], 1.f / sa[1], L, m, a8B, nullptr, sig,
           nullptr, n->err, n->lut8);
-      conv_ws8_kernel<32, kActs, false><<<gt, kWsThreads, ws8_smem_bytes<32>(), st>>>(
+      conv_ws8_kernel<32, kActs, false><<<gt, kWsThreads, ws8_smem_bytes<32, false>(), st>>>(
           a8B, n->wq + 9 * 32 * 32, n->wscale + 32, n->params + kB2, sa[1], 1.f / sa[2], L, m,
           a8A, nullptr, nullptr, nullptr, n->err, nullptr);
       if (logits) {
-        conv_ws8_kernel<16, kLogits, false><<<gt, kWsThreads, ws8_smem_bytes<16>(), st>>>(
+        conv_ws8_kernel<16, kLogits, false><<<gt, kWsThreads, ws8_smem_bytes<16, false>(), st>>>(
             a8A, n->wq + 2 * 9 * 32 * 32, n->wscale + 64, n->params + kB3, sa[2], 0.f, L, m,
             nullptr, logits + c0s * 4 * LL, nullptr, nullptr, n->err, nullptr);
       } else {
-        conv_ws8_kernel<16, kProposals, false><<<gt, kWsThreads, ws8_smem_bytes<16>(), st>>>(
+        conv_ws8_kernel<16, kProposals, false><<<gt, kWsThreads, ws8_smem_bytes<16, false>(), st>>>(
             a8A, n->wq + 2 * 9 * 32 * 32, n->wscale + 64, n->params + kB3, sa[2], 0.f, L, m,
             nullptr, nullptr, sig, prop, n->err, nullptr);
         pairing_kernel<<<grid_for(S, 256), 256, 0, st>>>(Nc, prop, L, m, resid + c0s * 2 * LL,
@@ -2357,27 +2375,32 @@ int net_run(qca_net_s* n, const uint8_t* noise, int L, int64_t shots, float* log
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       const int64_t units = S / ((int64_t)kTcM * kTcStrip);
-      const int gt = (int)(units < (int64_t)sms * 2 ? units : (int64_t)sms * 2);
-      cudaFuncSetAttribute(conv_ws_kernel<32, kActs, true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem_bytes<32>());
-      cudaFuncSetAttribute(conv_ws_kernel<32, kActs, false>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem_bytes<32>());
+      auto grid_of = [&](int ctas) {
+        return (int)(units < (int64_t)sms * ctas ? units : (int64_t)sms * ctas);
+      };
+      const int gs = grid_of(WsShape<true>::ctas), gt = grid_of(WsShape<false>::ctas);
+      cudaFuncSetAttribute(conv_ws_kernel<32, kActs, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ws_smem_bytes<32, true>());
+      cudaFuncSetAttribute(conv_ws_kernel<32, kActs, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ws_smem_bytes<32, false>());
       cudaFuncSetAttribute(conv_ws_kernel<16, kLogits, false>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem_bytes<16>());
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ws_smem_bytes<16, false>());
       cudaFuncSetAttribute(conv_ws_kernel<16, kProposals, false>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem_bytes<16>());
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ws_smem_bytes<16, false>());
       // layers 1 + 2 (layer 1 looked up while staging), 3, 4
-      conv_ws_kernel<32, kActs, true><<<gt, kWsThreads, ws_smem_bytes<32>(), st>>>(
+      conv_ws_kernel<32, kActs, true><<<gs, kWsThreads, ws_smem_bytes<32, true>(), st>>>(
           nullptr, n->wb, n->params + kB1, L, m, actB, nullptr, sig, nullptr, n->err, n->lut);
-      conv_ws_kernel<32, kActs, false><<<gt, kWsThreads, ws_smem_bytes<32>(), st>>>(
+      conv_ws_kernel<32, kActs, false><<<gt, kWsThreads, ws_smem_bytes<32, false>(), st>>>(
           actB, n->wb + 9 * 32 * 32, n->params + kB2, L, m, actA, nullptr, nullptr, nullptr,
           n->err, nullptr);
       if (logits) {
-        conv_ws_kernel<16, kLogits, false><<<gt, kWsThreads, ws_smem_bytes<16>(), st>>>(
+        conv_ws_kernel<16, kLogits, false><<<gt, kWsThreads, ws_smem_bytes<16, false>(), st>>>(
             actA, n->wb + 2 * 9 * 32 * 32, n->params + kB3, L, m, nullptr, logits + c0s * 4 * LL,
             nullptr, nullptr, n->err, nullptr);
       } else {
-        conv_ws_kernel<16, kProposals, false><<<gt, kWsThreads, ws_smem_bytes<16>(), st>>>(
+        conv_ws_kernel<16, kProposals, false><<<gt, kWsThreads, ws_smem_bytes<16, false>(), st>>>(
             actA, n->wb + 2 * 9 * 32 * 32, n->params + kB3, L, m, nullptr, nullptr, sig, prop,
             n->err, nullptr);
         pairing_kernel<<<grid_for(S, 256), 256, 0, st>>>(Nc, prop, L, m, resid + c0s * 2 * LL,
