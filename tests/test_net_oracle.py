@@ -310,7 +310,7 @@ def test_loss_and_grads_match_torch_autograd():
     q = eps / 5 + (1 - eps) * onehot.double()
     tl = -(q * logp).sum(dim=1)[valid].mean()
     tl.backward()
-    assert loss == pytest.approx(float(tl), rel=1e-12)
+    assert loss == pytest.approx(float(tl.detach()), rel=1e-12)
     np.testing.assert_allclose(g, p.grad.numpy(), rtol=1e-9, atol=1e-12)
 
 
