@@ -39,8 +39,8 @@ UNIT = "shot-decodes/s"
 # Integer-ALU roofline of the sweep: the fused
 # v = 3 message update costs 16 min/compare lane-ops per site-update (4 fields x
 # (3 two-input mins of the width-7 cone window + 1 clamp)); the ALU pipe issues
-# 64 32-bit instructions / clk / SM (measured with a microbenchmark on GB300:
-# LOP3, IMNMX and the native 16x2 VIMNMX all issue at this rate), each carrying
+# 64 32-bit instructions / clk / SM (qca_probe_peaks measures min.u16x2, lop3
+# and min.u32 all at this rate; reported as "probe"), each carrying
 # 2 16-bit lanes; 152 SMs at the 2070 MHz maximum SM clock.
 ALU_OPS_PER_SITE_UPDATE = 16
 ALU_PEAK_LANE_OPS = 152 * 64 * 2 * 2.070e9
@@ -1116,6 +1116,14 @@ def main():
 
     kernel_s = statistics.mean(kernel_ms) / 1e3
     achieved = ALU_OPS_PER_SITE_UPDATE * site_updates / kernel_s
+    # the two denominators measured on this device (untimed, after the timed
+    # region): min.u16x2 issue rate and shared-memory load bandwidth
+    pk = qca.probe_peaks()
+    smem_achieved = SMEM_BYTES_PER_SITE_UPDATE * site_updates / kernel_s
+    probe = dict(pk, frac_alu_of_probe=achieved / pk["min16x2_lane_ops_per_s"],
+                 frac_smem_of_probe=smem_achieved / pk["smem_bytes_per_s"],
+                 note="microbenchmarks of the roofline denominators (qca_probe_peaks); "
+                      "roofline.peak stays the value derived from unit counts and clock")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -1133,11 +1141,12 @@ def main():
                      "traffic": traffic_per_launch(L, args.p, shots),
                      "kernel_ms": statistics.mean(kernel_ms)},
         "roofline_smem": {"bound": "smem",
-                          "achieved": SMEM_BYTES_PER_SITE_UPDATE * site_updates / kernel_s / 1e9,
+                          "achieved": smem_achieved / 1e9,
                           "peak": SMEM_PEAK / 1e9, "unit": "GB/s",
-                          "frac": SMEM_BYTES_PER_SITE_UPDATE * site_updates / kernel_s / SMEM_PEAK,
+                          "frac": smem_achieved / SMEM_PEAK,
                           "note": "second fraction of the same kernel: 8 B of shared memory "
                                   "per site-update; the ALU fraction is the higher, binding one"},
+        "probe": probe,
         "clocks": clk,
         "gpu_launches": launches,
         "e2e": e2e,

@@ -462,6 +462,29 @@ int qca_set_kernel_path(int L, int path);
  * host-path staging buffers) on the current device. */
 int qca_free_workspace(void);
 
+/* Microbenchmarks of the sweep's roofline denominators on the current device
+ * (no counterpart in the paper: measurement only).  Four kernels, each one
+ * wave of resident 512-thread CTAs on every SM for a few tens of
+ * milliseconds, time one instruction written as inline PTX: min.u16x2 (the
+ * sweep's byte-pair minimum), lop3.b32, min.u32, and conflict-free 16-byte
+ * shared-memory loads.  Thread 0 of every CTA reads the SM clock (clock64) and
+ * the global timer around its loop; the per-clock rates divide the work of
+ * the CTAs resident on an SM by the median CTA's cycles, the per-second rates
+ * use the launch's CUDA-event time.  Synchronises the device.  Errors:
+ * QCA_ERR_ARG for NULL, QCA_ERR_CUDA. */
+typedef struct qca_peaks {
+  int sms;                        /* multiprocessors */
+  int ctas_per_sm;                /* resident probe CTAs per SM (one wave) */
+  double sm_clock_mhz;            /* median SM clock during the min.u16x2 probe */
+  double min16x2_per_clk_sm;      /* min.u16x2 instructions per clock per SM (2 lanes each) */
+  double lop3_per_clk_sm;         /* lop3.b32 instructions per clock per SM */
+  double min_u32_per_clk_sm;      /* min.u32 instructions per clock per SM */
+  double smem_bytes_per_clk_sm;   /* shared-memory load bytes per clock per SM */
+  double min16x2_lane_ops_per_s;  /* 2 x min.u16x2 instructions per second, whole device */
+  double smem_bytes_per_s;        /* shared-memory load bytes per second, whole device */
+} qca_peaks;
+int qca_probe_peaks(qca_peaks* out);
+
 /* Static, thread-local description of the last error (never NULL). */
 const char* qca_last_error(void);
 

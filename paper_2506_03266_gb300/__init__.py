@@ -104,6 +104,7 @@ def lib():
             "qca_net_set_tensor_path": ([vp, i32], i32),
             "qca_net_status": ([vp], i32),
             "qca_watchdog_selftest": ([vp, vp, vp, vp], i32),
+            "qca_probe_peaks": ([vp], i32),
             "qca_net_logits_async": ([vp, vp, i32, i64, vp, vp], i32),
             "qca_net_predecode_async": ([vp, vp, i32, i64, vp, vp, vp], i32),
             "qca_net_decode_batch_async": ([vp, vp, i32, i64, i32, u64, vp, vp, vp, cfgp, vp,
@@ -622,6 +623,25 @@ def watchdog_selftest():
     _check(lib().qca_watchdog_selftest(ctypes.byref(a), ctypes.byref(b), ctypes.byref(t1),
                                        ctypes.byref(t2)))
     return bool(a.value), bool(b.value), t1.value, t2.value
+
+
+class QcaPeaks(ctypes.Structure):
+    """Mirror of struct qca_peaks (include/qca.h)."""
+    _fields_ = [("sms", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("sm_clock_mhz", ctypes.c_double), ("min16x2_per_clk_sm", ctypes.c_double),
+                ("lop3_per_clk_sm", ctypes.c_double), ("min_u32_per_clk_sm", ctypes.c_double),
+                ("smem_bytes_per_clk_sm", ctypes.c_double),
+                ("min16x2_lane_ops_per_s", ctypes.c_double), ("smem_bytes_per_s", ctypes.c_double)]
+
+
+def probe_peaks():
+    """Measured issue rates of min.u16x2, lop3.b32 and min.u32 and the
+    shared-memory load bandwidth of the current device (per clock per SM and
+    per second), with the SM clock seen during the probes: the denominators of
+    the sweep's integer-ALU and shared-memory rooflines."""
+    out = QcaPeaks()
+    _check(lib().qca_probe_peaks(ctypes.byref(out)))
+    return {name: getattr(out, name) for name, _ in QcaPeaks._fields_}
 
 
 def free_workspace():

@@ -84,6 +84,7 @@ def test_argument_errors_need_no_gpu(lib):
     # zero shots: nothing to do, NULL allowed, no device call
     assert lib.qca_decode_batch_async(None, 16, 0, 10, 0, None, None, None, None, None) == 0
     assert lib.qca_sample_errors_async(16, 0, 0, 0.1, 0, None, None) == 0
+    assert lib.qca_probe_peaks(None) == qca.QCA_ERR_ARG
 
 
 def test_kernel_path_table(lib):

@@ -1,0 +1,43 @@
+"""The roofline probes (qca_probe_peaks): rates that the hardware can reach at
+all (an SM issues at most four warp instructions, 128 thread instructions, per
+clock, and its shared memory delivers at most 128 B per clock), and per-clock
+and per-second figures that agree with the clock seen during the probe."""
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2506_03266_gb300 as qca  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def peaks():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    qca.build()
+    qca.lib()
+    return qca.probe_peaks()
+
+
+def test_probe_shape_and_clock(peaks):
+    assert peaks["sms"] == torch.cuda.get_device_properties(0).multi_processor_count
+    assert peaks["ctas_per_sm"] >= 1
+    assert 300.0 < peaks["sm_clock_mhz"] < 3000.0
+
+
+@pytest.mark.parametrize("key", ["min16x2_per_clk_sm", "lop3_per_clk_sm", "min_u32_per_clk_sm"])
+def test_issue_rates_are_physical(peaks, key):
+    assert 8.0 < peaks[key] <= 128.0 * 1.02, peaks
+
+
+def test_shared_memory_rate_is_physical(peaks):
+    # clock64 spans of the median CTA: about 1 % above the nominal 128 measured
+    assert 16.0 < peaks["smem_bytes_per_clk_sm"] <= 128.0 * 1.05, peaks
+
+
+def test_per_second_rates_match_per_clock_rates(peaks):
+    hz = peaks["sm_clock_mhz"] * 1e6
+    want = 2.0 * peaks["min16x2_per_clk_sm"] * peaks["sms"] * hz
+    assert peaks["min16x2_lane_ops_per_s"] == pytest.approx(want, rel=0.15), peaks
+    want = peaks["smem_bytes_per_clk_sm"] * peaks["sms"] * hz
+    assert peaks["smem_bytes_per_s"] == pytest.approx(want, rel=0.15), peaks
