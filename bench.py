@@ -708,6 +708,14 @@ def run_1d(args, rank, world, local):
         dist.destroy_process_group()
 
 
+# Shared-memory roofline of the literal variant kernel: a message sub-step reads
+# and writes each of a site's four field bytes once (8 B); open boundaries run
+# v = 3 sub-steps per step (24 B per site-update), the desynchronised decoder
+# one (at the firing sites, but the kernel carries every site) per tick.
+SMEM_BYTES_PER_SITE_STEP_OPEN = 24
+SMEM_BYTES_PER_SITE_TICK_DESYNC = 8
+
+
 def run_variant(args, rank, world, local):
     """Open boundaries (L = 64, p = 0.05) or uncoordinated desynchronisation
     (torus L = 32, p = 0.03, ticks of q = 0.1), 100 000 shots each; one step is
@@ -770,6 +778,9 @@ def run_variant(args, rank, world, local):
         return
     stats = step_stats(st, fl, shots)
     unit_steps = "steps" if open_ else "ticks"
+    site_units = float(st.astype(np.int64).sum()) * L * L
+    per_unit = SMEM_BYTES_PER_SITE_STEP_OPEN if open_ else SMEM_BYTES_PER_SITE_TICK_DESYNC
+    smem_achieved = per_unit * site_units / (ms_per_step / 1e3)
     if not open_:
         stats["mean_time"] = float(st.mean() * q)   # in units of the move clock's mean period
     name = ("open-boundary decode (rough left/right boundaries), L x L grid" if open_ else
@@ -780,13 +791,18 @@ def run_variant(args, rank, world, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "site_updates_per_s": float(st.astype(np.int64).sum()) * L * L / (ms_per_step / 1e3),
+        "site_updates_per_s": site_units / (ms_per_step / 1e3),
         "config": {"workload": (f"{name} L={L}, i.i.d. bit-flip p={p} (seed 0), {shots} shots "
                                 f"per GPU, v=3; {unit_steps} counted"),
                    "L": L, "p": p, "shots_per_gpu": shots,
                    "l2": "each CTA's state slot is reused across its shots"},
         "decoder": stats,
-        "roofline": None,
+        "roofline": {"bound": "smem", "achieved": smem_achieved / 1e9, "peak": SMEM_PEAK / 1e9,
+                     "unit": "GB/s", "frac": smem_achieved / SMEM_PEAK, "traffic": None,
+                     "note": (f"{per_unit} shared-memory bytes per site-"
+                              f"{'update' if open_ else 'tick'}: each message sub-step reads and "
+                              "writes a site's four field bytes once; literal per-site kernel, "
+                              "one launch per step")},
         "clocks": clk, "gpu_launches": args.steps, "e2e": None, "cpu_baseline": None,
     }
     print(json.dumps(line), flush=True)
