@@ -21,6 +21,11 @@
  *     e_x(r) = <r, r + x^>, plane 1 is e_y(r) = <r, r + y^>.
  *   - all array pointers are caller-owned DEVICE memory unless the entry point
  *     name ends in _host; the library never frees them.
+ *   - a typed array (int32, int64, float ...) must start on a multiple of its
+ *     element size, else QCA_ERR_ARG.  uint8 arrays may start anywhere: where
+ *     an input or correction array (or a packed shot block) is not 4-byte
+ *     aligned, the decoder uses its byte-access kernel instead of the faster
+ *     word-access ones, with the same results.
  *   - "stream" arguments are cudaStream_t handles passed as void*; NULL means
  *     the legacy default stream.  *_async calls return after enqueueing; the
  *     others synchronise before returning.

@@ -226,6 +226,7 @@ int qca_decode_1d_batch_async(const uint8_t* noise, int L, int64_t shots, int ma
     set_error("qca_decode_1d_batch_async: NULL array pointer");
     return QCA_ERR_ARG;
   }
+  if (int rc = check_aligned(out_steps, 4, "qca_decode_1d_batch_async: out_steps")) return rc;
   if (shots == 0) return QCA_OK;
   Args1D a;
   a.in = noise;

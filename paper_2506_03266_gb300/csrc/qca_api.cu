@@ -45,6 +45,14 @@ int cuda_fail(cudaError_t e, const char* what) {
   return QCA_ERR_CUDA;
 }
 
+int check_aligned(const void* p, size_t align, const char* what) {
+  if (reinterpret_cast<uintptr_t>(p) & (align - 1)) {
+    set_error("%s is not %zu-byte aligned", what, align);
+    return QCA_ERR_ARG;
+  }
+  return QCA_OK;
+}
+
 static int check_config(const qca_config* cfg, qca_config* out) {
   qca_default_config(out);
   if (cfg) *out = *cfg;
@@ -87,7 +95,13 @@ int decode_path(int L, int v, int m_max) {
 
 int launch_decode(const DecodeArgs& a, cudaStream_t stream) {
   if (a.shots == 0) return QCA_OK;
-  const int path = decode_path(a.L, a.v, a.m_max);
+  if (int rc = check_aligned(a.out_steps, 4, "out_steps")) return rc;
+  int path = decode_path(a.L, a.v, a.m_max);
+  // The on-chip and large-lattice kernels read the input and write the
+  // correction as 32-bit words.  A caller array or shot block off a 4-byte
+  // boundary goes to the generic sweep, which accesses bytes (same results).
+  const uintptr_t wide = reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(a.out_C);
+  if (path > 0 && (a.bytewise || (wide & 3))) path = 0;
   if (path == 3) return launch_tiled(a, stream);
   if (path > 0) return launch_fast(a, stream);
   return launch_generic(a, stream);
@@ -224,6 +238,7 @@ int qca_decode_batch_noalloc(const uint8_t* syndrome, int L, int64_t shots, int 
     set_error("NULL array pointer");
     return QCA_ERR_ARG;
   }
+  if ((rc = check_aligned(out_steps, 4, "out_steps"))) return rc;
   DecodeArgs a;
   fill_args(a, syndrome, L, shots, max_steps, rng_seed, c);
   a.out_C = out_correction;

@@ -44,6 +44,9 @@ struct DecodeArgs {
   const int32_t* shot_list;
   const int64_t* offsets;
   unsigned int* queue;
+  // Some shot block starts off a 4-byte boundary (packed uneven batches with
+  // odd L): only the byte-access generic sweep may read it.
+  int bytewise;
 };
 
 // Byte offset of shot `shot`'s input block: [2][L][L] noise, or [L][L] sigma.
@@ -62,6 +65,10 @@ __host__ __device__ __forceinline__ int64_t correction_offset_of(const DecodeArg
 // Per-thread error text (set by the host layer).
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
+// A typed device array must start on a multiple of its element size (the
+// kernels would fault on it otherwise): QCA_ERR_ARG with the array's name if
+// it does not, else QCA_OK.  NULL passes (the NULL checks are separate).
+int check_aligned(const void* p, size_t align, const char* what);
 
 // Random-move key chain shared by the kernels: key for (shot, step).
 __device__ __forceinline__ uint64_t move_step_key(uint64_t move_key, int64_t shot, int t) {

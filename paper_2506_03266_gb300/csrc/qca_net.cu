@@ -2485,6 +2485,7 @@ int qca_net_logits_async(qca_net_t n, const uint8_t* noise, int L, int64_t shots
     set_error("qca_net_logits_async: bad arguments");
     return QCA_ERR_ARG;
   }
+  if (int rc = check_aligned(out_logits, 4, "out_logits")) return rc;
   if (shots == 0) return QCA_OK;
   return net_run(n, noise, L, shots, out_logits, nullptr, nullptr, (cudaStream_t)stream);
 }

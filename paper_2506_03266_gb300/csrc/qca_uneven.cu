@@ -66,6 +66,7 @@ struct qca_uneven_plan_s {
   std::vector<int> sizes;        // distinct L
   std::vector<int64_t> start;    // first list index of each size
   std::vector<int64_t> count;    // shots of each size
+  std::vector<int> bytewise;     // per size: some block of it starts off a 4-byte boundary
   int32_t* d_list = nullptr;     // shot indices grouped by size
   int64_t* d_offsets = nullptr;  // byte offset of each shot's block
   unsigned int* d_counters = nullptr;
@@ -132,6 +133,10 @@ int qca_uneven_plan_create(const int32_t* L_host, int64_t shots, int64_t* offset
   };
   for (int64_t s = 0; s < shots; ++s) ++cnt[cls(L_host[s])];
   p->count = cnt;
+  // an odd L before a shot moves its block off a 4-byte boundary
+  p->bytewise.assign(distinct.size(), 0);
+  for (int64_t s = 0; s < shots; ++s)
+    if (offs[s] & 3) p->bytewise[cls(L_host[s])] = 1;
   p->start.assign(distinct.size(), 0);
   for (size_t i = 1; i < distinct.size(); ++i) p->start[i] = p->start[i - 1] + cnt[i - 1];
   std::vector<int32_t> list(shots);
@@ -195,6 +200,9 @@ int qca_sample_errors_uneven_async(const int32_t* L_dev, const int64_t* offsets_
     set_error("qca_sample_errors_uneven_async: bad arguments");
     return QCA_ERR_ARG;
   }
+  if (int rc = check_aligned(L_dev, 4, "L_dev")) return rc;
+  if (int rc = check_aligned(offsets_dev, 8, "offsets_dev")) return rc;
+  if (int rc = check_aligned(thr_dev, 8, "thr_dev")) return rc;
   if (shots == 0) return QCA_OK;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -240,6 +248,7 @@ int qca_decode_uneven_async(qca_uneven_plan_t p, const uint8_t* errors, int max_
     a.shot_list = p->d_list + p->start[i];
     a.offsets = p->d_offsets;
     a.queue = p->d_counters + i;
+    a.bytewise = p->bytewise[i];
     rc = launch_decode(a, p->side[i]);
     if (rc) return rc;
     e = cudaEventRecord(p->join[i], p->side[i]);

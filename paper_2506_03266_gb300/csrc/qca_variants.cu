@@ -376,6 +376,7 @@ int variant_args(VariantArgs& a, const uint8_t* noise, int L, int64_t shots, int
     set_error("%s: NULL array pointer", who);
     return QCA_ERR_ARG;
   }
+  if (int rc = check_aligned(out_steps, 4, "out_steps (or out_ticks)")) return rc;
   a.in = noise;
   a.L = L;
   a.shots = shots;

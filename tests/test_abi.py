@@ -85,6 +85,10 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.qca_decode_batch_async(None, 16, 0, 10, 0, None, None, None, None, None) == 0
     assert lib.qca_sample_errors_async(16, 0, 0, 0.1, 0, None, None) == 0
     assert lib.qca_probe_peaks(None) == qca.QCA_ERR_ARG
+    # an int32 step array off a 4-byte boundary is refused before any launch
+    assert lib.qca_decode_batch_async(dummy, 16, 1, 10, 0, dummy, ctypes.c_void_p(18), dummy,
+                                      ctypes.byref(cfg), None) == qca.QCA_ERR_ARG
+    assert "aligned" in qca.last_error()
 
 
 def test_kernel_path_table(lib):
