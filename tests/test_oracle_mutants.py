@@ -41,6 +41,72 @@ MUTANTS = {
 }
 
 
+# Planted mistakes in the 1D oracle (Sec. 3.1) and in the open-boundary
+# variant (appendix on open boundary conditions), each caught by the pins of
+# tests/test_oracle_1d.py or tests/test_oracle_variants.py.
+MUTANTS_1D = {
+    "1d_empty_is_smallest": ("f[r] = -1; /* sgn(-inf + m^-) */", "f[r] = 1; /* sgn(-inf + m^-) */"),
+    "1d_force_sign": ("f[r] = (int8_t)((d > 0) - (d < 0));", "f[r] = (int8_t)((d < 0) - (d > 0));"),
+    "1d_feedback_xor_not_or": ("flips[r] = (t1 == 1 || t2 == 1) ? 1 : 0;",
+                               "flips[r] = ((t1 == 1) != (t2 == 1)) ? 1 : 0;"),
+    "1d_upstream_sign": ("const int u = w1(r - s, L);", "const int u = w1(r + s, L);"),
+    "1d_cap_saturates": ("if (nv > m_max) nv = 0;", "if (nv > m_max) nv = m_max;"),
+    "1d_syndrome_drops_term": ("sigma[r] = (links[w1(r - 1, L)] ^ links[r]) ? -1 : 1;",
+                               "sigma[r] = links[r] ? -1 : 1;"),
+}
+MUTANTS_OPEN = {
+    "open_boundary_not_a_source": ("nv = 1; /* the rough boundary sources messages into the bulk */",
+                                   "nv = 0; /* the rough boundary sources messages into the bulk */"),
+    "open_syndrome_counts_boundary": ("      if (!is_bdry(x, L)) {\n        if (qo_open_link_exists",
+                                      "      if (1) {\n        if (qo_open_link_exists"),
+    "open_y_links_on_rough_columns": ("return x >= 1 && x <= L - 2 && y <= L - 2;",
+                                      "return x <= L - 2 && y <= L - 2;"),
+    "open_feedback_xor_not_or": ("F[a * LL + r] = (t1 == 1 || t2 == 1) ? 1 : 0;",
+                                 "F[a * LL + r] = ((t1 == 1) != (t2 == 1)) ? 1 : 0;"),
+    "open_cone_drops_transverse": ("for (int j = -1; j <= 1; ++j) {\n            const int xx = ax ? ux : ux + j",
+                                   "for (int j = 0; j <= 0; ++j) {\n            const int xx = ax ? ux : ux + j"),
+}
+
+
+def _run_pins(fns):
+    """Call pin functions; return the names of those that failed."""
+    failed = []
+    for name, fn in fns:
+        try:
+            fn()
+        except AssertionError:
+            failed.append(name)
+    return failed
+
+
+def _battery_1d():
+    import test_oracle_1d as t
+    fns = [(f"messages_L{L}", (lambda L=L: t.test_messages_are_upstream_distances(L)))
+           for L in (5, 7)]
+    fns += [(n, getattr(t, n)) for n in (
+        "test_force_rule_against_the_prose", "test_feedback_or_and_direction",
+        "test_single_error_one_step", "test_gap_of_two_meets_in_the_middle",
+        "test_balanced_antipodal_pair_never_moves",
+        "test_long_way_round_is_a_logical_error_but_matches_the_majority",
+        "test_invariants_on_random_noise",
+        "test_gerrymander_flips_the_logical_state_in_about_035_L",
+        "test_gerrymander_under_the_message_cap_strands_a_pair")]
+    return _run_pins(fns)
+
+
+def _battery_open():
+    import test_oracle_variants as t
+    fns = [(f"open_messages_L{L}",
+            (lambda L=L: t.test_open_messages_are_distances_to_anyons_or_the_boundary(L)))
+           for L in (5, 6)]
+    fns += [(n, getattr(t, n)) for n in (
+        "test_open_link_set", "test_open_syndrome_ignores_missing_links_and_boundary",
+        "test_open_single_boundary_error_absorbed", "test_open_bulk_pair_fuses_in_one_step",
+        "test_open_boundary_to_boundary_string_is_a_logical_error",
+        "test_open_anyon_prefers_the_nearer_boundary", "test_open_invariants_on_random_noise")]
+    return _run_pins(fns)
+
+
 def _battery(mod):
     """Run the pins on the currently loaded oracle library; return the names of
     the pins that failed."""
@@ -85,33 +151,59 @@ def _battery(mod):
     return failed
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_planted_mistake(tmp_path, monkeypatch, name):
-    old, new = MUTANTS[name]
-    src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation anchor for {name} not unique/found"
+def _mutant_lib(tmp_path, target, old, new):
+    """Build the oracle with one source file text-edited; return the library."""
     d = tmp_path / "mut"
     d.mkdir()
     shutil.copy(HDR, d / "qca_oracle.h")
-    (d / "qca_oracle.c").write_text(src.replace(old, new))
+    for src in (SRC, SRC_1D, SRC_VAR):
+        text = open(src).read()
+        if src == target:
+            assert text.count(old) == 1, "mutation anchor not unique/found"
+            text = text.replace(old, new)
+        (d / os.path.basename(src)).write_text(text)
     lib = d / "libmut.so"
-    shutil.copy(SRC_1D, d / "qca_oracle_1d.c")
-    shutil.copy(SRC_VAR, d / "qca_oracle_variants.c")
-    subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", str(lib),
-                    str(d / "qca_oracle.c"), str(d / "qca_oracle_1d.c"),
-                    str(d / "qca_oracle_variants.c"), "-lm"], check=True)
+    subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", str(lib)] +
+                   [str(d / os.path.basename(src)) for src in (SRC, SRC_1D, SRC_VAR)] + ["-lm"],
+                   check=True)
+    return lib
+
+
+def _with_lib(monkeypatch, lib, battery):
     monkeypatch.setattr(oracle, "_lib", None)
     monkeypatch.setattr(oracle, "build", lambda force=False: str(lib))
     try:
-        failed = _battery(oracle)
+        return battery()
     finally:
         oracle._lib = None
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(tmp_path, monkeypatch, name):
+    lib = _mutant_lib(tmp_path, SRC, *MUTANTS[name])
+    failed = _with_lib(monkeypatch, lib, lambda: _battery(oracle))
     assert failed, f"mutant {name} survived every pin"
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_1D))
+def test_1d_pins_catch_planted_mistake(tmp_path, monkeypatch, name):
+    lib = _mutant_lib(tmp_path, SRC_1D, *MUTANTS_1D[name])
+    failed = _with_lib(monkeypatch, lib, _battery_1d)
+    assert failed, f"mutant {name} survived every 1D pin"
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_OPEN))
+def test_open_pins_catch_planted_mistake(tmp_path, monkeypatch, name):
+    lib = _mutant_lib(tmp_path, SRC_VAR, *MUTANTS_OPEN[name])
+    failed = _with_lib(monkeypatch, lib, _battery_open)
+    assert failed, f"mutant {name} survived every open-boundary pin"
 
 
 def test_unmutated_oracle_passes_battery(monkeypatch):
     monkeypatch.setattr(oracle, "_lib", None)
     try:
         assert _battery(oracle) == []
+        assert _battery_1d() == []
+        assert _battery_open() == []
     finally:
         oracle._lib = None

@@ -83,6 +83,17 @@ def test_open_single_boundary_error_absorbed():
     assert (steps, flag) == (1, 0)
 
 
+def test_open_bulk_pair_fuses_in_one_step():
+    # e_x(4, 4) on L = 9: anyons at (4, 4) and (5, 4), one link apart and three
+    # or more from the rough columns, so each hears its partner first and both
+    # mark the link between them, which flips once (the OR of the feedback)
+    L = 9
+    N = links(L, [(0, 4, 4)])
+    C, steps, flag = oracle.open_decode_shot(N)
+    np.testing.assert_array_equal(C, N)
+    assert (steps, flag) == (1, 0)
+
+
 def test_open_boundary_to_boundary_string_is_a_logical_error():
     L = 8
     N = links(L, [(0, x, 3) for x in range(L - 1)])
