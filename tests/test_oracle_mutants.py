@@ -67,6 +67,15 @@ MUTANTS_OPEN = {
                                    "for (int j = 0; j <= 0; ++j) {\n            const int xx = ax ? ux : ux + j"),
 }
 
+MUTANTS_DESYNC = {
+    "desync_move_at_message_rate": ("(uint64_t)(2 * i + 1)) < thr_move;",
+                                    "(uint64_t)(2 * i + 1)) < thr_msg;"),
+    "desync_every_site_updates": ("if (!fire)\n        for (int k = 0; k < 4; ++k)",
+                                  "if (0)\n        for (int k = 0; k < 4; ++k)"),
+    "desync_one_draw_for_both_clocks": ("(uint64_t)(2 * i + 1)) < thr_move;",
+                                        "(uint64_t)(2 * i)) < thr_move;"),
+}
+
 
 def _run_pins(fns):
     """Call pin functions; return the names of those that failed."""
@@ -105,6 +114,13 @@ def _battery_open():
         "test_open_boundary_to_boundary_string_is_a_logical_error",
         "test_open_anyon_prefers_the_nearer_boundary", "test_open_invariants_on_random_noise")]
     return _run_pins(fns)
+
+
+def _battery_desync():
+    import test_oracle_variants as t
+    return _run_pins([(n, getattr(t, n)) for n in (
+        "test_desync_full_rate_unit_speed_is_the_synchronous_decoder",
+        "test_desync_first_tick_fusion_rate", "test_desync_no_moves_never_decodes")])
 
 
 def _battery(mod):
@@ -199,11 +215,19 @@ def test_open_pins_catch_planted_mistake(tmp_path, monkeypatch, name):
     assert failed, f"mutant {name} survived every open-boundary pin"
 
 
+@pytest.mark.parametrize("name", sorted(MUTANTS_DESYNC))
+def test_desync_pins_catch_planted_mistake(tmp_path, monkeypatch, name):
+    lib = _mutant_lib(tmp_path, SRC_VAR, *MUTANTS_DESYNC[name])
+    failed = _with_lib(monkeypatch, lib, _battery_desync)
+    assert failed, f"mutant {name} survived every desynchronisation pin"
+
+
 def test_unmutated_oracle_passes_battery(monkeypatch):
     monkeypatch.setattr(oracle, "_lib", None)
     try:
         assert _battery(oracle) == []
         assert _battery_1d() == []
         assert _battery_open() == []
+        assert _battery_desync() == []
     finally:
         oracle._lib = None

@@ -143,6 +143,28 @@ def test_desync_full_rate_unit_speed_is_the_synchronous_decoder():
             assert (td, fd) == (ts, fs)
 
 
+def test_desync_first_tick_fusion_rate():
+    # one e_x error on the torus: its two anyons are adjacent.  From empty
+    # fields, an anyon's only nonzero field after its first message update
+    # points at its partner, so in the first tick it steps onto the link
+    # between them iff its message update fired (probability min(1, v q)) and
+    # its move fired (probability q), two independent draws.  The pair fuses
+    # in that tick iff at least one of the two did: 1 - (1 - min(1, v q) q)^2,
+    # 0.2256 at v = 3, q = 0.2
+    L, v, q, shots = 8, 3, 0.2, 4000
+    N = links(L, [(0, 3, 3)])
+    fused = 0
+    for s in range(shots):
+        C, t, f = oracle.desync_decode_shot(N, q, v=v, seed=1, shot=s, max_ticks=1)
+        assert t == 1
+        if f != 2:
+            np.testing.assert_array_equal(C, N)
+            fused += 1
+    want = 1 - (1 - min(1.0, v * q) * q) ** 2
+    sigma = np.sqrt(want * (1 - want) / shots)
+    assert abs(fused / shots - want) < 4 * sigma, (fused / shots, want)
+
+
 def test_desync_no_moves_never_decodes():
     N = oracle.sample_errors(8, 5, 0.1, seed=1)
     for n in N:
