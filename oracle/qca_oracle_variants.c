@@ -48,11 +48,6 @@
 
 #define QOV_TAG_DESYNC 0x444553594E43ULL /* "DESYNC" */
 
-static int vwrap(int i, int L) {
-  int r = i % L;
-  return r < 0 ? r + L : r;
-}
-
 /* ------------------------------------------------------------ open lattice */
 
 static int in_lat(int x, int y, int L) { return x >= 0 && x < L && y >= 0 && y < L; }
@@ -183,6 +178,7 @@ int qo_open_decode_shot(const uint8_t* N, int L, int v, int m_max, int max_steps
 int qo_desync_decode_shot(const uint8_t* N, int L, int v, int m_max, int max_ticks,
                           uint64_t thr_msg, uint64_t thr_move, uint64_t seed, int64_t shot,
                           uint8_t* C, int32_t* ticks) {
+  (void)v; /* the message rate v enters through thr_msg = floor(min(1, v q) 2^64) */
   const size_t LL = (size_t)L * L;
   int8_t* sigma = (int8_t*)malloc(LL);
   int32_t* m = (int32_t*)calloc(4 * LL, sizeof(int32_t));
