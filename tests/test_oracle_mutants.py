@@ -77,13 +77,42 @@ MUTANTS_DESYNC = {
 }
 
 
+# Planted mistakes in the pre-decoder's reference (oracle/net.py), each caught
+# by the pins of tests/test_net_oracle.py.
+NET_SRC = os.path.join(os.path.dirname(oracle.__file__), "net.py")
+MUTANTS_NET = {
+    "net_conv_tap_shift_sign": (
+        "shifted = np.roll(x, shift=(1 - ky, 1 - kx), axis=(1, 2))\n            out +=",
+        "shifted = np.roll(x, shift=(ky - 1, kx - 1), axis=(1, 2))\n            out +="),
+    "net_relu_on_logits": ("        x = conv3x3_circular(x, W, b)\n        if i < len(layers) - 1:",
+                           "        x = conv3x3_circular(x, W, b)\n        if True:"),
+    "net_bf16_truncates": ("u = ((u + 0x7FFF + lsb) >> 16) << 16", "u = (u >> 16) << 16"),
+    "net_labels_skip_partner_check": ("if anyon[yn, xn] and d[yn, xn] == back:",
+                                      "if anyon[yn, xn]:"),
+    "net_labels_y_directions_swapped": ("d[f[1] == -1] = 2\n    d[f[1] == 1] = 3",
+                                        "d[f[1] == -1] = 3\n    d[f[1] == 1] = 2"),
+    "net_pairing_roll_direction": ("C0[0] = ((prop == 0) & (np.roll(prop, -1, axis=1) == 1))",
+                                   "C0[0] = ((prop == 0) & (np.roll(prop, 1, axis=1) == 1))"),
+    "net_zero_logit_proposes": ("np.where(best > 0.0, k, 4)", "np.where(best >= 0.0, k, 4)"),
+    "net_e4m3_no_saturation": ("q = np.minimum(q, E4M3_MAX)", "q = q"),
+    "net_e4m3_no_subnormals": ("e = np.maximum(E - 1, -6)", "e = E - 1"),
+    "net_fp8_scale_per_tensor": (
+        "amax = np.max(np.abs(W.astype(np.float32)).reshape(W.shape[0], -1), axis=1)",
+        "amax = np.full(W.shape[0], np.max(np.abs(W.astype(np.float32))))"),
+    "net_label_smoothing_off": ("LABEL_SMOOTHING = 0.1", "LABEL_SMOOTHING = 0.0"),
+    "net_fifth_class_logit_one": ("zz = np.concatenate([z, np.zeros((1,) + z.shape[1:])])",
+                                  "zz = np.concatenate([z, np.ones((1,) + z.shape[1:])])"),
+}
+
+
 def _run_pins(fns):
-    """Call pin functions; return the names of those that failed."""
+    """Call pin functions; return the names of those that failed (a pin that
+    raises on a mutant catches it as surely as one whose assertion fails)."""
     failed = []
     for name, fn in fns:
         try:
             fn()
-        except AssertionError:
+        except Exception:
             failed.append(name)
     return failed
 
@@ -220,6 +249,36 @@ def test_desync_pins_catch_planted_mistake(tmp_path, monkeypatch, name):
     lib = _mutant_lib(tmp_path, SRC_VAR, *MUTANTS_DESYNC[name])
     failed = _with_lib(monkeypatch, lib, _battery_desync)
     assert failed, f"mutant {name} survived every desynchronisation pin"
+
+
+def _battery_net(mod, monkeypatch):
+    import test_net_oracle as t
+    monkeypatch.setattr(t, "onet", mod)
+    fns = [(f"single_tap_{ky}{kx}", (lambda ky=ky, kx=kx: t.test_conv_single_tap_is_a_shift(ky, kx)))
+           for ky, kx in ((0, 0), (2, 1))]
+    fns += [(n, getattr(t, n)) for n in sorted(dir(t))
+            if n.startswith("test_") and n != "test_conv_single_tap_is_a_shift"]
+    return _run_pins(fns)
+
+
+def _net_mutant(old, new):
+    import types
+    src = open(NET_SRC).read()
+    assert src.count(old) == 1, "mutation anchor not unique/found"
+    mod = types.ModuleType("net_mutant")
+    exec(compile(src.replace(old, new), NET_SRC, "exec"), mod.__dict__)
+    return mod
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_NET))
+def test_net_pins_catch_planted_mistake(monkeypatch, name):
+    failed = _battery_net(_net_mutant(*MUTANTS_NET[name]), monkeypatch)
+    assert failed, f"mutant {name} survived every pre-decoder pin"
+
+
+def test_unmutated_net_reference_passes_battery(monkeypatch):
+    import oracle.net
+    assert _battery_net(oracle.net, monkeypatch) == []
 
 
 def test_unmutated_oracle_passes_battery(monkeypatch):
