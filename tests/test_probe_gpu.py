@@ -27,12 +27,13 @@ def test_probe_shape_and_clock(peaks):
 
 @pytest.mark.parametrize("key", ["min16x2_per_clk_sm", "lop3_per_clk_sm", "min_u32_per_clk_sm"])
 def test_issue_rates_are_physical(peaks, key):
-    assert 8.0 < peaks[key] <= 128.0 * 1.02, peaks
+    assert 8.0 < peaks[key] <= 128.0 * 1.10, peaks
 
 
 def test_shared_memory_rate_is_physical(peaks):
-    # clock64 spans of the median CTA: about 1 % above the nominal 128 measured
-    assert 16.0 < peaks["smem_bytes_per_clk_sm"] <= 128.0 * 1.05, peaks
+    # clock64 spans of the median CTA read about 1 % above the nominal 128; the
+    # bound is for gross errors (hoisted loads read 498)
+    assert 16.0 < peaks["smem_bytes_per_clk_sm"] <= 128.0 * 1.10, peaks
 
 
 def test_per_second_rates_match_per_clock_rates(peaks):
