@@ -38,6 +38,16 @@ MUTANTS = {
     "cut_uses_wrong_plane": ("px ^= R[site(0, y, L)];", "px ^= R[LL + site(0, y, L)];"),
     "force_axis_swapped": ("f[(size_t)(a - 1) * LL + r] = (int8_t)force_sign(mp, mm);",
                            "f[(size_t)(2 - a) * LL + r] = (int8_t)force_sign(mp, mm);"),
+    "budget_off_by_one": ("if (t >= max_steps) {\n      flag = 2;",
+                          "if (t > max_steps) {\n      flag = 2;"),
+    "cap_off_by_one": ("if (nv > m_max) nv = 0;", "if (nv >= m_max) nv = 0;"),
+    "feedback_one_sided": ("(uint8_t)or_pm(t1, t2);", "(uint8_t)or_pm(t1, 0);"),
+    "anyon_test_centre_only": ("if (sigma[C[i]] == -1) anyon = 1;",
+                               "if (i == 1 && sigma[C[i]] == -1) anyon = 1;"),
+    "one_substep_short": ("for (int i = 0; i < v; ++i) {\n    qo_message_substep",
+                          "for (int i = 1; i < v; ++i) {\n    qo_message_substep"),
+    "correction_overwritten": ("for (size_t i = 0; i < 2 * LL; ++i) C[i] ^= F[i];",
+                               "for (size_t i = 0; i < 2 * LL; ++i) C[i] = F[i];"),
 }
 
 
