@@ -212,7 +212,9 @@ int qca_decode_uneven_async(qca_uneven_plan_t plan, const uint8_t* errors, int m
 /* ---- Tuning of the on-chip sweep (per lattice size, process-wide) --------
  * band_height: rows of one plane a warp segment sweeps (4, 8, 16 or 32; it sets
  * the threads per CTA and so the CTAs per SM); 0 = built-in heuristic (the band
- * whose warp count is nearest 4 up to L = 64, L / 8 above, at most 16).
+ * whose warp count is nearest 4 up to L = 64, L / 8 above, at most 16; where
+ * none of the four heights fits a size, another divisor of the CTA's rows of
+ * at least 4, by the same rule).
  * sparse_divisor: steps with at most L^2 / sparse_divisor anyons write the
  * anyon terms per anyon, busier steps compute them densely; 0 = the default,
  * 64 for the one-CTA kernel (L <= 128) and 256 for the two-CTA cluster.

@@ -822,7 +822,9 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
   // band height: 32, 16, 8 or 4 rows, dividing the CTA's rows, within the
   // thread limit; the one whose warp count is nearest a target (4 warps up to
   // L = 64, L / 8 above, at most 16; measured over band heights at L = 24 to
-  // 128), the taller band on a tie
+  // 128), the taller band on a tie.  The sweep takes any height of at least 4
+  // that divides the CTA's rows; other heights are used only where none of
+  // these four fits.
   const int max_warps = (CL == 1) ? 32 : 16;
   const int target = L <= 64 ? 4 : std::min(16, L / 8);
   int best_H = 0, best_d = 1 << 30;
@@ -835,6 +837,20 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
     if (d <= best_d) {
       best_d = d;
       best_H = H;
+    }
+  }
+  if (!best_H) {
+    // no power-of-two band fits (for example L = 100 or 160): any other
+    // divisor of the CTA's rows of at least 4, by the same rule
+    for (int H = 5; H <= g.rows_local; ++H) {
+      if (g.rows_local % H) continue;
+      const int warps = (4 * (g.rows_local / H) + g.spw - 1) / g.spw;
+      if (warps > max_warps) continue;
+      const int d = warps > target ? warps - target : target - warps;
+      if (d < best_d) {
+        best_d = d;
+        best_H = H;
+      }
     }
   }
   for (int H : {4, 8, 16, 32}) {  // a valid override wins

@@ -69,7 +69,8 @@ def test_small_config_full_parity():
     assert_same(gpu_decode(N, 4096), oracle.decode_batch(N, max_steps=4096), "L16")
 
 
-@pytest.mark.parametrize("L", [3, 4, 5, 6, 7, 8, 9, 12, 13, 20, 24, 31, 32, 36, 48, 64, 80, 96, 112])
+@pytest.mark.parametrize("L", [3, 4, 5, 6, 7, 8, 9, 12, 13, 20, 24, 31, 32, 36, 48, 64, 68, 80, 96,
+                               100, 112])
 @pytest.mark.parametrize("p", [0.03, 0.09])
 def test_parity_across_sizes(L, p):
     shots = 120 if L <= 32 else 40
@@ -78,9 +79,9 @@ def test_parity_across_sizes(L, p):
     assert_same(gpu_decode(N, ms), oracle.decode_batch(N, max_steps=ms), f"L{L} p{p}")
 
 
-# 160 and 200 have no on-chip band geometry in the two-CTA form and decode on
-# the generic sweep
-@pytest.mark.parametrize("L", [128, 160, 192, 200, 256])
+# 136, 160, 200 and 248 (like 68 and 100 above) sweep bands of a height other
+# than 4, 8, 16 or 32 rows (17, 20, 25 and 31)
+@pytest.mark.parametrize("L", [128, 136, 160, 192, 200, 248, 256])
 def test_parity_large_lattices_sampled(L):
     shots = 6
     N = oracle.sample_errors(L, shots, 0.06, seed=3)
