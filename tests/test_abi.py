@@ -91,6 +91,30 @@ def test_argument_errors_need_no_gpu(lib):
     assert "aligned" in qca.last_error()
 
 
+def test_band_geometry_covers_every_supported_size(lib):
+    # host-side geometry of the on-chip sweep (no GPU needed): every multiple
+    # of 4 up to 128 and of 8 up to 256 gets a band height of at least 4 rows
+    # that divides the CTA's rows (L up to 128, L / 2 in the two-CTA cluster)
+    for L in range(8, 257, 4):
+        qca.set_tuning(L, 0, 0)
+        path = qca.kernel_path(L)
+        if L > 128 and L % 8:
+            assert path == 0, L
+            continue
+        assert path == (1 if L <= 128 else 2), L
+        H, div, threads = qca.get_tuning(L)
+        rows = L if L <= 128 else L // 2
+        assert H >= 4 and rows % H == 0, (L, H)
+        assert threads % 32 == 0 and 0 < threads <= (1024 if L <= 128 else 512), (L, threads)
+    # sizes with a 4-, 8-, 16- or 32-row band keep the measured rule's choice
+    for L, H in [(8, 8), (12, 4), (24, 8), (32, 8), (48, 16), (56, 8), (64, 32), (96, 32),
+                 (128, 32), (192, 32), (256, 32)]:
+        assert qca.get_tuning(L)[0] == H, L
+    # and the others take another divisor of their rows
+    for L, H in [(68, 34), (100, 25), (136, 17), (160, 20), (200, 25), (248, 31)]:
+        assert qca.get_tuning(L)[0] == H, L
+
+
 def test_kernel_path_table(lib):
     assert qca.kernel_path(16) >= 0
     assert qca.kernel_path(256) >= 0
