@@ -115,6 +115,12 @@ def test_band_geometry_covers_every_supported_size(lib):
         assert qca.get_tuning(L)[0] == H, L
 
 
+def test_large_lattice_path_selection(lib):
+    # above 256: the large-lattice sweep for multiples of 128, else the generic one
+    for L in range(257, 1025):
+        assert qca.kernel_path(L) == (3 if L % 128 == 0 else 0), L
+
+
 def test_kernel_path_table(lib):
     assert qca.kernel_path(16) >= 0
     assert qca.kernel_path(256) >= 0
