@@ -54,7 +54,11 @@ extern "C" {
 #define QCA_MAX_L_1D 16384   /* longest ring of the 1D decoder                      */
 
 /* Decoder options.  Defaults (qca_default_config) are the paper's numerics
- * (Sec. 7: v = 3, deterministic rule) with an 8-bit message register. */
+ * (Sec. 7: v = 3, deterministic rule) with an 8-bit message register.
+ * tie_order and balance_rule select between readings of Eqs. blahdef /
+ * degbreak; the 2D torus entry points (uniform, uneven, syndrome, host, no
+ * allocation, net + automaton) take every value, the 1D, open-boundary and
+ * desynchronised decoders only the defaults (QCA_ERR_UNSUPPORTED otherwise). */
 typedef struct qca_config {
   int32_t v;             /* message sub-steps per time step (A^(v,D) = (A^(D))^v, Def.
                             Dd_msg_passing); supported: 1..8; default 3                     */
@@ -65,7 +69,26 @@ typedef struct qca_config {
                             limited-memory corollary of Sec. 5.1); default 0                 */
   int64_t shot_offset;   /* index of this batch's first shot in the random-move stream;
                             default 0                                                       */
+  int32_t tie_order;     /* argmin' of Eq. degbreak among equal-valued fields:
+                            QCA_TIE_LEX (default): smallest m, then the smallest s*a, i.e.
+                              (-,y) before (-,x) before (+,x) before (+,y);
+                            QCA_TIE_LITERAL: the printed offset s*a/(D+1) taken as is, i.e.
+                              the smallest integer key 3m + s*a, and where two keys are
+                              equal (m^{-y} = k+1 against m^{+x} = k, or m^{-x} = k+1
+                              against m^{+y} = k) the larger m                              */
+  int32_t balance_rule;  /* anyon whose chosen axis a is balanced (m^{+a} = m^{-a} > 0):
+                            QCA_BALANCE_STAY (default): no move (the deterministic rule of
+                              the paper's footnote on steady states, Sec. 5.3);
+                            QCA_BALANCE_RANDOM: one link along +a or -a, +a when the top bit
+                              of splitmix64(splitmix64(splitmix64(splitmix64(rng_seed ^
+                              0x42414C414E4345) ^ (shot_offset + shot)) ^ t) ^ (y L + x))
+                              is 0 (t = step index from 0)                                   */
 } qca_config;
+
+#define QCA_TIE_LEX 0
+#define QCA_TIE_LITERAL 1
+#define QCA_BALANCE_STAY 0
+#define QCA_BALANCE_RANDOM 1
 
 /* Fill *cfg with the defaults above.  Returns QCA_ERR_ARG if cfg is NULL. */
 int qca_default_config(qca_config* cfg);
@@ -122,6 +145,17 @@ int qca_decode_syndrome_batch_async(const uint8_t* sigma, int L, int64_t shots, 
                                     uint8_t* out_exhausted, const qca_config* cfg,
                                     void* stream);
 
+/* Synchronous companion of qca_decode_batch for pure syndromes (footnote of
+ * Def. plogandtdec: the decoder sees sigma only): the arguments of
+ * qca_decode_syndrome_batch_async without out_exhausted, options and stream;
+ * default options, legacy default stream, synchronises before returning.  An
+ * exhausted budget shows as out_steps[s] == max_steps with the syndrome left
+ * non-empty (use the async form's out_exhausted to tell it apart).  Errors
+ * as for the async form. */
+int qca_decode_syndrome_batch(const uint8_t* sigma, int L, int shots, int max_steps,
+                              uint64_t rng_seed, uint8_t* out_correction, int32_t* out_steps,
+                              uint8_t* out_cut_parity);
+
 /* End-to-end form of qca_decode_batch on HOST buffers (same layouts): copies
  * the noise to the device in chunks, decodes, and copies the correction, steps
  * and flags back, overlapping transfers with decoding.  Host buffers should be
@@ -150,11 +184,18 @@ int qca_decode_batch_host(const uint8_t* syndrome, int L, int64_t shots, int max
  * It always runs the generic sweep, so results are bit-identical to
  * qca_decode_batch.
  *
- *  - The first call on a device looks up the array's device address (with
- *    that device current); make that first call before any stream capture.
+ *  - The first call on a device (with that device current) looks up the
+ *    array's device address, which loads the array and the kernel onto the
+ *    device; a call with shots = 0 does this and nothing else.  Make that
+ *    first call while setting up, before reserving the device's memory for
+ *    other uses and before any stream capture.
  *  - Each shot needs 14 * L * L bytes (rounded up to 256) of the array; an L
  *    whose single shot does not fit is rejected with QCA_ERR_UNSUPPORTED.
- *    Larger batches simply take several passes over the array.
+ *    min(4 * SMs, floor(QCA_NOALLOC_SCRATCH_BYTES / that)) shots are decoded
+ *    at once, one CTA each, and larger batches take turns: 608 at once on a
+ *    152-SM GPU up to L = 44, 18 at L = 256, 8 at L = 384, and one at
+ *    L = 1024 (a single CTA then decodes the whole batch, shot after shot,
+ *    which is correct but slow).
  *  - Every call shares the one array, which keeps the last call's contents:
  *    calls that overlap on the GPU (for instance on two streams without an
  *    ordering between them) race and give wrong results.  Issue them on one

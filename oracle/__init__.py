@@ -34,6 +34,10 @@ _lib = None
 # message register (m_max = 255, reading R5).
 V_DEFAULT = 3
 M_MAX_DEFAULT = 255
+# Readings of Eq. degbreak (R3) and of a balanced axis (R4): 0 / 0 are the
+# defaults (lexicographic ties; a balanced anyon stays).
+TIE_LEX, TIE_LITERAL = 0, 1
+BALANCE_STAY, BALANCE_RANDOM = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -79,21 +83,25 @@ def _load():
         lib.qo_message_substep.restype = None
         lib.qo_forces.argtypes = [c_int, i8p, i32p, i8p]
         lib.qo_forces.restype = None
+        lib.qo_forces_rule.argtypes = [c_int, c_int, i8p, i32p, i8p, ctypes.c_void_p]
+        lib.qo_forces_rule.restype = None
         lib.qo_feedback_links.argtypes = [c_int, i8p, i8p, u8p]
         lib.qo_feedback_links.restype = None
-        lib.qo_step.argtypes = [c_int, c_int, c_int, c_u64, c_u64, c_i64, ctypes.c_int32,
-                                i8p, i32p, u8p, ctypes.c_void_p]
+        lib.qo_step.argtypes = [c_int, c_int, c_int, c_int, c_int, c_u64, c_u64, c_i64,
+                                ctypes.c_int32, i8p, i32p, u8p, ctypes.c_void_p]
         lib.qo_step.restype = c_int
         lib.qo_cut_parity.argtypes = [c_int, u8p, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
         lib.qo_cut_parity.restype = None
-        lib.qo_decode_shot.argtypes = [u8p, c_int, c_int, c_int, c_int, c_u64, c_u64, c_i64,
-                                       u8p, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, c_int]
+        lib.qo_decode_shot.argtypes = [u8p, c_int, c_int, c_int, c_int, c_int, c_int, c_u64,
+                                       c_u64, c_i64, u8p, ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.c_void_p, c_int]
         lib.qo_decode_shot.restype = c_int
-        lib.qo_decode_syndrome_shot.argtypes = [u8p, c_int, c_int, c_int, c_int, c_u64, c_u64,
-                                                c_i64, u8p, ctypes.POINTER(ctypes.c_int32), u8p]
+        lib.qo_decode_syndrome_shot.argtypes = [u8p, c_int, c_int, c_int, c_int, c_int, c_int,
+                                                c_u64, c_u64, c_i64, u8p,
+                                                ctypes.POINTER(ctypes.c_int32), u8p]
         lib.qo_decode_syndrome_shot.restype = c_int
-        lib.qo_decode_batch.argtypes = [u8p, c_int, c_i64, c_i64, c_int, c_int, c_int, c_u64,
-                                        c_u64, u8p, i32p, u8p]
+        lib.qo_decode_batch.argtypes = [u8p, c_int, c_i64, c_i64, c_int, c_int, c_int, c_int,
+                                        c_int, c_u64, c_u64, u8p, i32p, u8p]
         lib.qo_decode_batch.restype = None
         lib.qo1_sample_errors.argtypes = [c_int, c_i64, c_i64, c_u64, c_u64, u8p]
         lib.qo1_sample_errors.restype = None
@@ -177,14 +185,21 @@ def message_substep(sigma: np.ndarray, m: np.ndarray, m_max: int = M_MAX_DEFAULT
     return out
 
 
-def forces(sigma: np.ndarray, m: np.ndarray) -> np.ndarray:
-    """f^a_r, int8 [2][L][L] (Eqs. blahdef / degbreak)."""
+def forces(sigma: np.ndarray, m: np.ndarray, tie_order: int = TIE_LEX,
+           with_balanced: bool = False):
+    """f^a_r, int8 [2][L][L] (Eqs. blahdef / degbreak).  With with_balanced,
+    returns (f, balanced) where balanced (uint8 [L][L]) holds the chosen axis
+    (1 x, 2 y) of anyons whose chosen axis is balanced."""
     sigma = np.ascontiguousarray(sigma, dtype=np.int8)
     m = np.ascontiguousarray(m, dtype=np.int32)
     L = sigma.shape[0]
     f = np.zeros((2, L, L), dtype=np.int8)
-    _load().qo_forces(L, sigma, m, f)
-    return f
+    if tie_order == TIE_LEX and not with_balanced:
+        _load().qo_forces(L, sigma, m, f)
+        return f
+    bal = np.zeros((L, L), dtype=np.uint8)
+    _load().qo_forces_rule(L, tie_order, sigma, m, f, bal.ctypes.data_as(ctypes.c_void_p))
+    return (f, bal) if with_balanced else f
 
 
 def feedback_links(sigma: np.ndarray, f: np.ndarray) -> np.ndarray:
@@ -198,13 +213,13 @@ def feedback_links(sigma: np.ndarray, f: np.ndarray) -> np.ndarray:
 
 
 def step(sigma: np.ndarray, m: np.ndarray, C: np.ndarray, *, v: int = V_DEFAULT,
-         m_max: int = M_MAX_DEFAULT, move_thr: int = 0, seed: int = 0, shot: int = 0,
-         t: int = 0):
+         m_max: int = M_MAX_DEFAULT, tie_order: int = TIE_LEX, balance_rule: int = BALANCE_STAY,
+         move_thr: int = 0, seed: int = 0, shot: int = 0, t: int = 0):
     """One decoder step, in place on (sigma, m, C).  Returns (anyons, flips)."""
     L = sigma.shape[0]
     flips = np.zeros((2, L, L), dtype=np.uint8)
-    n = _load().qo_step(L, v, m_max, move_thr, seed, shot, t, sigma, m, C,
-                        flips.ctypes.data_as(ctypes.c_void_p))
+    n = _load().qo_step(L, v, m_max, tie_order, balance_rule, move_thr, seed, shot, t, sigma, m,
+                        C, flips.ctypes.data_as(ctypes.c_void_p))
     return n, flips
 
 
@@ -218,7 +233,8 @@ def cut_parity(R: np.ndarray):
 
 def decode_shot(N: np.ndarray, *, v: int = V_DEFAULT, m_max: int = M_MAX_DEFAULT,
                 max_steps: int = 4096, move_thr: int = 0, seed: int = 0, shot: int = 0,
-                trace: bool = False):
+                trace: bool = False, tie_order: int = TIE_LEX,
+                balance_rule: int = BALANCE_STAY):
     """Decode one noise realisation N (uint8 [2][L][L]).
 
     Returns (C, steps, flag) or, with trace=True, (C, steps, flag, anyons_per_step).
@@ -228,7 +244,8 @@ def decode_shot(N: np.ndarray, *, v: int = V_DEFAULT, m_max: int = M_MAX_DEFAULT
     C = np.zeros_like(N)
     steps = ctypes.c_int32()
     tr = np.zeros(max(1, max_steps), dtype=np.int32) if trace else None
-    flag = _load().qo_decode_shot(N, L, v, m_max, max_steps, move_thr, seed, shot, C,
+    flag = _load().qo_decode_shot(N, L, v, m_max, tie_order, balance_rule, max_steps, move_thr,
+                                  seed, shot, C,
                                   ctypes.byref(steps),
                                   tr.ctypes.data_as(ctypes.c_void_p) if trace else None,
                                   len(tr) if trace else 0)
@@ -238,20 +255,22 @@ def decode_shot(N: np.ndarray, *, v: int = V_DEFAULT, m_max: int = M_MAX_DEFAULT
 
 
 def decode_syndrome_shot(anyon: np.ndarray, *, v: int = V_DEFAULT, m_max: int = M_MAX_DEFAULT,
-                         max_steps: int = 4096, move_thr: int = 0, seed: int = 0, shot: int = 0):
+                         max_steps: int = 4096, move_thr: int = 0, seed: int = 0, shot: int = 0,
+                         tie_order: int = TIE_LEX, balance_rule: int = BALANCE_STAY):
     """Decode a pure syndrome (uint8 [L][L], 1 = anyon).  Returns (C, steps, flag, cut)."""
     anyon = np.ascontiguousarray(anyon, dtype=np.uint8)
     L = anyon.shape[-1]
     C = np.zeros((2, L, L), dtype=np.uint8)
     cut = np.zeros(2, dtype=np.uint8)
     steps = ctypes.c_int32()
-    flag = _load().qo_decode_syndrome_shot(anyon, L, v, m_max, max_steps, move_thr, seed, shot,
-                                           C, ctypes.byref(steps), cut)
+    flag = _load().qo_decode_syndrome_shot(anyon, L, v, m_max, tie_order, balance_rule, max_steps,
+                                           move_thr, seed, shot, C, ctypes.byref(steps), cut)
     return C, steps.value, flag, cut
 
 
 def decode_batch(N: np.ndarray, *, v: int = V_DEFAULT, m_max: int = M_MAX_DEFAULT,
-                 max_steps: int = 4096, move_thr: int = 0, seed: int = 0, shot0: int = 0):
+                 max_steps: int = 4096, move_thr: int = 0, seed: int = 0, shot0: int = 0,
+                 tie_order: int = TIE_LEX, balance_rule: int = BALANCE_STAY):
     """Decode uint8 [shots][2][L][L].  Returns (C, steps int32[shots], flags uint8[shots])."""
     N = np.ascontiguousarray(N, dtype=np.uint8)
     shots, L = N.shape[0], N.shape[-1]
@@ -259,8 +278,8 @@ def decode_batch(N: np.ndarray, *, v: int = V_DEFAULT, m_max: int = M_MAX_DEFAUL
     steps = np.zeros(shots, dtype=np.int32)
     flags = np.zeros(shots, dtype=np.uint8)
     if shots:
-        _load().qo_decode_batch(N, L, shot0, shots, v, m_max, max_steps, move_thr, seed, C, steps,
-                                flags)
+        _load().qo_decode_batch(N, L, shot0, shots, v, m_max, tie_order, balance_rule, max_steps,
+                                move_thr, seed, C, steps, flags)
     return C, steps, flags
 
 

@@ -15,8 +15,15 @@
  *   R2  Only anyon sites (sigma_r = -1) move; the feedback exponent is
  *       evaluated for anyon sites only (Sec. 3.1: "Consider an anyon at r").
  *   R3  argmin' of Eq. degbreak is read lexicographically: smallest m first,
- *       then the smallest s*a, i.e. the preference (-,y) > (-,x) > (+,x) > (+,y).
- *   R4  Balanced messages on the chosen axis give f = 0 (no move).
+ *       then the smallest s*a, i.e. the preference (-,y) > (-,x) > (+,x) > (+,y)
+ *       (tie order QO_TIE_LEX, the default).  The printed offset s*a/(D+1) is
+ *       kept as the option QO_TIE_LITERAL: smallest integer key 3m + s*a, and
+ *       where two keys are equal (m^{-y} = k+1 against m^{+x} = k, m^{-x} = k+1
+ *       against m^{+y} = k) the larger m.
+ *   R4  Balanced messages on the chosen axis give f = 0 (no move), the
+ *       deterministic rule (balance rule QO_BALANCE_STAY, the default).  The
+ *       option QO_BALANCE_RANDOM moves such an anyon one link along +a or -a,
+ *       chosen by a counter draw (footnote of Sec. 5.3 contrasts the two).
  *   R5  A message whose value would exceed m_max disappears (becomes 0).
  *   R6  C^(a)_r = the three sites r + j b^, j in {-1,0,1}, b != a.
  *   R7  "min + 1" in A^(D) runs over the nonzero neighbour values only.
@@ -38,6 +45,8 @@
  * key derivations.  (ASCII "NOISE" and "MOVE".) */
 #define QO_TAG_NOISE 0x4E4F495345ULL
 #define QO_TAG_MOVE 0x4D4F5645ULL
+/* ASCII "BALANCE": draws of the balanced-axis random rule (R4 option). */
+#define QO_TAG_BALANCE 0x42414C414E4345ULL
 
 uint64_t qo_splitmix64(uint64_t z) {
   /* Steele, Lea & Flood (2014), SplitMix64: golden-gamma increment followed by
@@ -190,12 +199,16 @@ static int force_sign(int32_t mplus, int32_t mminus) {
 
 /* Eqs. blahdef / degbreak:
  *   M_r = {(s, a) : m^{s a}_r > 0},
- *   (s_r, a_r) = argmin' over M_r of m^{s a}_r (ties: smaller s*a first, R3),
+ *   (s_r, a_r) = argmin' over M_r of m^{s a}_r (tie order R3),
  *   f^a_r = delta_{a, a_r} sgn(-m^{+a}_r + m^{-a}_r).
- * Evaluated at anyon sites only (R2); f = 0 elsewhere. */
-void qo_forces(int L, const int8_t* sigma, const int32_t* m, int8_t* f) {
+ * Evaluated at anyon sites only (R2); f = 0 elsewhere.  balanced (may be
+ * NULL) receives a_r (1 or 2) where the chosen axis is balanced (both fields
+ * nonzero and equal, so f = 0 by R4), else 0. */
+void qo_forces_rule(int L, int tie_order, const int8_t* sigma, const int32_t* m, int8_t* f,
+                    uint8_t* balanced) {
   const size_t LL = (size_t)L * L;
   memset(f, 0, 2 * LL);
+  if (balanced) memset(balanced, 0, LL);
   for (size_t r = 0; r < LL; ++r) {
     if (sigma[r] != -1) continue;
     int best_k = -1;
@@ -208,14 +221,25 @@ void qo_forces(int L, const int8_t* sigma, const int32_t* m, int8_t* f) {
       }
       int32_t bv = m[best_k * LL + r];
       int sa = field_s(k) * field_a(k), bsa = field_s(best_k) * field_a(best_k);
-      if (val < bv || (val == bv && sa < bsa)) best_k = k;
+      if (tie_order == QO_TIE_LITERAL) {
+        /* argmin of m + s a / (D + 1), D = 2, as the integer 3 m + s a */
+        int64_t key = 3 * (int64_t)val + sa, bkey = 3 * (int64_t)bv + bsa;
+        if (key < bkey || (key == bkey && val > bv)) best_k = k;
+      } else {
+        if (val < bv || (val == bv && sa < bsa)) best_k = k;
+      }
     }
     if (best_k < 0) continue; /* M_r empty: (s_r, a_r) = (0, 0) */
     int a = field_a(best_k);
     int32_t mp = m[field_index(+1, a) * LL + r];
     int32_t mm = m[field_index(-1, a) * LL + r];
     f[(size_t)(a - 1) * LL + r] = (int8_t)force_sign(mp, mm);
+    if (balanced && mp > 0 && mp == mm) balanced[r] = (uint8_t)a;
   }
+}
+
+void qo_forces(int L, const int8_t* sigma, const int32_t* m, int8_t* f) {
+  qo_forces_rule(L, QO_TIE_LEX, sigma, m, f, NULL);
 }
 
 /* The OR of Def. 1d_msg_passing: 1 iff x = 1 or y = 1. */
@@ -236,6 +260,22 @@ void qo_feedback_links(int L, const int8_t* sigma, const int8_t* f, uint8_t* fli
         int t2 = (sigma[rn] == -1) ? sigma[rn] * (-fa[rn]) : 0;
         flips[(size_t)(a - 1) * LL + r] = (uint8_t)or_pm(t1, t2);
       }
+  }
+}
+
+/* Balance rule QO_BALANCE_RANDOM (R4 option): an anyon whose chosen axis a
+ * is balanced moves one link along +a if the top bit of its draw
+ * u = sm(sm(sm(sm(seed ^ BALANCE) ^ shot) ^ t) ^ r) is 0, along -a if it is 1. */
+static void balanced_moves(int L, uint64_t seed, int64_t shot, int32_t t, const uint8_t* balanced,
+                           int8_t* f) {
+  const size_t LL = (size_t)L * L;
+  const uint64_t k1 = qo_splitmix64(qo_splitmix64(seed ^ QO_TAG_BALANCE) ^ (uint64_t)shot);
+  const uint64_t k2 = qo_splitmix64(k1 ^ (uint64_t)(uint32_t)t);
+  for (size_t r = 0; r < LL; ++r) {
+    if (!balanced[r]) continue;
+    uint64_t u = qo_splitmix64(k2 ^ (uint64_t)r);
+    /* an anyon moves +a^ when f^a = -1 and -a^ when f^a = +1 */
+    f[(size_t)(balanced[r] - 1) * LL + r] = (int8_t)((u >> 63) ? +1 : -1);
   }
 }
 
@@ -260,19 +300,22 @@ static void random_moves(int L, uint64_t move_thr, uint64_t seed, int64_t shot, 
   }
 }
 
-int qo_step(int L, int v, int m_max, uint64_t move_thr, uint64_t seed, int64_t shot,
-            int32_t t, int8_t* sigma, int32_t* m, uint8_t* C, uint8_t* flips_out) {
+int qo_step(int L, int v, int m_max, int tie_order, int balance_rule, uint64_t move_thr,
+            uint64_t seed, int64_t shot, int32_t t, int8_t* sigma, int32_t* m, uint8_t* C,
+            uint8_t* flips_out) {
   const size_t LL = (size_t)L * L;
   int32_t* tmp = (int32_t*)malloc(4 * LL * sizeof(int32_t));
   int8_t* f = (int8_t*)malloc(2 * LL);
   uint8_t* F = (uint8_t*)malloc(2 * LL);
+  uint8_t* bal = (uint8_t*)malloc(LL);
   /* 1. A^(v,D) = (A^(D))^v with sigma held fixed. */
   for (int i = 0; i < v; ++i) {
     qo_message_substep(L, m_max, sigma, m, tmp);
     memcpy(m, tmp, 4 * LL * sizeof(int32_t));
   }
   /* 2. feedback F(m, sigma) */
-  qo_forces(L, sigma, m, f);
+  qo_forces_rule(L, tie_order, sigma, m, f, bal);
+  if (balance_rule == QO_BALANCE_RANDOM) balanced_moves(L, seed, shot, t, bal, f);
   random_moves(L, move_thr, seed, shot, t, sigma, f);
   qo_feedback_links(L, sigma, f, F);
   /* 3. apply: C <- C xor F, sigma <- sigma * sigma_F */
@@ -286,6 +329,7 @@ int qo_step(int L, int v, int m_max, uint64_t move_thr, uint64_t seed, int64_t s
   }
   if (flips_out) memcpy(flips_out, F, 2 * LL);
   free(sigF);
+  free(bal);
   free(F);
   free(f);
   free(tmp);
@@ -301,9 +345,9 @@ void qo_cut_parity(int L, const uint8_t* R, int* wx, int* wy) {
   *wy = py;
 }
 
-static int run_decoder(int8_t* sigma, int L, int v, int m_max, int max_steps, uint64_t move_thr,
-                       uint64_t seed, int64_t shot, uint8_t* C, int32_t* steps,
-                       int32_t* anyon_trace, int trace_cap) {
+static int run_decoder(int8_t* sigma, int L, int v, int m_max, int tie_order, int balance_rule,
+                       int max_steps, uint64_t move_thr, uint64_t seed, int64_t shot, uint8_t* C,
+                       int32_t* steps, int32_t* anyon_trace, int trace_cap) {
   const size_t LL = (size_t)L * L;
   int32_t* m = (int32_t*)calloc(4 * LL, sizeof(int32_t)); /* m_0 = 0 everywhere */
   memset(C, 0, 2 * LL);
@@ -316,7 +360,8 @@ static int run_decoder(int8_t* sigma, int L, int v, int m_max, int max_steps, ui
       flag = 2;
       break;
     }
-    anyons = qo_step(L, v, m_max, move_thr, seed, shot, t, sigma, m, C, NULL);
+    anyons = qo_step(L, v, m_max, tie_order, balance_rule, move_thr, seed, shot, t, sigma, m, C,
+                     NULL);
     if (anyon_trace && t < trace_cap) anyon_trace[t] = anyons;
     ++t;
   }
@@ -325,14 +370,14 @@ static int run_decoder(int8_t* sigma, int L, int v, int m_max, int max_steps, ui
   return flag;
 }
 
-int qo_decode_shot(const uint8_t* N, int L, int v, int m_max, int max_steps, uint64_t move_thr,
-                   uint64_t seed, int64_t shot, uint8_t* C, int32_t* steps,
-                   int32_t* anyon_trace, int trace_cap) {
+int qo_decode_shot(const uint8_t* N, int L, int v, int m_max, int tie_order, int balance_rule,
+                   int max_steps, uint64_t move_thr, uint64_t seed, int64_t shot, uint8_t* C,
+                   int32_t* steps, int32_t* anyon_trace, int trace_cap) {
   const size_t LL = (size_t)L * L;
   int8_t* sigma = (int8_t*)malloc(LL);
   qo_syndrome(L, N, sigma);
-  int flag = run_decoder(sigma, L, v, m_max, max_steps, move_thr, seed, shot, C, steps,
-                         anyon_trace, trace_cap);
+  int flag = run_decoder(sigma, L, v, m_max, tie_order, balance_rule, max_steps, move_thr, seed,
+                         shot, C, steps, anyon_trace, trace_cap);
   free(sigma);
   if (flag == 2) return 2;
   /* Def. plogandtdec / Sec. 7.2: failure iff N xor C wraps a torus cycle. */
@@ -344,13 +389,14 @@ int qo_decode_shot(const uint8_t* N, int L, int v, int m_max, int max_steps, uin
   return (wx || wy) ? 1 : 0;
 }
 
-int qo_decode_syndrome_shot(const uint8_t* anyon, int L, int v, int m_max, int max_steps,
-                            uint64_t move_thr, uint64_t seed, int64_t shot, uint8_t* C,
-                            int32_t* steps, uint8_t* cut) {
+int qo_decode_syndrome_shot(const uint8_t* anyon, int L, int v, int m_max, int tie_order,
+                            int balance_rule, int max_steps, uint64_t move_thr, uint64_t seed,
+                            int64_t shot, uint8_t* C, int32_t* steps, uint8_t* cut) {
   const size_t LL = (size_t)L * L;
   int8_t* sigma = (int8_t*)malloc(LL);
   for (size_t r = 0; r < LL; ++r) sigma[r] = anyon[r] ? -1 : +1;
-  int flag = run_decoder(sigma, L, v, m_max, max_steps, move_thr, seed, shot, C, steps, NULL, 0);
+  int flag = run_decoder(sigma, L, v, m_max, tie_order, balance_rule, max_steps, move_thr, seed,
+                         shot, C, steps, NULL, 0);
   free(sigma);
   int wx, wy;
   qo_cut_parity(L, C, &wx, &wy);
@@ -360,12 +406,12 @@ int qo_decode_syndrome_shot(const uint8_t* anyon, int L, int v, int m_max, int m
 }
 
 void qo_decode_batch(const uint8_t* N, int L, int64_t shot0, int64_t shots, int v, int m_max,
-                     int max_steps, uint64_t move_thr, uint64_t seed, uint8_t* C, int32_t* steps,
-                     uint8_t* flags) {
+                     int tie_order, int balance_rule, int max_steps, uint64_t move_thr,
+                     uint64_t seed, uint8_t* C, int32_t* steps, uint8_t* flags) {
   const size_t E = 2 * (size_t)L * L;
   for (int64_t s = 0; s < shots; ++s) {
-    int fl = qo_decode_shot(N + s * E, L, v, m_max, max_steps, move_thr, seed, shot0 + s,
-                            C + s * E, steps + s, NULL, 0);
+    int fl = qo_decode_shot(N + s * E, L, v, m_max, tie_order, balance_rule, max_steps, move_thr,
+                            seed, shot0 + s, C + s * E, steps + s, NULL, 0);
     flags[s] = (uint8_t)fl;
   }
 }

@@ -40,18 +40,32 @@ void qo_syndrome(int L, const uint8_t* edges, int8_t* sigma);
 /* One application of the automaton rule A^(D), D = 2 (Def. Dd_msg_passing). */
 void qo_message_substep(int L, int m_max, const int8_t* sigma, const int32_t* m_in,
                         int32_t* m_out);
-/* Forces f^a_r of Eqs. blahdef / degbreak for every anyon site (0 elsewhere). */
+/* Tie orders of argmin' (Eq. degbreak) and rules for a balanced axis (see
+ * readings R3 and R4 in the .c file). */
+#define QO_TIE_LEX 0
+#define QO_TIE_LITERAL 1
+#define QO_BALANCE_STAY 0
+#define QO_BALANCE_RANDOM 1
+/* Forces f^a_r of Eqs. blahdef / degbreak for every anyon site (0 elsewhere),
+ * default tie order. */
 void qo_forces(int L, const int8_t* sigma, const int32_t* m, int8_t* f);
+/* Same with a tie order; balanced (may be NULL) receives the chosen axis (1 x,
+ * 2 y) at anyons whose chosen axis is balanced, else 0. */
+void qo_forces_rule(int L, int tie_order, const int8_t* sigma, const int32_t* m, int8_t* f,
+                    uint8_t* balanced);
 /* Links flipped by the feedback operator of Eq. ddfeedback: uint8 [2][L][L]. */
 void qo_feedback_links(int L, const int8_t* sigma, const int8_t* f, uint8_t* flips);
 /* One decoder time step in place: v message sub-steps, forces, feedback,
  * correction update C ^= F and syndrome update sigma <- sigma * sigma_F.
+ * tie_order / balance_rule select the readings of Eq. degbreak and of a
+ * balanced axis (QO_TIE_*, QO_BALANCE_*; 0 / 0 are the defaults).
  * move_thr > 0 enables the optional random-move rule (Sec. 5, corollary on
  * limited memory): an anyon whose draw is below move_thr moves in a random
  * direction instead.  flips_out (may be NULL) receives the flipped links.
  * Returns the number of anyons after the step. */
-int qo_step(int L, int v, int m_max, uint64_t move_thr, uint64_t seed, int64_t shot,
-            int32_t t, int8_t* sigma, int32_t* m, uint8_t* C, uint8_t* flips_out);
+int qo_step(int L, int v, int m_max, int tie_order, int balance_rule, uint64_t move_thr,
+            uint64_t seed, int64_t shot, int32_t t, int8_t* sigma, int32_t* m, uint8_t* C,
+            uint8_t* flips_out);
 /* Cut parities of a link set R: wx = XOR_y R.e_x((0,y)), wy = XOR_x R.e_y((x,0)). */
 void qo_cut_parity(int L, const uint8_t* R, int* wx, int* wy);
 /* Decode one shot whose noise realisation is N (Sec. 7; Def. plogandtdec).
@@ -59,19 +73,19 @@ void qo_cut_parity(int L, const uint8_t* R, int* wx, int* wy);
  * (0 success, 1 nontrivial homology of N xor C, 2 step budget exhausted).
  * anyon_trace (may be NULL) receives the anyon count after each step, at most
  * trace_cap entries.  Returns the flag. */
-int qo_decode_shot(const uint8_t* N, int L, int v, int m_max, int max_steps,
-                   uint64_t move_thr, uint64_t seed, int64_t shot,
+int qo_decode_shot(const uint8_t* N, int L, int v, int m_max, int tie_order, int balance_rule,
+                   int max_steps, uint64_t move_thr, uint64_t seed, int64_t shot,
                    uint8_t* C, int32_t* steps, int32_t* anyon_trace, int trace_cap);
 /* Same, from a pure syndrome (anyon indicator uint8 [L][L], 1 = anyon).
  * Writes C, steps, and the cut parities of C alone in cut[0] (wx) / cut[1]
  * (wy).  Returns 0 if the syndrome emptied, 2 if the budget ran out. */
-int qo_decode_syndrome_shot(const uint8_t* anyon, int L, int v, int m_max, int max_steps,
-                            uint64_t move_thr, uint64_t seed, int64_t shot,
-                            uint8_t* C, int32_t* steps, uint8_t* cut);
+int qo_decode_syndrome_shot(const uint8_t* anyon, int L, int v, int m_max, int tie_order,
+                            int balance_rule, int max_steps, uint64_t move_thr, uint64_t seed,
+                            int64_t shot, uint8_t* C, int32_t* steps, uint8_t* cut);
 /* Loop of qo_decode_shot over shots [shot0, shot0+shots); arrays are per shot. */
 void qo_decode_batch(const uint8_t* N, int L, int64_t shot0, int64_t shots, int v, int m_max,
-                     int max_steps, uint64_t move_thr, uint64_t seed,
-                     uint8_t* C, int32_t* steps, uint8_t* flags);
+                     int tie_order, int balance_rule, int max_steps, uint64_t move_thr,
+                     uint64_t seed, uint8_t* C, int32_t* steps, uint8_t* flags);
 
 /* ---- 1D repetition code (qca_oracle_1d.c; Sec. 3.1, Def. "message passing
  * automaton, 1D"; Sec. 7.1).  Ring of L sites, link <r, r+1> = bit r. */

@@ -39,7 +39,14 @@ class QcaError(RuntimeError):
 class QcaConfig(ctypes.Structure):
     """Mirror of struct qca_config (include/qca.h)."""
     _fields_ = [("v", ctypes.c_int32), ("m_max", ctypes.c_int32), ("p_move", ctypes.c_double),
-                ("shot_offset", ctypes.c_int64)]
+                ("shot_offset", ctypes.c_int64), ("tie_order", ctypes.c_int32),
+                ("balance_rule", ctypes.c_int32)]
+
+
+# Readings of Eq. degbreak and of a balanced axis (qca_config.tie_order /
+# balance_rule).
+TIE_LEX, TIE_LITERAL = 0, 1
+BALANCE_STAY, BALANCE_RANDOM = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -68,6 +75,7 @@ def lib():
             "qca_decode_batch_async": ([vp, i32, i64, i32, u64, vp, vp, vp, cfgp, vp], i32),
             "qca_decode_syndrome_batch_async": ([vp, i32, i64, i32, u64, vp, vp, vp, vp, cfgp, vp],
                                                 i32),
+            "qca_decode_syndrome_batch": ([vp, i32, i32, i32, u64, vp, vp, vp], i32),
             "qca_decode_batch_host": ([vp, i32, i64, i32, u64, vp, vp, vp, cfgp], i32),
             "qca_decode_batch_noalloc": ([vp, i32, i64, i32, u64, vp, vp, vp, cfgp, vp], i32),
             "qca_uneven_draw": ([i64, u64, vp, vp], i32),
@@ -129,10 +137,12 @@ def last_error() -> str:
 
 
 def make_config(v: int = 3, m_max: int = 255, p_move: float = 0.0,
-                shot_offset: int = 0) -> QcaConfig:
+                shot_offset: int = 0, tie_order: int = TIE_LEX,
+                balance_rule: int = BALANCE_STAY) -> QcaConfig:
     c = QcaConfig()
     _check(lib().qca_default_config(ctypes.byref(c)))
     c.v, c.m_max, c.p_move, c.shot_offset = v, m_max, p_move, shot_offset
+    c.tie_order, c.balance_rule = tie_order, balance_rule
     return c
 
 
@@ -255,7 +265,7 @@ def sample_errors(L: int, shots: int, p: float, seed: int, shot0: int = 0, out=N
 
 def decode_batch(errors, max_steps: int = 4096, rng_seed: int = 0, *, v: int = 3,
                  m_max: int = 255, p_move: float = 0.0, shot_offset: int = 0, out=None,
-                 stream=None):
+                 stream=None, tie_order: int = TIE_LEX, balance_rule: int = BALANCE_STAY):
     """Decode noise realisations uint8 [shots][2][L][L] (cuda).
 
     Returns (correction uint8 [shots][2][L][L], steps int32 [shots],
@@ -270,7 +280,7 @@ def decode_batch(errors, max_steps: int = 4096, rng_seed: int = 0, *, v: int = 3
         fail = torch.empty(shots, dtype=torch.uint8, device=errors.device)
     else:
         C, steps, fail = out
-    cfg = make_config(v, m_max, p_move, shot_offset)
+    cfg = make_config(v, m_max, p_move, shot_offset, tie_order, balance_rule)
     _check(lib().qca_decode_batch_async(
         ctypes.c_void_p(errors.data_ptr()), L, shots, max_steps, rng_seed & (2**64 - 1),
         ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(steps.data_ptr()),
@@ -280,7 +290,8 @@ def decode_batch(errors, max_steps: int = 4096, rng_seed: int = 0, *, v: int = 3
 
 def decode_syndrome_batch(sigma, max_steps: int = 4096, rng_seed: int = 0, *, v: int = 3,
                           m_max: int = 255, p_move: float = 0.0, shot_offset: int = 0,
-                          stream=None):
+                          stream=None, tie_order: int = TIE_LEX,
+                          balance_rule: int = BALANCE_STAY):
     """Decode anyon indicators uint8 [shots][L][L] (cuda, 1 = anyon).
 
     Returns (correction, steps, cut_parity uint8 [shots][2], exhausted uint8 [shots]).
@@ -292,7 +303,7 @@ def decode_syndrome_batch(sigma, max_steps: int = 4096, rng_seed: int = 0, *, v:
     steps = torch.empty(shots, dtype=torch.int32, device=sigma.device)
     cut = torch.empty((shots, 2), dtype=torch.uint8, device=sigma.device)
     exh = torch.empty(shots, dtype=torch.uint8, device=sigma.device)
-    cfg = make_config(v, m_max, p_move, shot_offset)
+    cfg = make_config(v, m_max, p_move, shot_offset, tie_order, balance_rule)
     _check(lib().qca_decode_syndrome_batch_async(
         ctypes.c_void_p(sigma.data_ptr()), L, shots, max_steps, rng_seed & (2**64 - 1),
         ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(steps.data_ptr()),
@@ -301,9 +312,26 @@ def decode_syndrome_batch(sigma, max_steps: int = 4096, rng_seed: int = 0, *, v:
     return C, steps, cut, exh
 
 
+def decode_syndrome_batch_sync(sigma, max_steps: int = 4096, rng_seed: int = 0):
+    """The synchronous companion entry point qca_decode_syndrome_batch (default
+    options, legacy default stream).  Returns (correction, steps, cut_parity)."""
+    torch = _torch()
+    shots, L = sigma.shape[0], sigma.shape[-1]
+    _dev_u8(torch, sigma, (shots, L, L), "sigma")
+    C = torch.empty((shots, 2, L, L), dtype=torch.uint8, device=sigma.device)
+    steps = torch.empty(shots, dtype=torch.int32, device=sigma.device)
+    cut = torch.empty((shots, 2), dtype=torch.uint8, device=sigma.device)
+    torch.cuda.current_stream().synchronize()  # sigma is ready before the legacy stream reads it
+    _check(lib().qca_decode_syndrome_batch(
+        ctypes.c_void_p(sigma.data_ptr()), L, shots, max_steps, rng_seed & (2**64 - 1),
+        ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(steps.data_ptr()),
+        ctypes.c_void_p(cut.data_ptr())))
+    return C, steps, cut
+
+
 def decode_batch_host(errors, max_steps: int = 4096, rng_seed: int = 0, *, v: int = 3,
                       m_max: int = 255, p_move: float = 0.0, correction: bool = True,
-                      out=None):
+                      out=None, tie_order: int = TIE_LEX, balance_rule: int = BALANCE_STAY):
     """End-to-end decode of HOST tensors (uint8 [shots][2][L][L], ideally pinned).
 
     Returns host tensors (correction or None, steps, logical_fail).
@@ -319,7 +347,7 @@ def decode_batch_host(errors, max_steps: int = 4096, rng_seed: int = 0, *, v: in
         fail = torch.empty(shots, dtype=torch.uint8, pin_memory=pin)
     else:
         C, steps, fail = out
-    cfg = make_config(v, m_max, p_move, 0)
+    cfg = make_config(v, m_max, p_move, 0, tie_order, balance_rule)
     _check(lib().qca_decode_batch_host(
         ctypes.c_void_p(errors.data_ptr()), L, shots, max_steps, rng_seed & (2**64 - 1),
         ctypes.c_void_p(C.data_ptr()) if C is not None else None,
@@ -329,7 +357,8 @@ def decode_batch_host(errors, max_steps: int = 4096, rng_seed: int = 0, *, v: in
 
 def decode_batch_noalloc(errors, out, max_steps: int = 4096, rng_seed: int = 0, *, v: int = 3,
                          m_max: int = 255, p_move: float = 0.0, shot_offset: int = 0,
-                         stream=None):
+                         stream=None, tie_order: int = TIE_LEX,
+                         balance_rule: int = BALANCE_STAY):
     """Decode through qca_decode_batch_noalloc: the library allocates nothing.
 
     For callers that cannot allocate device memory while decoding (see the
@@ -342,7 +371,7 @@ def decode_batch_noalloc(errors, out, max_steps: int = 4096, rng_seed: int = 0, 
     shots, L = errors.shape[0], errors.shape[-1]
     _dev_u8(torch, errors, (shots, 2, L, L), "errors")
     C, steps, fail = out
-    cfg = make_config(v, m_max, p_move, shot_offset)
+    cfg = make_config(v, m_max, p_move, shot_offset, tie_order, balance_rule)
     _check(lib().qca_decode_batch_noalloc(
         ctypes.c_void_p(errors.data_ptr()), L, shots, max_steps, rng_seed & (2**64 - 1),
         ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(steps.data_ptr()),
@@ -431,7 +460,8 @@ class UnevenPlan:
         return out
 
     def decode(self, errors, max_steps: int = 4096, rng_seed: int = 0, out=None, v: int = 3,
-               m_max: int = 255, p_move: float = 0.0, stream=None):
+               m_max: int = 255, p_move: float = 0.0, stream=None, tie_order: int = TIE_LEX,
+               balance_rule: int = BALANCE_STAY):
         """Decode packed noise; returns (correction packed uint8, steps, logical_fail)."""
         torch = _torch()
         if out is None:
@@ -440,7 +470,7 @@ class UnevenPlan:
             fail = torch.empty(self.shots, dtype=torch.uint8, device=errors.device)
         else:
             C, steps, fail = out
-        cfg = make_config(v, m_max, p_move, 0)
+        cfg = make_config(v, m_max, p_move, 0, tie_order, balance_rule)
         _check(lib().qca_decode_uneven_async(
             self.handle, ctypes.c_void_p(errors.data_ptr()), max_steps, rng_seed & (2**64 - 1),
             ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(steps.data_ptr()),
@@ -592,7 +622,8 @@ class Net:
 
     def decode_batch(self, errors, max_steps: int = 4096, rng_seed: int = 0, *, v: int = 3,
                      m_max: int = 255, p_move: float = 0.0, shot_offset: int = 0, out=None,
-                     scratch=None, stream=None):
+                     scratch=None, stream=None, tie_order: int = TIE_LEX,
+                     balance_rule: int = BALANCE_STAY):
         """Net + automaton: (correction, automaton steps, logical_fail)."""
         torch = _torch()
         shots, L = errors.shape[0], errors.shape[-1]
@@ -605,7 +636,7 @@ class Net:
             C, steps, fail = out
         if scratch is None:
             scratch = torch.empty_like(errors)
-        cfg = make_config(v, m_max, p_move, shot_offset)
+        cfg = make_config(v, m_max, p_move, shot_offset, tie_order, balance_rule)
         _check(lib().qca_net_decode_batch_async(
             self.handle, ctypes.c_void_p(errors.data_ptr()), L, shots, max_steps,
             rng_seed & (2**64 - 1), ctypes.c_void_p(C.data_ptr()),

@@ -222,6 +222,10 @@ int qca_decode_1d_batch_async(const uint8_t* noise, int L, int64_t shots, int ma
     set_error("qca_decode_1d_batch_async: v must be 1..8, m_max 1..255, p_move in [0, 1]");
     return QCA_ERR_UNSUPPORTED;
   }
+  if (c.tie_order != QCA_TIE_LEX || c.balance_rule != QCA_BALANCE_STAY) {
+    set_error("qca_decode_1d_batch_async: only the default tie order and balance rule");
+    return QCA_ERR_UNSUPPORTED;
+  }
   if (shots > 0 && (!noise || !out_correction || !out_steps || !out_flag)) {
     set_error("qca_decode_1d_batch_async: NULL array pointer");
     return QCA_ERR_ARG;

@@ -68,6 +68,15 @@ static int check_config(const qca_config* cfg, qca_config* out) {
     set_error("p_move must lie in [0, 1]");
     return QCA_ERR_ARG;
   }
+  if (out->tie_order != QCA_TIE_LEX && out->tie_order != QCA_TIE_LITERAL) {
+    set_error("tie_order = %d is neither QCA_TIE_LEX nor QCA_TIE_LITERAL", out->tie_order);
+    return QCA_ERR_ARG;
+  }
+  if (out->balance_rule != QCA_BALANCE_STAY && out->balance_rule != QCA_BALANCE_RANDOM) {
+    set_error("balance_rule = %d is neither QCA_BALANCE_STAY nor QCA_BALANCE_RANDOM",
+              out->balance_rule);
+    return QCA_ERR_ARG;
+  }
   return QCA_OK;
 }
 
@@ -121,6 +130,9 @@ static int fill_args(DecodeArgs& a, const uint8_t* in, int L, int64_t shots, int
   a.move_thr = prob_threshold(c.p_move);
   a.move_key = splitmix64(seed ^ kTagMove);
   a.shot_offset = c.shot_offset;
+  a.tie_order = c.tie_order;
+  a.balance_rule = c.balance_rule;
+  a.balance_key = splitmix64(seed ^ kTagBalance);
   return QCA_OK;
 }
 
@@ -139,7 +151,7 @@ using namespace qca;
 
 extern "C" {
 
-int qca_version(void) { return 100; }
+int qca_version(void) { return 101; }
 
 const char* qca_last_error(void) { return g_err; }
 
@@ -152,6 +164,8 @@ int qca_default_config(qca_config* cfg) {
   cfg->m_max = 255;
   cfg->p_move = 0.0;
   cfg->shot_offset = 0;
+  cfg->tie_order = QCA_TIE_LEX;
+  cfg->balance_rule = QCA_BALANCE_STAY;
   return QCA_OK;
 }
 
@@ -227,6 +241,16 @@ int qca_decode_syndrome_batch_async(const uint8_t* sigma, int L, int64_t shots, 
   return dispatch(a, (cudaStream_t)stream);
 }
 
+int qca_decode_syndrome_batch(const uint8_t* sigma, int L, int shots, int max_steps,
+                              uint64_t rng_seed, uint8_t* out_correction, int32_t* out_steps,
+                              uint8_t* out_cut_parity) {
+  int rc = qca_decode_syndrome_batch_async(sigma, L, shots, max_steps, rng_seed, out_correction,
+                                           out_steps, out_cut_parity, nullptr, nullptr,
+                                           nullptr);
+  if (rc) return rc;
+  return cuda_fail(cudaStreamSynchronize(nullptr), "qca_decode_syndrome_batch");
+}
+
 int qca_decode_batch_noalloc(const uint8_t* syndrome, int L, int64_t shots, int max_steps,
                              uint64_t rng_seed, uint8_t* out_correction, int32_t* out_steps,
                              uint8_t* out_logical_fail, const qca_config* cfg, void* stream) {
@@ -244,7 +268,8 @@ int qca_decode_batch_noalloc(const uint8_t* syndrome, int L, int64_t shots, int 
   a.out_C = out_correction;
   a.out_steps = out_steps;
   a.out_flag = out_logical_fail;
-  if (shots == 0) return QCA_OK;
+  // a call with no shots still runs the one-time set-up of the device (the
+  // scratch address and the kernel's module), so it can serve as the warm-up
   return launch_generic_noalloc(a, (cudaStream_t)stream);
 }
 

@@ -11,6 +11,8 @@ namespace qca {
 // Stream tags of the counter-based generator (ASCII "NOISE" and "MOVE").
 constexpr uint64_t kTagNoise = 0x4E4F495345ULL;
 constexpr uint64_t kTagMove = 0x4D4F5645ULL;
+// Stream tag of the balanced-axis random rule (ASCII "BALANCE").
+constexpr uint64_t kTagBalance = 0x42414C414E4345ULL;
 
 // SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014): golden-gamma
 // increment, then the variant-13 mix.  Device copy of the published definition.
@@ -32,6 +34,9 @@ struct DecodeArgs {
   uint64_t move_thr;       // random-move threshold (0 = deterministic rule)
   uint64_t move_key;       // splitmix64(seed ^ kTagMove)
   int64_t shot_offset;     // global index of shot 0 of this batch
+  int tie_order;           // QCA_TIE_LEX or QCA_TIE_LITERAL (Eq. degbreak)
+  int balance_rule;        // QCA_BALANCE_STAY or QCA_BALANCE_RANDOM
+  uint64_t balance_key;    // splitmix64(seed ^ kTagBalance)
   int from_sigma;          // input is a syndrome, not a noise realisation
   uint8_t* out_C;          // [shots][2][L][L]
   int32_t* out_steps;      // [shots]
@@ -74,6 +79,60 @@ int check_aligned(const void* p, size_t align, const char* what);
 __device__ __forceinline__ uint64_t move_step_key(uint64_t move_key, int64_t shot, int t) {
   uint64_t k1 = splitmix64(move_key ^ (uint64_t)shot);
   return splitmix64(k1 ^ (uint64_t)(uint32_t)t);
+}
+
+// Forces of Eqs. blahdef / degbreak at an anyon site from its four fields,
+// given in any encoding that is monotone in m and maps "no message" to 0xFF
+// (the on-chip kernels' offset encoding; (m - 1) & 0xFF for plain values).
+// The argmin' over the nonzero fields is lexicographic (smallest m, then the
+// smallest s*a: (-,y), (-,x), (+,x), (+,y)) or, with QCA_TIE_LITERAL, the
+// smallest integer key 3m + s*a with equal keys going to the larger m; the
+// key difference of two fields does not depend on the encoding's offset.  The
+// anyon then moves toward the smaller field of the chosen axis (m^{+a} comes
+// from the -a side, so it moves -a).
+// Returns 0 (no message), 1 +x, 2 -x, 3 +y, 4 -y, or 5 / 6 for a balanced
+// x / y axis (both fields set and equal), which the caller resolves with its
+// balance rule (no move, or balance_resolve).
+__host__ __device__ __forceinline__ int force_code(uint32_t wpx, uint32_t wmx, uint32_t wpy,
+                                                   uint32_t wmy, int tie_order) {
+  int ay;
+  if (tie_order == QCA_TIE_LITERAL) {
+    // composite key: (3w + s*a + 2) * 256 + (255 - w); equal keys cannot come
+    // from two fields, so the minimum is unique
+    int best = 0x7fffffff;
+    ay = -1;
+    const uint32_t w4[4] = {wpx, wmx, wpy, wmy};
+    const int sa4[4] = {1, -1, 2, -2};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (w4[k] == 0xFFu) continue;
+      const int key = ((3 * (int)w4[k] + sa4[k] + 2) << 8) + (255 - (int)w4[k]);
+      if (key < best) {
+        best = key;
+        ay = k >> 1;
+      }
+    }
+    if (ay < 0) return 0;
+  } else {
+    uint32_t best = wmy;
+    ay = 1;
+    if (wmx < best) { best = wmx; ay = 0; }
+    if (wpx < best) { best = wpx; ay = 0; }
+    if (wpy < best) { best = wpy; ay = 1; }
+    if (best == 0xFFu) return 0;
+  }
+  const uint32_t up = ay ? wpy : wpx, um = ay ? wmy : wmx;
+  if (up == um) return 5 + ay;
+  if (up < um) return ay ? 4 : 2;
+  return ay ? 3 : 1;
+}
+
+// Draw of the balanced-axis random rule for site r at step t of a shot:
+// splitmix64(splitmix64(splitmix64(balance_key ^ shot) ^ t) ^ r); its top bit
+// picks +a (0) or -a (1).
+__device__ __forceinline__ int balance_resolve(int code, uint64_t key_step, int64_t r) {
+  const uint64_t u = splitmix64(key_step ^ (uint64_t)r);
+  return (code == 5 ? 1 : 3) + (int)(u >> 63);
 }
 
 // Validate sizes and options and fill the common fields of a DecodeArgs.

@@ -159,24 +159,6 @@ __device__ __forceinline__ uint8_t* plane_ptr(uint8_t* planes, const FastGeom& g
   return Cluster<CL>::at(planes, owner) + ((size_t)(p * g.rows_local + lr)) * g.ls + c;
 }
 
-// Direction from the four fields in offset encoding (0xFF = no message):
-// smallest value wins, ties to the smaller s*a, i.e. (-,y), (-,x), (+,x), (+,y);
-// then move toward the smaller of the two fields of the chosen axis (m^{+a}
-// comes from the -a side), no move if they are equal.
-// Codes: 0 none, 1 +x, 2 -x, 3 +y, 4 -y.
-__device__ __forceinline__ int choose_dir(uint32_t wpx, uint32_t wmx, uint32_t wpy, uint32_t wmy) {
-  uint32_t best = wmy;
-  int axis_y = 1;
-  if (wmx < best) { best = wmx; axis_y = 0; }
-  if (wpx < best) { best = wpx; axis_y = 0; }
-  if (wpy < best) { best = wpy; axis_y = 1; }
-  if (best == 0xFFu) return 0;
-  const uint32_t up = axis_y ? wpy : wpx, um = axis_y ? wmy : wmx;
-  if (up == um) return 0;
-  if (up < um) return axis_y ? 4 : 2;
-  return axis_y ? 3 : 1;
-}
-
 // 4 bytes that are each 0 or 1 -> 4 bits (byte k -> bit k).
 __device__ __forceinline__ uint32_t nibble_of(uint32_t w) { return (w * 0x01020408u) >> 24; }
 // 4 bytes -> 4 bits "byte is nonzero".
@@ -676,11 +658,15 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
       Cluster<CL>::sync();
       snapshot();  // halo rows for the next step
       // ================= 2. forces and feedback for the anyons of this CTA's rows
-      uint64_t kstep = 0;
+      uint64_t kstep = 0, kbal = 0;
       if (a.move_thr) kstep = move_step_key(a.move_key, a.shot_offset + shot, t);
+      if (a.balance_rule) kbal = move_step_key(a.balance_key, a.shot_offset + shot, t);
       auto decide = [&](int x, int y) -> int {
-        int dir = choose_dir(*plane_ptr<CL>(planes, g, 0, y, x), *plane_ptr<CL>(planes, g, 1, y, x),
-                             *plane_ptr<CL>(planes, g, 2, x, y), *plane_ptr<CL>(planes, g, 3, x, y));
+        // Eqs. blahdef / degbreak on the offset-encoded fields (0xFF = none)
+        int dir = force_code(*plane_ptr<CL>(planes, g, 0, y, x), *plane_ptr<CL>(planes, g, 1, y, x),
+                             *plane_ptr<CL>(planes, g, 2, x, y), *plane_ptr<CL>(planes, g, 3, x, y),
+                             a.tie_order);
+        if (dir >= 5) dir = a.balance_rule ? balance_resolve(dir, kbal, y * L + x) : 0;
         if (a.move_thr) {
           const uint64_t u = splitmix64(kstep ^ (uint64_t)(y * L + x));
           if (u < a.move_thr) dir = 1 + (int)(splitmix64(u) >> 62);
@@ -841,7 +827,9 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
   }
   if (!best_H) {
     // no power-of-two band fits (for example L = 100 or 160): any other
-    // divisor of the CTA's rows of at least 4, by the same rule
+    // divisor of the CTA's rows of at least 4 whose warp count is nearest the
+    // target, the shorter band on a tie (heights are tried in increasing
+    // order and only a strictly nearer count replaces the choice)
     for (int H = 5; H <= g.rows_local; ++H) {
       if (g.rows_local % H) continue;
       const int warps = (4 * (g.rows_local / H) + g.spw - 1) / g.spw;

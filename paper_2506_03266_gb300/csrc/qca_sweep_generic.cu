@@ -23,31 +23,8 @@ constexpr int kThreads = 512;
 
 __device__ __forceinline__ int wrapi(int i, int L) { return i < 0 ? i + L : (i >= L ? i - L : i); }
 
-// Direction codes: 0 none, 1 +x, 2 -x, 3 +y, 4 -y.
-// Forces of Eqs. blahdef/degbreak with 0 read as "no message" (+infinity):
-// smallest nonzero field wins, ties to the smaller s*a ((-,y) < (-,x) < (+,x) <
-// (+,y)); the anyon then moves toward the smaller of m^{+a}, m^{-a} (m^{+a}
-// comes from the -a side), and stays if they are equal.
-__device__ __forceinline__ int choose_direction(int mpx, int mmx, int mpy, int mmy) {
-  // candidates in preference order for equal values
-  const int val[4] = {mmy, mmx, mpx, mpy};
-  int best = -1, bv = 0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    if (val[i] > 0 && (best < 0 || val[i] < bv)) {
-      best = i;
-      bv = val[i];
-    }
-  }
-  if (best < 0) return 0;
-  const bool yaxis = (best == 0 || best == 3);
-  int mp = yaxis ? mpy : mpx, mm = yaxis ? mmy : mmx;
-  const unsigned up = mp ? (unsigned)mp : 0x7fffffffu;
-  const unsigned um = mm ? (unsigned)mm : 0x7fffffffu;
-  if (up == um) return 0;
-  if (up < um) return yaxis ? 4 : 2;  // message from the -a side: move -a
-  return yaxis ? 3 : 1;
-}
+// Plain field value (0 = no message) in the encoding force_code takes.
+__device__ __forceinline__ uint32_t enc(int m) { return (uint32_t)(m - 1) & 0xFFu; }
 
 __global__ void __launch_bounds__(kThreads) sweep_generic_kernel(DecodeArgs a, uint8_t* ws,
                                                                  size_t slot_bytes) {
@@ -129,12 +106,16 @@ __global__ void __launch_bounds__(kThreads) sweep_generic_kernel(DecodeArgs a, u
         mnxt = tmp;
       }
       // ---- forces at anyon sites
-      uint64_t kstep = 0;
+      uint64_t kstep = 0, kbal = 0;
       if (a.move_thr) kstep = move_step_key(a.move_key, a.shot_offset + shot, t);
+      if (a.balance_rule) kbal = move_step_key(a.balance_key, a.shot_offset + shot, t);
       for (int i = threadIdx.x; i < LL; i += blockDim.x) {
         int d = 0;
         if (sig[i]) {
-          d = choose_direction(mcur[i], mcur[LL + i], mcur[2 * LL + i], mcur[3 * LL + i]);
+          // Eqs. blahdef / degbreak; codes 1 +x, 2 -x, 3 +y, 4 -y, 5 / 6 balanced
+          d = force_code(enc(mcur[i]), enc(mcur[LL + i]), enc(mcur[2 * LL + i]),
+                         enc(mcur[3 * LL + i]), a.tie_order);
+          if (d >= 5) d = a.balance_rule ? balance_resolve(d, kbal, i) : 0;
           if (a.move_thr) {
             const uint64_t u = splitmix64(kstep ^ (uint64_t)i);
             if (u < a.move_thr) d = 1 + (int)(splitmix64(u) >> 62);
@@ -311,12 +292,16 @@ int launch_generic_noalloc(const DecodeArgs& a, cudaStream_t stream) {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
       // In host code the array's name only stands in for it; the kernel needs
-      // the device address, valid on the current device.
-      e = cudaGetSymbolAddress(reinterpret_cast<void**>(&g_noalloc_ptr[dev]), g_noalloc_scratch);
-      if (e != cudaSuccess) {
-        g_noalloc_ptr[dev] = nullptr;
-        return cuda_fail(e, "cudaGetSymbolAddress of the no-allocation scratch");
-      }
+      // the device address, valid on the current device.  The lookup loads the
+      // module that holds the array; querying the kernel's attributes loads
+      // the kernel too, so that a later call only launches.
+      uint8_t* ptr = nullptr;
+      e = cudaGetSymbolAddress(reinterpret_cast<void**>(&ptr), g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the no-allocation scratch");
+      cudaFuncAttributes fa;
+      e = cudaFuncGetAttributes(&fa, sweep_generic_kernel);
+      if (e != cudaSuccess) return cuda_fail(e, "loading the no-allocation sweep kernel");
+      g_noalloc_ptr[dev] = ptr;
     }
     scratch = g_noalloc_ptr[dev];
   }

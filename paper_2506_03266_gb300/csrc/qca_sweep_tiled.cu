@@ -136,21 +136,6 @@ __device__ __forceinline__ uint32_t nib_mask(uint32_t nib) {
 }
 __device__ __forceinline__ uint32_t nibble_of_bytes(uint32_t w) { return (w * 0x01020408u) >> 24; }
 
-// Direction from the four fields (offset encoding): readings R1-R4.
-// Codes: 0 none, 1 +x, 2 -x, 3 +y, 4 -y.
-__device__ __forceinline__ int tiled_dir(uint32_t wpx, uint32_t wmx, uint32_t wpy, uint32_t wmy) {
-  uint32_t best = wmy;
-  int axis_y = 1;
-  if (wmx < best) { best = wmx; axis_y = 0; }
-  if (wpx < best) { best = wpx; axis_y = 0; }
-  if (wpy < best) { best = wpy; axis_y = 1; }
-  if (best == 0xFFu) return 0;
-  const uint32_t up = axis_y ? wpy : wpx, um = axis_y ? wmy : wmx;
-  if (up == um) return 0;
-  if (up < um) return axis_y ? 4 : 2;
-  return axis_y ? 3 : 1;
-}
-
 template <class T>
 __device__ __forceinline__ T* rank_ptr(T* p, int r) {
   return cg::this_cluster().map_shared_rank(p, (unsigned)r);
@@ -443,8 +428,9 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
         const uint8_t* Ppy = plane(dst, 2);
         const uint8_t* Pmy = plane(dst, 3);
         const uint32_t* Sx = sigf(0);
-        uint64_t kstep = 0;
+        uint64_t kstep = 0, kbal = 0;
         if (a.move_thr) kstep = move_step_key(a.move_key, a.shot_offset + shot, t);
+        if (a.balance_rule) kbal = move_step_key(a.balance_key, a.shot_offset + shot, t);
         for (int rr = warp; rr < RL; rr += nw) {
           const int y = r0 + rr, wq = lane;
           if (wq >= W) continue;
@@ -474,7 +460,10 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
             for (int k = 0; k < 4; ++k) {
               if (xs[k] < 0) continue;
               const int x = xs[k];
-              int dir = tiled_dir(f[k][0], f[k][1], f[k][2], f[k][3]);
+              // Eqs. blahdef / degbreak on the offset-encoded fields (0xFF = none)
+              int dir = force_code(f[k][0], f[k][1], f[k][2], f[k][3], a.tie_order);
+              if (dir >= 5)
+                dir = a.balance_rule ? balance_resolve(dir, kbal, (int64_t)y * L + x) : 0;
               if (a.move_thr) {
                 const uint64_t u = splitmix64(kstep ^ (uint64_t)((int64_t)y * L + x));
                 if (u < a.move_thr) dir = 1 + (int)(splitmix64(u) >> 62);

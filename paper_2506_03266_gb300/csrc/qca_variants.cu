@@ -372,6 +372,10 @@ int variant_args(VariantArgs& a, const uint8_t* noise, int L, int64_t shots, int
     set_error("%s: v must be 1..8 and m_max 1..255", who);
     return QCA_ERR_UNSUPPORTED;
   }
+  if (c.tie_order != QCA_TIE_LEX || c.balance_rule != QCA_BALANCE_STAY) {
+    set_error("%s: only the default tie order and balance rule", who);
+    return QCA_ERR_UNSUPPORTED;
+  }
   if (shots > 0 && (!noise || !out_C || !out_steps || !out_flag)) {
     set_error("%s: NULL array pointer", who);
     return QCA_ERR_ARG;

@@ -19,3 +19,11 @@ def oracle_mod():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _close_oracle_pool():
+    yield
+    import oracle_pool
+
+    oracle_pool.close()

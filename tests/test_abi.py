@@ -32,7 +32,8 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ["qca_decode_batch", "qca_decode_batch_async", "qca_sample_errors",
-                 "qca_decode_syndrome_batch_async", "qca_decode_batch_host", "qca_last_error",
+                 "qca_decode_syndrome_batch", "qca_decode_syndrome_batch_async",
+                 "qca_decode_batch_host", "qca_last_error",
                  "qca_free_workspace", "qca_default_config"]:
         assert must in names
 
@@ -47,6 +48,8 @@ def test_version_and_defaults(lib):
     c = qca.QcaConfig()
     assert lib.qca_default_config(ctypes.byref(c)) == 0
     assert (c.v, c.m_max, c.p_move, c.shot_offset) == (3, 255, 0.0, 0)
+    assert (c.tie_order, c.balance_rule) == (qca.TIE_LEX, qca.BALANCE_STAY)
+    assert ctypes.sizeof(qca.QcaConfig) == 32  # the struct layout of include/qca.h
     assert lib.qca_default_config(None) == qca.QCA_ERR_ARG
 
 
@@ -81,6 +84,11 @@ def test_argument_errors_need_no_gpu(lib):
     bad = qca.make_config(p_move=-0.1)
     assert lib.qca_decode_batch_async(dummy, 16, 1, 10, 0, dummy, dummy, dummy,
                                       ctypes.byref(bad), None) == qca.QCA_ERR_ARG
+    for bad in (qca.make_config(tie_order=2), qca.make_config(balance_rule=-1)):
+        assert lib.qca_decode_batch_async(dummy, 16, 1, 10, 0, dummy, dummy, dummy,
+                                          ctypes.byref(bad), None) == qca.QCA_ERR_ARG
+    assert lib.qca_decode_syndrome_batch(None, 16, 1, 10, 0, dummy, dummy, dummy) == \
+        qca.QCA_ERR_ARG
     # zero shots: nothing to do, NULL allowed, no device call
     assert lib.qca_decode_batch_async(None, 16, 0, 10, 0, None, None, None, None, None) == 0
     assert lib.qca_sample_errors_async(16, 0, 0, 0.1, 0, None, None) == 0

@@ -88,6 +88,20 @@ def test_parity_large_lattices_sampled(L):
     assert_same(gpu_decode(N, 300), oracle.decode_batch(N, max_steps=300), f"L{L}")
 
 
+@pytest.mark.parametrize("p", [0.08, 0.09])
+def test_cluster_path_near_and_above_threshold(p):
+    """The two-CTA cluster (L = 256) against the oracle where decoding is hard:
+    16 shots at p = 0.08 and 0.09, budget 300; among them shots that exhaust
+    the budget (flag 2), a case the bench workload never reaches."""
+    import oracle_pool
+    L = 256
+    assert qca.kernel_path(L) == 2
+    N = oracle.sample_errors(L, 16, p, seed=21)
+    cpu = oracle_pool.decode_many(N, max_steps=300)
+    assert (cpu[2] == 2).any() and (cpu[2] == 1).any()
+    assert_same(gpu_decode(N, 300), cpu, f"L256 p{p}")
+
+
 @pytest.mark.parametrize("v,m_max", [(1, 255), (2, 255), (4, 255), (3, 7), (3, 40), (5, 20)])
 def test_parity_options(v, m_max):
     L = 20

@@ -149,6 +149,24 @@ def test_single_anyon_message_values(oracle_mod):
 
 # ------------------------------------------------------- forces, feedback --
 
+def _printed_key_link(mpx, mmx, mpy, mmy):
+    """Expected move under the option that takes Eq. degbreak as printed: the
+    axis of argmin over the nonzero fields of m + s*a/(D+1), D = 2, evaluated
+    in exact rationals; where two keys are equal the larger m wins.  Then, as
+    in the prose, the anyon moves toward the smaller field of that axis (an
+    empty field counts as +infinity) and stays when the two are equal."""
+    from fractions import Fraction
+    vals = {(1, 1): mpx, (-1, 1): mmx, (1, 2): mpy, (-1, 2): mmy}
+    cands = [(v + Fraction(s * a, 3), -v, (s, a)) for (s, a), v in vals.items() if v > 0]
+    if not cands:
+        return None
+    _, _, (s, a) = min(cands)
+    mp, mm = vals[(1, a)] or 10**9, vals[(-1, a)] or 10**9
+    if mp == mm:
+        return None
+    return (a, -1) if mp < mm else (a, +1)
+
+
 def _prose_link(mpx, mmx, mpy, mmy):
     """Expected move of an anyon from the prose of Sec. 1 and Sec. 3.1/3.2: it
     moves one link toward the source of its smallest nonzero message (m^{+a}
@@ -166,21 +184,26 @@ def _prose_link(mpx, mmx, mpy, mmy):
     return (a, -s)
 
 
-def test_forces_and_feedback_follow_prose(oracle_mod):
+@pytest.mark.parametrize("tie_order", [0, 1])
+def test_forces_and_feedback_follow_prose(oracle_mod, tie_order):
+    """Tie order 0 against the prose reading; tie order 1 against the printed
+    key of Eq. degbreak.  Fields 0..4 cover every exact key tie (values one
+    apart) and every plain tie."""
     L, x0, y0 = 5, 2, 2
     sigma = np.ones((L, L), np.int8)
     sigma[y0, x0] = -1
-    vals = range(0, 4)
+    vals = range(0, 5)
+    expect = _prose_link if tie_order == 0 else _printed_key_link
     for mpx in vals:
         for mmx in vals:
             for mpy in vals:
                 for mmy in vals:
                     m = np.zeros((4, L, L), np.int32)
                     m[:, y0, x0] = (mpx, mmx, mpy, mmy)
-                    f = oracle_mod.forces(sigma, m)
+                    f = oracle_mod.forces(sigma, m, tie_order=tie_order)
                     F = oracle_mod.feedback_links(sigma, f)
                     want = np.zeros((2, L, L), np.uint8)
-                    mv = _prose_link(mpx, mmx, mpy, mmy)
+                    mv = expect(mpx, mmx, mpy, mmy)
                     if mv is not None:
                         a, d = mv
                         if a == 1:
@@ -216,13 +239,55 @@ def test_feedback_or_flips_shared_link_once(oracle_mod):
 
 # ------------------------------------------------------- worked examples --
 
-@pytest.mark.parametrize("case", CASES, ids=[c["name"] for c in CASES])
-def test_golden_worked_examples(oracle_mod, case):
+CASE_TIES = [(c, t) for c in CASES for t in c["tie_orders"]]
+
+
+@pytest.mark.parametrize("case,tie_order", CASE_TIES,
+                         ids=[f"{c['name']}-tie{t}" for c, t in CASE_TIES])
+def test_golden_worked_examples(oracle_mod, case, tie_order):
     C, steps, flag = oracle_mod.decode_shot(case["N"], m_max=case["m_max"],
-                                            max_steps=case["max_steps"])
+                                            max_steps=case["max_steps"], tie_order=tie_order)
     assert steps == case["steps"]
     assert flag == case["flag"]
     np.testing.assert_array_equal(C, case["C"])
+
+
+def test_tie_golden_cases_discriminate(oracle_mod):
+    """Each case written for one tie order fails under the other, so the two
+    options really differ on them."""
+    for c in CASES:
+        if len(c["tie_orders"]) != 1:
+            continue
+        other = 1 - c["tie_orders"][0]
+        C, steps, flag = oracle_mod.decode_shot(c["N"], m_max=c["m_max"],
+                                                max_steps=c["max_steps"], tie_order=other)
+        assert not np.array_equal(C, c["C"]), c["name"]
+
+
+def test_balanced_random_rule(oracle_mod):
+    """Balance rule 1 (R4 option): the antipodal pair of an even torus, a
+    steady state of the deterministic rule, gets moving.  Anyons at (0,0) and
+    (3,0) on L = 6 hear m^{+x} = m^{-x} = 3 after the first step (wrap), so
+    their axis x is balanced; each moves +x when the top bit of its draw
+    sm(sm(sm(sm(seed ^ BALANCE) ^ shot) ^ t) ^ r) is 0, else -x."""
+    L = 6
+    N = np.zeros((2, L, L), np.uint8)
+    N[0, 0, 0:3] = 1  # e_x((0,0)), e_x((1,0)), e_x((2,0)): anyons at (0,0), (3,0)
+    sm = oracle_mod.splitmix64
+    seed, shot = 77, 5
+    k = sm(sm(sm(seed ^ 0x42414C414E4345) ^ shot) ^ 0)
+    want = np.zeros((2, L, L), np.uint8)
+    for x in (0, 3):
+        bit = sm(k ^ x) >> 63  # site index r = y*L + x with y = 0
+        want[0, 0, x if bit == 0 else (x - 1) % L] ^= 1
+    C, steps, flag = oracle_mod.decode_shot(N, max_steps=1, balance_rule=1, seed=seed, shot=shot)
+    np.testing.assert_array_equal(C, want)
+    # deterministic rule: stuck until the budget; random rule: the pair meets
+    _, steps0, flag0 = oracle_mod.decode_shot(N, max_steps=200)
+    assert (steps0, flag0) == (200, 2)
+    for sh in range(8):
+        _, st, fl = oracle_mod.decode_shot(N, max_steps=200, balance_rule=1, seed=seed, shot=sh)
+        assert fl != 2 and st < 200
 
 
 # -------------------------------------------------------------- invariants --

@@ -48,6 +48,12 @@ MUTANTS = {
                           "for (int i = 1; i < v; ++i) {\n    qo_message_substep"),
     "correction_overwritten": ("for (size_t i = 0; i < 2 * LL; ++i) C[i] ^= F[i];",
                                "for (size_t i = 0; i < 2 * LL; ++i) C[i] = F[i];"),
+    "literal_key_ties_to_nearer": ("(key == bkey && val > bv)", "(key == bkey && val < bv)"),
+    "literal_key_offset_sign": ("key = 3 * (int64_t)val + sa, bkey = 3 * (int64_t)bv + bsa;",
+                                "key = 3 * (int64_t)val - sa, bkey = 3 * (int64_t)bv - bsa;"),
+    "balanced_draw_sign": ("(int8_t)((u >> 63) ? +1 : -1);", "(int8_t)((u >> 63) ? -1 : +1);"),
+    "balanced_draw_drops_step": ("const uint64_t k2 = qo_splitmix64(k1 ^ (uint64_t)(uint32_t)t);\n  for (size_t r = 0; r < LL; ++r) {\n    if (!balanced[r])",
+                                 "const uint64_t k2 = k1;\n  for (size_t r = 0; r < LL; ++r) {\n    if (!balanced[r])"),
 }
 
 
@@ -167,10 +173,13 @@ def _battery(mod):
     the pins that failed."""
     failed = []
     for case in all_cases():
-        C, steps, flag = mod.decode_shot(case["N"], m_max=case["m_max"],
-                                         max_steps=case["max_steps"])
-        if steps != case["steps"] or flag != case["flag"] or not np.array_equal(C, case["C"]):
-            failed.append("golden:" + case["name"])
+        for tie in case["tie_orders"]:
+            C, steps, flag = mod.decode_shot(case["N"], m_max=case["m_max"],
+                                             max_steps=case["max_steps"], tie_order=tie)
+            if steps != case["steps"] or flag != case["flag"] or not np.array_equal(C, case["C"]):
+                failed.append(f"golden:{case['name']}:tie{tie}")
+    import test_oracle as t
+    failed += _run_pins([("balanced_random_rule", lambda: t.test_balanced_random_rule(mod))])
     rng = np.random.default_rng(3)
     for L in (5, 7):
         anyon = rng.random((L, L)) < 0.08

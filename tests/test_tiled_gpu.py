@@ -126,11 +126,14 @@ def test_syndrome_entry_L384():
     np.testing.assert_array_equal(exh.cpu().numpy(), (fo == 2).astype(np.uint8))
 
 
-def test_L1024_sampled_shots_and_full_batch_properties():
-    # the large-lattice workload's size: one launch over 64 shots; two sampled
-    # shots against the oracle, every shot checked for an empty final syndrome
+@pytest.mark.parametrize("p,n_sampled", [(0.05, 4), (0.07, 2)])
+def test_L1024_sampled_shots_and_full_batch_properties(p, n_sampled):
+    # the large-lattice workload's size: one launch over 64 shots; every shot
+    # checked for an empty final syndrome, and sampled shots (the longest one
+    # among them) against the oracle, decoded in parallel worker processes
+    import oracle_pool
     L, shots = 1024, 64
-    N = qca.sample_errors(L, shots, 0.05, seed=0)
+    N = qca.sample_errors(L, shots, p, seed=0)
     C, steps, fail = qca.decode_batch(N, max_steps=4096)
     torch.cuda.synchronize()
     assert int((fail == 3).sum()) == 0
@@ -139,8 +142,13 @@ def test_L1024_sampled_shots_and_full_batch_properties():
     sig = ex ^ torch.roll(ex, 1, dims=2) ^ ey ^ torch.roll(ey, 1, dims=1)
     done = (fail != 2)
     assert int(sig[done].sum()) == 0
-    Nh = N.cpu().numpy()
-    for s in (37,):
-        Co, so, fo = oracle.decode_shot(Nh[s], max_steps=4096)
-        assert int(steps[s]) == so and int(fail[s]) == fo
-        np.testing.assert_array_equal(C[s].cpu().numpy(), Co)
+    steps_c = steps.cpu().numpy()
+    rng = np.random.default_rng(int(p * 1000))
+    pick = [int(np.argmax(steps_c))] + \
+        rng.choice(np.setdiff1d(np.arange(shots), [np.argmax(steps_c)]), n_sampled - 1,
+                   replace=False).tolist()
+    Nh = N[pick].cpu().numpy()
+    Co, so, fo = oracle_pool.decode_many(Nh, max_steps=4096)
+    for i, s in enumerate(pick):
+        assert int(steps[s]) == so[i] and int(fail[s]) == fo[i], s
+        np.testing.assert_array_equal(C[s].cpu().numpy(), Co[i])

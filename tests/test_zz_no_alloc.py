@@ -42,7 +42,22 @@ def _noalloc(N, max_steps):
     return C.cpu().numpy(), steps.cpu().numpy(), fail.cpu().numpy()
 
 
-@pytest.mark.parametrize("L,shots,p", [(16, 300, 0.06), (31, 60, 0.08), (256, 40, 0.05)])
+def test_noalloc_zero_shot_call_sets_up_the_device():
+    """A call with no shots is the documented warm-up: it returns 0 and the
+    next call decodes correctly."""
+    lib = qca.lib()
+    assert lib.qca_decode_batch_noalloc(None, 16, 0, 10, 0, None, None, None, None, None) == 0
+    N = qca.sample_errors(16, 50, 0.06, seed=3)
+    want = _reference(N, 600)
+    got = _noalloc(N, 600)
+    for g_arr, w_arr in zip(got, want):
+        np.testing.assert_array_equal(g_arr, w_arr)
+
+
+# L = 384 leaves room for 8 shots at once in the fixed array and L = 1024 for
+# one, so these batches take several turns
+@pytest.mark.parametrize("L,shots,p", [(16, 300, 0.06), (31, 60, 0.08), (256, 40, 0.05),
+                                       (384, 10, 0.05), (1024, 2, 0.05)])
 def test_noalloc_matches_existing_entry_point_twice(L, shots, p):
     # two different inputs, decoded one after the other on the shared array
     for seed in (11, 12):
