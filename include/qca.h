@@ -427,6 +427,16 @@ int64_t qca_net_chunk_shots(int L);
 int qca_net_logits_async(qca_net_t net, const uint8_t* noise, int L, int64_t shots,
                          float* out_logits, void* stream);
 
+/* Checking aid: run the net's forward (the active precision and tensor path)
+ * on noise device uint8 [shots][2][L][L] and write the activations of layer
+ * `layer` (1..3) as the next layer reads them into out (device fp32
+ * [shots][32][L][L]): the bf16 values, or in the FP8 form the e4m3 values,
+ * which the next layer multiplies by the scale s_layer.  Lets a test feed the kernels' own layer-k output into an
+ * FP64 layer k+1.  1 <= shots <= qca_net_chunk_shots(L).  Allocates a
+ * temporary buffer; runs on the legacy default stream and synchronises. */
+int qca_net_activations(qca_net_t net, const uint8_t* noise, int L, int64_t shots, int layer,
+                        float* out);
+
 /* Pre-decode: out_residual uint8 [shots][2][L][L] = N xor C0 and, if out_c0
  * is not NULL, out_c0 = C0 (same layout). */
 int qca_net_predecode_async(qca_net_t net, const uint8_t* noise, int L, int64_t shots,

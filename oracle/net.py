@@ -184,6 +184,63 @@ def forward_fp8(anyon: np.ndarray, params: np.ndarray, act_scales) -> np.ndarray
     return x
 
 
+# ------------------------------------------- rounding of stored activations
+# Each layer's output is stored in a narrow format before the next layer reads
+# it: bf16(relu(z)) in the bf16 form, e4m3(relu(z) / s) * s in the FP8 form.
+# The kernels form z as an fp32 sum of the same terms the FP64 reference adds;
+# the two sums differ by at most (number of terms) * 2^-23 times the sum of the
+# terms' magnitudes (288 products: below 2^-14 of that sum).  Where the stored
+# value is not constant over that interval around the FP64 z, either rounding
+# is a correct result of the kernel's arithmetic.
+
+ACC_REL_BOUND = 2.0 ** -14
+
+
+def layer_weights(params: np.ndarray, fp8: bool = False):
+    """[(W, b)] as each layer multiplies them: bf16-rounded weights (bf16 form;
+    also layer 1 of the FP8 form) or dequantised per-channel e4m3 weights
+    (layers 2-4 of the FP8 form)."""
+    out = []
+    for i, (W, b) in enumerate(unpack(params)):
+        out.append((fp8_weights(W) if (fp8 and i > 0) else bf16_round(W), b))
+    return out
+
+
+def conv_magnitude(x: np.ndarray, W: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Sum of the magnitudes of the terms of each output of conv3x3_circular:
+    |b| + sum |W| |x| over taps and input channels."""
+    return conv3x3_circular(np.abs(x), np.abs(W), np.abs(b))
+
+
+def store_activation(z: np.ndarray, scale: float = None) -> np.ndarray:
+    """The stored form of relu(z): bf16 (scale None) or e4m3(relu(z) / scale) * scale."""
+    r = np.maximum(z, 0.0)
+    if scale is None:
+        return bf16_round(r)
+    return e4m3_round(r / scale) * scale
+
+
+def store_interval(z: np.ndarray, mag: np.ndarray, scale: float = None,
+                   rel: float = ACC_REL_BOUND):
+    """Stored values at the two ends of [z - rel*mag, z + rel*mag]: the
+    rounding is monotone, so every sum within the interval stores a value
+    between them (inclusive), and where they agree exactly that value."""
+    d = rel * mag
+    return store_activation(z - d, scale), store_activation(z + d, scale)
+
+
+def dilate(mask: np.ndarray, steps: int) -> np.ndarray:
+    """Circular 3x3 dilation of a boolean [..., L, L] map, `steps` times."""
+    m = mask.copy()
+    for _ in range(steps):
+        acc = m.copy()
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                acc |= np.roll(m, shift=(dy, dx), axis=(-2, -1))
+        m = acc
+    return m
+
+
 # ------------------------------------------------------------- training
 
 LABEL_SMOOTHING = 0.1

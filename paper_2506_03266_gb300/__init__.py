@@ -114,6 +114,7 @@ def lib():
             "qca_watchdog_selftest": ([vp, vp, vp, vp], i32),
             "qca_probe_peaks": ([vp], i32),
             "qca_net_logits_async": ([vp, vp, i32, i64, vp, vp], i32),
+            "qca_net_activations": ([vp, vp, i32, i64, i32, vp], i32),
             "qca_net_predecode_async": ([vp, vp, i32, i64, vp, vp, vp], i32),
             "qca_net_decode_batch_async": ([vp, vp, i32, i64, i32, u64, vp, vp, vp, cfgp, vp,
                                             vp], i32),
@@ -605,6 +606,19 @@ class Net:
         _check(lib().qca_net_logits_async(self.handle, ctypes.c_void_p(errors.data_ptr()), L,
                                           shots, ctypes.c_void_p(out.data_ptr()),
                                           _stream(torch, stream)))
+        return out
+
+    def activations(self, errors, layer: int):
+        """Layer `layer` (1..3) activations as the next layer reads them, fp32
+        [shots][32][L][L]: bf16 values, or e4m3 values before the layer's
+        scale in the FP8 form (qca_net_activations; synchronises)."""
+        torch = _torch()
+        shots, L = errors.shape[0], errors.shape[-1]
+        _dev_u8(torch, errors, (shots, 2, L, L), "errors")
+        out = torch.empty((shots, 32, L, L), dtype=torch.float32, device=errors.device)
+        torch.cuda.synchronize()
+        _check(lib().qca_net_activations(self.handle, ctypes.c_void_p(errors.data_ptr()), L,
+                                         shots, layer, ctypes.c_void_p(out.data_ptr())))
         return out
 
     def predecode(self, errors, stream=None):

@@ -1884,6 +1884,56 @@ __global__ void __launch_bounds__(256) wgrad_mma_kernel(const __nv_bfloat16* __r
   }
 }
 
+// Read-out of one layer's activations as the next layer consumes them, as
+// fp32 [shot][32][L][L] (a checking aid, not part of inference).  form: 0 bf16
+// [site][32], 1 bf16 planar [shot][y][octet][x][8], 2 e4m3 [site][32], 3 e4m3
+// planar [shot][y][16-channel group][x][16], 4 / 5 the bf16 / e4m3 layer-1
+// table [512][32] indexed by the 3 x 3 anyon pattern of sig (bit ky * 3 + kx).
+// e4m3 codes are written as their e4m3 values (exact in fp32), not rescaled.
+__global__ void capture_kernel(const void* __restrict__ src, int form,
+                               const uint8_t* __restrict__ sig, int L, int64_t shots,
+                               float* __restrict__ out) {
+  const int64_t LL = (int64_t)L * L;
+  const int64_t n = shots * 32 * LL;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t shot = i / (32 * LL);
+    const int64_t r = i - shot * 32 * LL;
+    const int c = (int)(r / LL);
+    const int site = (int)(r - (int64_t)c * LL);
+    const int y = site / L, x = site - (site / L) * L;
+    const int64_t gs = shot * LL + site;
+    const __nv_bfloat16* b = reinterpret_cast<const __nv_bfloat16*>(src);
+    const uint8_t* q = reinterpret_cast<const uint8_t*>(src);
+    float v = 0.f;
+    int code = -1;
+    if (form == 0) {
+      v = __bfloat162float(b[gs * 32 + c]);
+    } else if (form == 1) {
+      v = __bfloat162float(b[(((shot * L + y) * 4 + c / 8) * (int64_t)L + x) * 8 + c % 8]);
+    } else if (form == 2) {
+      code = q[gs * 32 + c];
+    } else if (form == 3) {
+      code = q[(((shot * L + y) * 2 + c / 16) * (int64_t)L + x) * 16 + c % 16];
+    } else {
+      int pat = 0;
+      for (int tap = 0; tap < 9; ++tap) {
+        const int yy = wrapL(y + tap / 3 - 1, L), xx = wrapL(x + tap % 3 - 1, L);
+        if (sig[shot * LL + (int64_t)yy * L + xx]) pat |= 1 << tap;
+      }
+      if (form == 4)
+        v = __bfloat162float(b[pat * 32 + c]);
+      else
+        code = q[pat * 32 + c];
+    }
+    if (code >= 0) {
+      const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)code, __NV_E4M3);
+      v = __half2float(__half(h));
+    }
+    out[i] = v;
+  }
+}
+
 int grid_for(int64_t items, int threads) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -2488,6 +2538,53 @@ int qca_net_logits_async(qca_net_t n, const uint8_t* noise, int L, int64_t shots
   if (int rc = check_aligned(out_logits, 4, "out_logits")) return rc;
   if (shots == 0) return QCA_OK;
   return net_run(n, noise, L, shots, out_logits, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+int qca_net_activations(qca_net_t n, const uint8_t* noise, int L, int64_t shots, int layer,
+                        float* out) {
+  if (!n || L < 4 || L > QCA_MAX_L || shots < 1 || !noise || !out || layer < 1 || layer > 3) {
+    set_error("qca_net_activations: bad arguments");
+    return QCA_ERR_ARG;
+  }
+  if (shots > net_chunk(L)) {
+    set_error("qca_net_activations: at most %lld shots at L = %d (one inference chunk)",
+              (long long)net_chunk(L), L);
+    return QCA_ERR_ARG;
+  }
+  if (int rc = check_aligned(out, 4, "out")) return rc;
+  const int64_t LL = (int64_t)L * L, S = shots * LL;
+  float* logits = nullptr;
+  cudaError_t e = cudaMalloc(&logits, sizeof(float) * 4 * S);
+  if (e != cudaSuccess) return cuda_fail(e, "qca_net_activations buffer");
+  int rc = net_run(n, noise, L, shots, logits, nullptr, nullptr, nullptr);
+  const bool tc_tile = L % kTcM == 0 && L % kTcStrip == 0;
+  const bool fp8 = n->precision == 1;
+  const bool planar = n->use_tc == 2 && tc_tile;
+  uint8_t* sig = n->ws;
+  __nv_bfloat16* actA = reinterpret_cast<__nv_bfloat16*>(n->ws + ((2 * S + 255) & ~(int64_t)255));
+  __nv_bfloat16* actB = actA + S * 32;
+  const void* src = nullptr;
+  int form = 0;
+  if (rc == QCA_OK) {
+    if (layer == 1) {
+      if (fp8) {
+        layer1_lut8_kernel<<<32, 256>>>(n->w1, n->params, 1.f / n->act_scale[0], n->lut8);
+        src = n->lut8;
+        form = 5;
+      } else {
+        src = n->lut;
+        form = 4;
+      }
+    } else {
+      src = (layer == 2) ? (const void*)actB : (const void*)actA;
+      form = fp8 ? (planar ? 3 : 2) : (planar ? 1 : 0);
+    }
+    capture_kernel<<<grid_for(S * 32, 256), 256>>>(src, form, sig, L, shots, out);
+    rc = cuda_fail(cudaGetLastError(), "activation read-out");
+  }
+  if (rc == QCA_OK) rc = cuda_fail(cudaDeviceSynchronize(), "qca_net_activations");
+  cudaFree(logits);
+  return rc;
 }
 
 int qca_net_predecode_async(qca_net_t n, const uint8_t* noise, int L, int64_t shots,

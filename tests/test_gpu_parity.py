@@ -54,8 +54,13 @@ def test_sampler_bit_exact(L, p, shot0):
 
 # ------------------------------------------------------------ worked cases --
 
-@pytest.mark.parametrize("case", all_cases(), ids=[c["name"] for c in all_cases()])
+LEX_CASES = [c for c in all_cases() if 0 in c["tie_orders"]]
+
+
+@pytest.mark.parametrize("case", LEX_CASES, ids=[c["name"] for c in LEX_CASES])
 def test_golden_cases_on_gpu(case):
+    # default options (lexicographic ties); tests/test_rules_gpu.py runs every
+    # case under each tie order it is written for
     C, s, f = gpu_decode(case["N"][None], max_steps=case["max_steps"], m_max=case["m_max"])
     assert s[0] == case["steps"] and f[0] == case["flag"]
     np.testing.assert_array_equal(C[0], case["C"])
