@@ -84,6 +84,7 @@ def lib():
             "qca_autotune": ([i32, i64, ctypes.c_double, u64, i32, vp, vp, vp], i32),
             "qca_uneven_plan_create": ([vp, i64, vp, vp, ctypes.POINTER(vp)], i32),
             "qca_uneven_plan_destroy": ([vp], i32),
+            "qca_uneven_plan_set_mode": ([vp, i32], i32),
             "qca_uneven_plan_offsets_device": ([vp, ctypes.POINTER(vp)], i32),
             "qca_sample_errors_uneven_async": ([vp, vp, vp, i64, u64, vp, vp], i32),
             "qca_decode_uneven_async": ([vp, vp, i32, u64, vp, vp, vp, cfgp, vp], i32),
@@ -428,6 +429,11 @@ class UnevenPlan:
                                             ctypes.byref(total), ctypes.byref(h)))
         self.handle = h
         self.total_bytes = total.value
+
+    def set_mode(self, mode: str):
+        """"mixed" (default): one persistent launch over every size the on-chip
+        sweep takes; "per_size": one persistent launch per size."""
+        _check(lib().qca_uneven_plan_set_mode(self.handle, {"mixed": 0, "per_size": 1}[mode]))
 
     def close(self):
         if self.handle:

@@ -155,6 +155,14 @@ int generic_forced(int L);  // qca_set_kernel_path(L, 0) is in effect
 // 1 / 2 on-chip (one CTA / two-CTA cluster), 3 tiled; and the launch.
 int decode_path(int L, int v, int m_max);
 int launch_decode(const DecodeArgs& a, cudaStream_t stream);
+// Mixed lattice sizes in one persistent launch (on-chip sweep): the group
+// size of a lattice size in it (0 two-CTA pair, else 512, 256, 128 or 64
+// threads; -1 not on the on-chip sweep), and the launch over items queued by
+// group size (pairs first), then by decreasing L.
+int mixed_group_threads(int L, int m_max);
+int launch_mixed(const DecodeArgs& a, const uint8_t* item_class, const int* sizes,
+                 const int* group_threads, int nclass, int64_t n_pair, int64_t n_items,
+                 cudaStream_t stream);
 // Generic sweep on the library's fixed device array (no allocation).
 int launch_generic_noalloc(const DecodeArgs& a, cudaStream_t stream);
 size_t noalloc_slot_bytes(int L);

@@ -2576,7 +2576,11 @@ int qca_net_activations(qca_net_t n, const uint8_t* noise, int L, int64_t shots,
         form = 4;
       }
     } else {
-      src = (layer == 2) ? (const void*)actB : (const void*)actA;
+      // the FP8 form keeps its e4m3 maps (32 bytes per site) in the same
+      // workspace: layer 2 at byte S * 32, layer 3 at the start
+      const uint8_t* a8A = reinterpret_cast<const uint8_t*>(actA);
+      src = fp8 ? ((layer == 2) ? (const void*)(a8A + S * 32) : (const void*)a8A)
+                : ((layer == 2) ? (const void*)actB : (const void*)actA);
       form = fp8 ? (planar ? 3 : 2) : (planar ? 1 : 0);
     }
     capture_kernel<<<grid_for(S * 32, 256), 256>>>(src, form, sig, L, shots, out);

@@ -105,6 +105,34 @@ struct Cluster {
   }
 };
 
+// The threads that decode one shot: the whole CTA (barrier 0, the plain block
+// barrier) or a slice of it (threads [base, base + nt) with named barrier
+// `bar`), so that one CTA can decode several small lattices at once.
+struct Grp {
+  int tid;  // thread index within the group
+  int nt;   // threads in the group (a multiple of 32)
+  int bar;  // 0: the whole CTA; else a named barrier id (1..15)
+  __device__ __forceinline__ void sync() const {
+    if (bar == 0) {
+      __syncthreads();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
+    }
+  }
+  // barrier with the OR of p over the group
+  __device__ __forceinline__ int sync_or(int p) const {
+    if (bar == 0) return __syncthreads_or(p);
+    int r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n"
+        " selp.s32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"(p), "r"(bar), "r"(nt)
+        : "memory");
+    return r;
+  }
+};
+
 __device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b) { return __vminu2(a, b); }
 
 // Rolling width-7 window over rows for one 16-bit-lane chain:
@@ -169,14 +197,13 @@ __device__ __forceinline__ uint32_t nonzero_nibble(uint32_t w) {
 
 // Rebuild the anyon list from sigma; returns "any anyon" (block-uniform).
 __device__ __forceinline__ int build_list(const uint32_t* sig, const FastGeom& g, uint16_t* list,
-                                          int* count) {
-  // each thread owns a contiguous run of words: one scan and one atomic per warp
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+                                          int* count, const Grp& G) {
+  // thread t owns words t, t + nt, ... (a warp's accesses hit distinct banks):
+  // one scan and one atomic per warp
+  const int tid = G.tid, nt = G.nt, lane = tid & 31;
   const int wsm = (1 << g.lws) - 1;
-  const int per = (g.nws + nt - 1) / nt;
-  const int w0 = tid * per, w1 = min(g.nws, w0 + per);
   int n = 0;
-  for (int w = w0; w < w1; ++w) n += __popc(sig[w]);
+  for (int w = tid; w < g.nws; w += nt) n += __popc(sig[w]);
   int incl = n;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -188,7 +215,7 @@ __device__ __forceinline__ int build_list(const uint32_t* sig, const FastGeom& g
   if (lane == 31 && total) wbase = atomicAdd(count, total);
   wbase = __shfl_sync(0xffffffffu, wbase, 31);
   int pos = wbase + incl - n;
-  for (int w = w0; w < w1; ++w) {
+  for (int w = tid; w < g.nws; w += nt) {
     uint32_t b = sig[w];
     const int y = w >> g.lws, xb = (w & wsm) << 5;
     while (b) {
@@ -198,7 +225,7 @@ __device__ __forceinline__ int build_list(const uint32_t* sig, const FastGeom& g
       ++pos;
     }
   }
-  return __syncthreads_or(n);
+  return G.sync_or(n);
 }
 
 // Feedback applied densely, 32 sites per word: sigma <- sigma * sigma_F with
@@ -207,24 +234,23 @@ __device__ __forceinline__ int build_list(const uint32_t* sig, const FastGeom& g
 // e_y(r - y^).  The CTA's rows of the correction take F as well.  Every CTA
 // holds the whole flipped-link map.  Then the anyon list is rebuilt from the
 // new sigma; returns "any anyon" (block-uniform).
+template <int kMaxPer>
 __device__ __forceinline__ int apply_flips(uint32_t* sig, const uint32_t* flip, uint32_t* Cb,
                                            const FastGeom& g, uint16_t* list, int* count,
-                                           int row_lo, int row_hi) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, L = g.L;
+                                           int row_lo, int row_hi, const Grp& G) {
+  const int tid = G.tid, nt = G.nt, lane = tid & 31, L = g.L;
   const int wsm = (1 << g.lws) - 1;
-  const int per = (g.nws + nt - 1) / nt;
-  const int w0 = tid * per, w1 = min(g.nws, w0 + per);
   const int last_w = (L - 1) >> 5, last_b = (L - 1) & 31;
-  // the words of a thread are handled as independent chains (unrolled for up
-  // to kMaxPer words, the most any configuration gives a thread)
-  constexpr int kMaxPer = 4;
+  // thread t owns words t, t + nt, ... (a warp's accesses hit distinct banks),
+  // handled as independent chains (unrolled for up to kMaxPer words, the most
+  // the configuration gives a thread)
   uint32_t snew[kMaxPer];
   int n = 0;
 #pragma unroll
   for (int k = 0; k < kMaxPer; ++k) {
-    const int w = w0 + k;
+    const int w = tid + k * nt;
     snew[k] = 0;
-    if (w >= w1) continue;
+    if (w >= g.nws) continue;
     const int y = w >> g.lws, j = w & wsm, x0 = j << 5;
     if (x0 >= L) continue;  // padding word
     const int ym = (y == 0) ? L - 1 : y - 1;
@@ -258,7 +284,7 @@ __device__ __forceinline__ int apply_flips(uint32_t* sig, const uint32_t* flip, 
   int pos = wbase + incl - n;
 #pragma unroll
   for (int k = 0; k < kMaxPer; ++k) {
-    const int w = w0 + k;
+    const int w = tid + k * nt;
     uint32_t b = snew[k];
     const int y = w >> g.lws, xb = (w & wsm) << 5;
     while (b) {
@@ -268,15 +294,15 @@ __device__ __forceinline__ int apply_flips(uint32_t* sig, const uint32_t* flip, 
       ++pos;
     }
   }
-  return __syncthreads_or(n);
+  return G.sync_or(n);
 }
 
 // Calls f(x, y) for every anyon of the current sigma, from the list when it
 // held them all, else straight from the bitmap.
 template <class F>
 __device__ __forceinline__ void for_each_anyon(const uint16_t* list, int count, const uint32_t* sig,
-                                               const FastGeom& g, F&& f) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+                                               const FastGeom& g, const Grp& G, F&& f) {
+  const int tid = G.tid, nt = G.nt;
   if (count <= g.cap) {
     // The list is sorted by site; give the 32 lanes of a warp entries far apart
     // (list index = lane-major transpose) so that their accesses spread over banks.
@@ -357,15 +383,15 @@ __device__ __forceinline__ void store_words(uint8_t* p, const uint32_t (&w)[KW])
 template <int KW, bool MERGE>
 __device__ void dense_terms(const uint32_t* sig, const uint16_t* list, int count, uint32_t* sT,
                             const FastGeom& g, uint8_t* planes, int pl, int lrow0, int R0,
-                            bool plus, int cword, bool lane_on) {
-  const int tid = threadIdx.x, nt = blockDim.x, L = g.L;
+                            bool plus, int cword, bool lane_on, const Grp& G) {
+  const int tid = G.tid, nt = G.nt, L = g.L;
   // transposed sigma: bit (row x, column y), the frame of the y planes
   for (int i = tid; i < g.nws; i += nt) sT[i] = 0;
-  __syncthreads();
-  for_each_anyon(list, count, sig, g, [&](int x, int y) {
+  G.sync();
+  for_each_anyon(list, count, sig, g, G, [&](int x, int y) {
     atomicOr(&sT[(x << g.lws) + (y >> 5)], 1u << (y & 31));
   });
-  __syncthreads();
+  G.sync();
   if (lane_on) {
     const uint32_t* bm = (pl < 2) ? sig : sT;
     const uint32_t off2 = (uint32_t)(g.off + 2) * 0x01010101u;
@@ -416,12 +442,21 @@ __device__ void dense_terms(const uint32_t* sig, const uint16_t* list, int count
       e5 = e6;
     }
   }
-  __syncthreads();
+  G.sync();
 }
 
+// Most bitmap words a thread handles in the dense feedback pass: geometries
+// are accepted only within it (make_geom).
+template <int CL>
+constexpr int kWordsPerThread = CL == 1 ? 2 : 4;
+
+// Decodes one shot with the group G (the whole CTA or a slice of it, CL = 1;
+// or the CTAs of a 2-CTA cluster, each with its whole block, CL = 2) on the
+// shared-memory state at `smem` laid out for geometry g.  Every thread of the
+// group (and of the cluster) calls it with the same shot.
 template <int CL, int KW>
-__global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArgs a, FastGeom g) {
-  extern __shared__ __align__(16) uint8_t smem[];
+__device__ __forceinline__ void decode_shot(const DecodeArgs& a, const FastGeom& g, uint8_t* smem,
+                                            int64_t shot, const Grp& G) {
   const int L = g.L;
   const int LL = L * L;
   const int rank = Cluster<CL>::rank();
@@ -433,7 +468,7 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
   uint16_t* list = reinterpret_cast<uint16_t*>(Cb + 2 * g.nws);
   int* misc = reinterpret_cast<int*>(list + ((g.cap + 7) & ~7));
 
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = G.tid, nt = G.nt;
   const int warp = tid >> 5, lane = tid & 31;
   // ---- dense-sweep role of this thread
   const int seg = warp * g.spw + lane / g.G;
@@ -453,9 +488,15 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
   uint8_t* my_rows = planes + ((size_t)(pl * g.rows_local + lrow0)) * LS + cword * 4;
   const int row_lo = rank * g.rows_local, row_hi = row_lo + g.rows_local;
 
-  const int nclusters = gridDim.x / CL;
-  const int cid = blockIdx.x / CL;
   const int wpr = 1 << g.lws;  // bitmap words per row
+  // barrier of the whole decoder: the group's, or the cluster's
+  auto csync = [&]() {
+    if constexpr (CL == 1) {
+      G.sync();
+    } else {
+      Cluster<CL>::sync();
+    }
+  };
 
   uint32_t halo[6][KW];
   auto snapshot = [&]() {
@@ -470,6 +511,307 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
     }
   };
 
+  const int64_t base = shot_offset_of(a, shot);
+  const uint8_t* N = a.in + base;
+  // ---- init: bitmaps cleared, sigma measured (every CTA of the cluster holds
+  //      the full sigma); the planes are written whole by the first step
+  {
+    for (int i = tid; i < 6 * g.nws; i += nt) flipb[i] = 0;  // flip maps and Cb
+    if (tid == 0) misc[0] = 0;
+  }
+  // sigma, 32 sites per thread and word; Def. synch_ccqs: parity of the four
+  // links incident to r (or the given anyon indicator)
+  for (int w = tid; w < g.nws; w += nt) {
+    const int y = w >> g.lws, x0 = (w & (wpr - 1)) << 5;
+    uint32_t bits = 0;
+    if (x0 < L) {
+      const int n = min(32, L - x0);
+      if (a.from_sigma) {
+        const uint8_t* row = N + (size_t)y * L + x0;
+        for (int k = 0; k < n; k += 4)
+          bits |= nonzero_nibble(*reinterpret_cast<const uint32_t*>(row + k)) << k;
+      } else {
+        const uint8_t* ex = N + (size_t)y * L + x0;
+        const uint8_t* ey = N + LL + (size_t)y * L + x0;
+        const uint8_t* eyd = N + LL + (size_t)wrapi(y - 1, L) * L + x0;
+        uint32_t bx = 0, by = 0, byd = 0;
+        for (int k = 0; k < n; k += 4) {
+          bx |= nibble_of(*reinterpret_cast<const uint32_t*>(ex + k)) << k;
+          by |= nibble_of(*reinterpret_cast<const uint32_t*>(ey + k)) << k;
+          byd |= nibble_of(*reinterpret_cast<const uint32_t*>(eyd + k)) << k;
+        }
+        const uint32_t left = N[(size_t)y * L + wrapi(x0 - 1, L)] & 1u;  // e_x(r - x^) at x0
+        bits = bx ^ ((bx << 1) | left) ^ by ^ byd;
+        if (n < 32) bits &= (1u << n) - 1u;
+      }
+    }
+    sig_cur[w] = bits;
+  }
+  G.sync();
+  int any = build_list(sig_cur, g, list, &misc[0], G);
+  int count = misc[0];
+
+  int t = 0, flag = 0;
+  while (any) {
+    if (t >= a.max_steps) {
+      flag = 2;
+      break;
+    }
+    // flipped-link maps alternate by step parity: a partner CTA may still read
+    // the previous step's map while this step writes the other one
+    uint32_t* const flip = flipb + (t & 1) * 2 * g.nws;
+    if (t == 0) {
+      // ================= 1. first step: the planes start empty, so the
+      // message update reduces to the anyon terms; compute them densely
+      // for every site (32 sites per bitmap operation) instead of
+      // scattering the cone sections of the many initial anyons.
+      dense_terms<KW, false>(sig_cur, list, count, flip, g, planes, pl, lrow0, R0, plus, cword,
+                             lane_on, G);
+    } else if (warp_on) {
+      // ================= 1a. dense message update of this thread's band
+      Chain cH[KW], cL[KW];
+      uint32_t first[3][KW];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) load_words<KW>(my_rows + (size_t)k * LS, first[k]);
+#pragma unroll
+      for (int q = 0; q < KW; ++q) {
+        uint32_t ah[6], al[6];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          ah[k] = halo[k][q];
+          ah[3 + k] = first[k][q];
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) al[k] = ah[k] << 8;
+        cH[q].init(ah);
+        cL[q].init(al);
+      }
+      auto row = [&](int i, const uint32_t (&in)[KW]) {
+        uint32_t m[KW];
+#pragma unroll
+        for (int q = 0; q < KW; ++q) {
+          const uint32_t tH = cH[q].step(in[q]);
+          const uint32_t tL = cL[q].step(in[q] << 8);
+          m[q] = finish_word(tL, tH);
+        }
+        uint32_t out[KW];
+        if (KW == 1) {
+          if (plus) {
+            const uint32_t nb = __shfl_sync(0xffffffffu, m[0], left_lane);
+            out[0] = __funnelshift_r(nb, m[0], 8);
+          } else {
+            const uint32_t nb = __shfl_sync(0xffffffffu, m[0], right_lane);
+            out[0] = __funnelshift_r(m[0], nb, 24);
+          }
+        } else {
+          const uint32_t sendv = plus ? m[KW - 1] : m[0];
+          const uint32_t nb = __shfl_sync(0xffffffffu, sendv, plus ? left_lane : right_lane);
+          if (plus) {
+            out[0] = __funnelshift_r(nb, m[0], 8);
+#pragma unroll
+            for (int q = 1; q < KW; ++q) out[q] = __funnelshift_r(m[q - 1], m[q], 8);
+          } else {
+#pragma unroll
+            for (int q = 0; q + 1 < KW; ++q) out[q] = __funnelshift_r(m[q], m[q + 1], 24);
+            out[KW - 1] = __funnelshift_r(m[KW - 1], nb, 24);
+          }
+        }
+        if (lane_on) store_words<KW>(my_rows + (size_t)i * LS, out);
+      };
+#pragma unroll 4
+      for (int i = 0; i < g.H - 3; ++i) {
+        uint32_t in[KW];
+        load_words<KW>(my_rows + (size_t)(i + 3) * LS, in);
+        row(i, in);
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        uint32_t in[KW];
+#pragma unroll
+        for (int q = 0; q < KW; ++q) in[q] = halo[3 + k][q];
+        row(g.H - 3 + k, in);
+      }
+    }
+    // ================= 1b. anyon terms of steps after the first
+    if (t > 0) {
+      if (count <= g.cap && count <= g.sparse_max) {
+        // light-cone sections written per anyon, d = 3, 2, 1 (largest value
+        // first); a warp takes one anyon, lane = (plane, transverse offset), so
+        // the lanes of a store hit consecutive rows (distinct banks).  Each CTA
+        // writes the sections that fall in its rows.
+        G.sync();
+        auto pass = [&](auto dconst) {
+          constexpr int d = decltype(dconst)::value;
+          const uint8_t val = (uint8_t)(g.off + d - 1);
+          const int p = lane >> 3, jj = lane & 7;
+          const bool act = jj < 2 * d + 1;
+          const int nw = nt >> 5;
+          // four anyons per warp and iteration (independent loads, then stores)
+          for (int i0 = warp; i0 < count; i0 += 4 * nw) {
+            int e[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const int i = i0 + k * nw;
+              e[k] = (i < count) ? (int)list[i] : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const int x0 = e[k] & 0xFF, y0 = e[k] >> 8;
+              if (act && e[k] >= 0) {
+                const int row0 = (p < 2) ? y0 : x0;
+                const int col0 = (p < 2) ? x0 : y0;
+                const int col = wrapi((p % 2 == 0) ? col0 + d : col0 - d, L);
+                const int R = wrapi(row0 + jj - d, L);
+                if (CL == 1 || (R >= row_lo && R < row_hi))
+                  planes[(size_t)(p * g.rows_local + R - row_lo) * LS + col] = val;
+              }
+            }
+          }
+          G.sync();
+        };
+        pass(std::integral_constant<int, 3>{});
+        pass(std::integral_constant<int, 2>{});
+        pass(std::integral_constant<int, 1>{});
+      } else {
+        G.sync();  // the dense update above is complete
+        dense_terms<KW, true>(sig_cur, list, count, flip, g, planes, pl, lrow0, R0, plus, cword,
+                              lane_on, G);
+      }
+    }
+    // clear this step's flipped-link map (also the scratch of the dense terms)
+    G.sync();
+    for (int i = tid; i < 2 * g.nws; i += nt) flip[i] = 0;
+    // every plane of the cluster final; flip maps ready
+    csync();
+    snapshot();  // halo rows for the next step
+    // ================= 2. forces and feedback for the anyons of this CTA's rows
+    uint64_t kstep = 0, kbal = 0;
+    if (a.move_thr) kstep = move_step_key(a.move_key, a.shot_offset + shot, t);
+    if (a.balance_rule) kbal = move_step_key(a.balance_key, a.shot_offset + shot, t);
+    auto decide = [&](int x, int y) -> int {
+      // Eqs. blahdef / degbreak on the offset-encoded fields (0xFF = none)
+      int dir = force_code(*plane_ptr<CL>(planes, g, 0, y, x), *plane_ptr<CL>(planes, g, 1, y, x),
+                           *plane_ptr<CL>(planes, g, 2, x, y), *plane_ptr<CL>(planes, g, 3, x, y),
+                           a.tie_order);
+      if (dir >= 5) dir = a.balance_rule ? balance_resolve(dir, kbal, y * L + x) : 0;
+      if (a.move_thr) {
+        const uint64_t u = splitmix64(kstep ^ (uint64_t)(y * L + x));
+        if (u < a.move_thr) dir = 1 + (int)(splitmix64(u) >> 62);
+      }
+      return dir;
+    };
+    auto apply = [&](int x, int y, int dir) {
+      // mark link <lo, lo + a^>; a link crossed from both ends is marked
+      // twice and flips once (the OR of Eq. ddfeedback)
+      const int ax = (dir <= 2) ? 0 : 1;
+      const int lx = (dir == 2) ? wrapi(x - 1, L) : x;
+      const int ly = (dir == 4) ? wrapi(y - 1, L) : y;
+      const int wlo = (ly << g.lws) + (lx >> 5);
+      // every CTA keeps the whole map (fire-and-forget ORs, the remote one
+      // through distributed shared memory)
+#pragma unroll
+      for (int r = 0; r < CL; ++r)
+        atomicOr(Cluster<CL>::at(flip, r) + ax * g.nws + wlo, 1u << (lx & 31));
+    };
+    if (count <= g.cap) {
+      // four anyons per thread and iteration: all field loads are issued before
+      // the first atomic (latency hiding with few warps per SM)
+      const int stride = (count + 31) >> 5, span = 32 * stride;
+      for (int i0 = tid; i0 < span; i0 += 4 * nt) {
+        int ex[4], ey[4], dir[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int i = i0 + k * nt;
+          const int idx = (i & 31) * stride + (i >> 5);
+          const bool ok = i < span && idx < count;
+          const int e = ok ? list[idx] : 0;
+          ex[k] = e & 0xFF;
+          ey[k] = e >> 8;
+          const bool mine = ok && (CL == 1 || (ey[k] >= row_lo && ey[k] < row_hi));
+          dir[k] = mine ? decide(ex[k], ey[k]) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (dir[k]) apply(ex[k], ey[k], dir[k]);
+      }
+    } else {
+      for_each_anyon(list, count, sig_cur, g, G, [&](int x, int y) {
+        if (CL > 1 && (y < row_lo || y >= row_hi)) return;
+        const int dir = decide(x, y);
+        if (dir) apply(x, y, dir);
+      });
+    }
+    if (tid == 0) misc[0] = 0;  // list counter (count already read by every thread)
+    csync();
+    // ================= 3. sigma and correction from the flipped links, new
+    //                   anyon list, early exit
+    any = apply_flips<kWordsPerThread<CL>>(sig_cur, flip, Cb, g, list, &misc[0], row_lo, row_hi,
+                                            G);
+    count = misc[0];
+    ++t;
+  }
+  // ================= outputs: correction bytes, homology, steps, flag
+  // (each CTA holds the correction of its own rows)
+  uint8_t* outC = a.out_C + correction_offset_of(a, shot);
+  const int gpr = L / 4;  // 4-site groups per row
+  for (int ax = 0; ax < 2; ++ax) {
+    for (int i = tid; i < g.rows_local * gpr; i += nt) {
+      const int y = row_lo + i / gpr, x = (i - (i / gpr) * gpr) * 4;
+      const int w = (y << g.lws) + (x >> 5);
+      const uint32_t bits = Cb[ax * g.nws + w];
+      const uint32_t nib = (bits >> (x & 31)) & 0xFu;
+      *reinterpret_cast<uint32_t*>(outC + (size_t)ax * LL + (size_t)y * L + x) =
+          (nib * 0x00204081u) & 0x01010101u;
+    }
+  }
+  if (tid == 0) misc[1] = misc[2] = 0;
+  G.sync();
+  if (rank == 0) {
+    int wx = 0, wy = 0;
+    for (int i = tid; i < L; i += nt) {
+      // e_x((0, i)) and e_y((i, 0))
+      uint32_t bx = 0, by = 0;
+#pragma unroll
+      for (int r = 0; r < CL; ++r) {
+        const uint32_t* c = Cluster<CL>::at(Cb, r);
+        bx ^= c[i << g.lws];
+        by ^= c[g.nws + (i >> 5)] >> (i & 31);
+      }
+      wx ^= (int)(bx & 1);
+      wy ^= (int)(by & 1);
+      if (!a.from_sigma) {
+        wx ^= N[(size_t)i * L];
+        wy ^= N[LL + i];
+      }
+    }
+    if (wx) atomicXor(&misc[1], 1);
+    if (wy) atomicXor(&misc[2], 1);
+    G.sync();
+    if (tid == 0) {
+      a.out_steps[shot] = t;
+      if (a.from_sigma) {
+        a.out_cut[2 * shot] = (uint8_t)misc[1];
+        a.out_cut[2 * shot + 1] = (uint8_t)misc[2];
+        if (a.out_exhausted) a.out_exhausted[shot] = (uint8_t)(flag == 2);
+      } else {
+        a.out_flag[shot] = (uint8_t)(flag == 2 ? 2 : ((misc[1] | misc[2]) ? 1 : 0));
+      }
+    }
+  }
+  // partners may still read this CTA's correction share
+  csync();
+}
+
+template <int CL, int KW>
+__global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArgs a, FastGeom g) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int rank = Cluster<CL>::rank();
+  const int tid = threadIdx.x;
+  const Grp G{tid, (int)blockDim.x, 0};
+  int* misc = reinterpret_cast<int*>(smem + g.plane_bytes + (size_t)7 * g.nws * 4 +
+                                     (size_t)((g.cap + 7) & ~7) * 2);
+  const int nclusters = gridDim.x / CL;
+  const int cid = blockIdx.x / CL;
   // Work: static (cluster c takes c, c + nclusters, ...) or, with a queue,
   // dynamic (rank 0 of the cluster takes the next index and shares it).
   auto next_work = [&](int64_t prev) -> int64_t {
@@ -484,294 +826,7 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
   };
   for (int64_t k = next_work(-1); k < a.shots; k = next_work(k)) {
     const int64_t shot = a.shot_list ? (int64_t)a.shot_list[k] : k;
-    const int64_t base = shot_offset_of(a, shot);
-    const uint8_t* N = a.in + base;
-    // ---- init: bitmaps cleared, sigma measured (every CTA of the cluster holds
-    //      the full sigma); the planes are written whole by the first step
-    {
-      for (int i = tid; i < 6 * g.nws; i += nt) flipb[i] = 0;  // flip maps and Cb
-      if (tid == 0) misc[0] = 0;
-    }
-    // sigma, 32 sites per thread and word; Def. synch_ccqs: parity of the four
-    // links incident to r (or the given anyon indicator)
-    for (int w = tid; w < g.nws; w += nt) {
-      const int y = w >> g.lws, x0 = (w & (wpr - 1)) << 5;
-      uint32_t bits = 0;
-      if (x0 < L) {
-        const int n = min(32, L - x0);
-        if (a.from_sigma) {
-          const uint8_t* row = N + (size_t)y * L + x0;
-          for (int k = 0; k < n; k += 4)
-            bits |= nonzero_nibble(*reinterpret_cast<const uint32_t*>(row + k)) << k;
-        } else {
-          const uint8_t* ex = N + (size_t)y * L + x0;
-          const uint8_t* ey = N + LL + (size_t)y * L + x0;
-          const uint8_t* eyd = N + LL + (size_t)wrapi(y - 1, L) * L + x0;
-          uint32_t bx = 0, by = 0, byd = 0;
-          for (int k = 0; k < n; k += 4) {
-            bx |= nibble_of(*reinterpret_cast<const uint32_t*>(ex + k)) << k;
-            by |= nibble_of(*reinterpret_cast<const uint32_t*>(ey + k)) << k;
-            byd |= nibble_of(*reinterpret_cast<const uint32_t*>(eyd + k)) << k;
-          }
-          const uint32_t left = N[(size_t)y * L + wrapi(x0 - 1, L)] & 1u;  // e_x(r - x^) at x0
-          bits = bx ^ ((bx << 1) | left) ^ by ^ byd;
-          if (n < 32) bits &= (1u << n) - 1u;
-        }
-      }
-      sig_cur[w] = bits;
-    }
-    __syncthreads();
-    int any = build_list(sig_cur, g, list, &misc[0]);
-    int count = misc[0];
-
-    int t = 0, flag = 0;
-    while (any) {
-      if (t >= a.max_steps) {
-        flag = 2;
-        break;
-      }
-      // flipped-link maps alternate by step parity: a partner CTA may still read
-      // the previous step's map while this step writes the other one
-      uint32_t* const flip = flipb + (t & 1) * 2 * g.nws;
-      if (t == 0) {
-        // ================= 1. first step: the planes start empty, so the
-        // message update reduces to the anyon terms; compute them densely
-        // for every site (32 sites per bitmap operation) instead of
-        // scattering the cone sections of the many initial anyons.
-        dense_terms<KW, false>(sig_cur, list, count, flip, g, planes, pl, lrow0, R0, plus, cword,
-                               lane_on);
-      } else if (warp_on) {
-        // ================= 1a. dense message update of this thread's band
-        Chain cH[KW], cL[KW];
-        uint32_t first[3][KW];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) load_words<KW>(my_rows + (size_t)k * LS, first[k]);
-#pragma unroll
-        for (int q = 0; q < KW; ++q) {
-          uint32_t ah[6], al[6];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            ah[k] = halo[k][q];
-            ah[3 + k] = first[k][q];
-          }
-#pragma unroll
-          for (int k = 0; k < 6; ++k) al[k] = ah[k] << 8;
-          cH[q].init(ah);
-          cL[q].init(al);
-        }
-        auto row = [&](int i, const uint32_t (&in)[KW]) {
-          uint32_t m[KW];
-#pragma unroll
-          for (int q = 0; q < KW; ++q) {
-            const uint32_t tH = cH[q].step(in[q]);
-            const uint32_t tL = cL[q].step(in[q] << 8);
-            m[q] = finish_word(tL, tH);
-          }
-          uint32_t out[KW];
-          if (KW == 1) {
-            if (plus) {
-              const uint32_t nb = __shfl_sync(0xffffffffu, m[0], left_lane);
-              out[0] = __funnelshift_r(nb, m[0], 8);
-            } else {
-              const uint32_t nb = __shfl_sync(0xffffffffu, m[0], right_lane);
-              out[0] = __funnelshift_r(m[0], nb, 24);
-            }
-          } else {
-            const uint32_t sendv = plus ? m[KW - 1] : m[0];
-            const uint32_t nb = __shfl_sync(0xffffffffu, sendv, plus ? left_lane : right_lane);
-            if (plus) {
-              out[0] = __funnelshift_r(nb, m[0], 8);
-#pragma unroll
-              for (int q = 1; q < KW; ++q) out[q] = __funnelshift_r(m[q - 1], m[q], 8);
-            } else {
-#pragma unroll
-              for (int q = 0; q + 1 < KW; ++q) out[q] = __funnelshift_r(m[q], m[q + 1], 24);
-              out[KW - 1] = __funnelshift_r(m[KW - 1], nb, 24);
-            }
-          }
-          if (lane_on) store_words<KW>(my_rows + (size_t)i * LS, out);
-        };
-#pragma unroll 4
-        for (int i = 0; i < g.H - 3; ++i) {
-          uint32_t in[KW];
-          load_words<KW>(my_rows + (size_t)(i + 3) * LS, in);
-          row(i, in);
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          uint32_t in[KW];
-#pragma unroll
-          for (int q = 0; q < KW; ++q) in[q] = halo[3 + k][q];
-          row(g.H - 3 + k, in);
-        }
-      }
-      // ================= 1b. anyon terms of steps after the first
-      if (t > 0) {
-        if (count <= g.cap && count <= g.sparse_max) {
-          // light-cone sections written per anyon, d = 3, 2, 1 (largest value
-          // first); a warp takes one anyon, lane = (plane, transverse offset), so
-          // the lanes of a store hit consecutive rows (distinct banks).  Each CTA
-          // writes the sections that fall in its rows.
-          __syncthreads();
-          auto pass = [&](auto dconst) {
-            constexpr int d = decltype(dconst)::value;
-            const uint8_t val = (uint8_t)(g.off + d - 1);
-            const int p = lane >> 3, jj = lane & 7;
-            const bool act = jj < 2 * d + 1;
-            const int nw = nt >> 5;
-            // four anyons per warp and iteration (independent loads, then stores)
-            for (int i0 = warp; i0 < count; i0 += 4 * nw) {
-              int e[4];
-#pragma unroll
-              for (int k = 0; k < 4; ++k) {
-                const int i = i0 + k * nw;
-                e[k] = (i < count) ? (int)list[i] : -1;
-              }
-#pragma unroll
-              for (int k = 0; k < 4; ++k) {
-                const int x0 = e[k] & 0xFF, y0 = e[k] >> 8;
-                if (act && e[k] >= 0) {
-                  const int row0 = (p < 2) ? y0 : x0;
-                  const int col0 = (p < 2) ? x0 : y0;
-                  const int col = wrapi((p % 2 == 0) ? col0 + d : col0 - d, L);
-                  const int R = wrapi(row0 + jj - d, L);
-                  if (CL == 1 || (R >= row_lo && R < row_hi))
-                    planes[(size_t)(p * g.rows_local + R - row_lo) * LS + col] = val;
-                }
-              }
-            }
-            __syncthreads();
-          };
-          pass(std::integral_constant<int, 3>{});
-          pass(std::integral_constant<int, 2>{});
-          pass(std::integral_constant<int, 1>{});
-        } else {
-          __syncthreads();  // the dense update above is complete
-          dense_terms<KW, true>(sig_cur, list, count, flip, g, planes, pl, lrow0, R0, plus, cword,
-                                lane_on);
-        }
-      }
-      // clear this step's flipped-link map (also the scratch of the dense terms)
-      __syncthreads();
-      for (int i = tid; i < 2 * g.nws; i += nt) flip[i] = 0;
-      // every plane of the cluster final; flip maps ready
-      Cluster<CL>::sync();
-      snapshot();  // halo rows for the next step
-      // ================= 2. forces and feedback for the anyons of this CTA's rows
-      uint64_t kstep = 0, kbal = 0;
-      if (a.move_thr) kstep = move_step_key(a.move_key, a.shot_offset + shot, t);
-      if (a.balance_rule) kbal = move_step_key(a.balance_key, a.shot_offset + shot, t);
-      auto decide = [&](int x, int y) -> int {
-        // Eqs. blahdef / degbreak on the offset-encoded fields (0xFF = none)
-        int dir = force_code(*plane_ptr<CL>(planes, g, 0, y, x), *plane_ptr<CL>(planes, g, 1, y, x),
-                             *plane_ptr<CL>(planes, g, 2, x, y), *plane_ptr<CL>(planes, g, 3, x, y),
-                             a.tie_order);
-        if (dir >= 5) dir = a.balance_rule ? balance_resolve(dir, kbal, y * L + x) : 0;
-        if (a.move_thr) {
-          const uint64_t u = splitmix64(kstep ^ (uint64_t)(y * L + x));
-          if (u < a.move_thr) dir = 1 + (int)(splitmix64(u) >> 62);
-        }
-        return dir;
-      };
-      auto apply = [&](int x, int y, int dir) {
-        // mark link <lo, lo + a^>; a link crossed from both ends is marked
-        // twice and flips once (the OR of Eq. ddfeedback)
-        const int ax = (dir <= 2) ? 0 : 1;
-        const int lx = (dir == 2) ? wrapi(x - 1, L) : x;
-        const int ly = (dir == 4) ? wrapi(y - 1, L) : y;
-        const int wlo = (ly << g.lws) + (lx >> 5);
-        // every CTA keeps the whole map (fire-and-forget ORs, the remote one
-        // through distributed shared memory)
-#pragma unroll
-        for (int r = 0; r < CL; ++r)
-          atomicOr(Cluster<CL>::at(flip, r) + ax * g.nws + wlo, 1u << (lx & 31));
-      };
-      if (count <= g.cap) {
-        // four anyons per thread and iteration: all field loads are issued before
-        // the first atomic (latency hiding with few warps per SM)
-        const int stride = (count + 31) >> 5, span = 32 * stride;
-        for (int i0 = tid; i0 < span; i0 += 4 * nt) {
-          int ex[4], ey[4], dir[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int i = i0 + k * nt;
-            const int idx = (i & 31) * stride + (i >> 5);
-            const bool ok = i < span && idx < count;
-            const int e = ok ? list[idx] : 0;
-            ex[k] = e & 0xFF;
-            ey[k] = e >> 8;
-            const bool mine = ok && (CL == 1 || (ey[k] >= row_lo && ey[k] < row_hi));
-            dir[k] = mine ? decide(ex[k], ey[k]) : 0;
-          }
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            if (dir[k]) apply(ex[k], ey[k], dir[k]);
-        }
-      } else {
-        for_each_anyon(list, count, sig_cur, g, [&](int x, int y) {
-          if (CL > 1 && (y < row_lo || y >= row_hi)) return;
-          const int dir = decide(x, y);
-          if (dir) apply(x, y, dir);
-        });
-      }
-      if (tid == 0) misc[0] = 0;  // list counter (count already read by every thread)
-      Cluster<CL>::sync();
-      // ================= 3. sigma and correction from the flipped links, new
-      //                   anyon list, early exit
-      any = apply_flips(sig_cur, flip, Cb, g, list, &misc[0], row_lo, row_hi);
-      count = misc[0];
-      ++t;
-    }
-    // ================= outputs: correction bytes, homology, steps, flag
-    // (each CTA holds the correction of its own rows)
-    uint8_t* outC = a.out_C + correction_offset_of(a, shot);
-    const int gpr = L / 4;  // 4-site groups per row
-    for (int ax = 0; ax < 2; ++ax) {
-      for (int i = tid; i < g.rows_local * gpr; i += nt) {
-        const int y = row_lo + i / gpr, x = (i - (i / gpr) * gpr) * 4;
-        const int w = (y << g.lws) + (x >> 5);
-        const uint32_t bits = Cb[ax * g.nws + w];
-        const uint32_t nib = (bits >> (x & 31)) & 0xFu;
-        *reinterpret_cast<uint32_t*>(outC + (size_t)ax * LL + (size_t)y * L + x) =
-            (nib * 0x00204081u) & 0x01010101u;
-      }
-    }
-    if (tid == 0) misc[1] = misc[2] = 0;
-    __syncthreads();
-    if (rank == 0) {
-      int wx = 0, wy = 0;
-      for (int i = tid; i < L; i += nt) {
-        // e_x((0, i)) and e_y((i, 0))
-        uint32_t bx = 0, by = 0;
-#pragma unroll
-        for (int r = 0; r < CL; ++r) {
-          const uint32_t* c = Cluster<CL>::at(Cb, r);
-          bx ^= c[i << g.lws];
-          by ^= c[g.nws + (i >> 5)] >> (i & 31);
-        }
-        wx ^= (int)(bx & 1);
-        wy ^= (int)(by & 1);
-        if (!a.from_sigma) {
-          wx ^= N[(size_t)i * L];
-          wy ^= N[LL + i];
-        }
-      }
-      if (wx) atomicXor(&misc[1], 1);
-      if (wy) atomicXor(&misc[2], 1);
-      __syncthreads();
-      if (tid == 0) {
-        a.out_steps[shot] = t;
-        if (a.from_sigma) {
-          a.out_cut[2 * shot] = (uint8_t)misc[1];
-          a.out_cut[2 * shot + 1] = (uint8_t)misc[2];
-          if (a.out_exhausted) a.out_exhausted[shot] = (uint8_t)(flag == 2);
-        } else {
-          a.out_flag[shot] = (uint8_t)(flag == 2 ? 2 : ((misc[1] | misc[2]) ? 1 : 0));
-        }
-      }
-    }
-    // partners may still read this CTA's correction share
-    Cluster<CL>::sync();
+    decode_shot<CL, KW>(a, g, smem, shot, G);
   }
   // no CTA of a cluster leaves while a partner could still reach its shared memory
   if (CL > 1) Cluster<CL>::sync();
@@ -794,7 +849,12 @@ int sparse_divisor_for(int L, int CL) {
   return CL == 2 ? 256 : 64;
 }
 
-bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, size_t& smem) {
+// Geometry of the on-chip sweep for L: CL (1 or 2 CTAs per shot), KW (words per
+// lane), bands and shared-memory layout.  warp_cap > 0 limits the warps of a
+// one-CTA geometry (the groups of the mixed-size kernel); such a request fails
+// for L > 128.
+bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, size_t& smem,
+               int warp_cap = 0) {
   if (L % 4 != 0 || L < 8 || L > 256) return false;
   if (m_max < 3) return false;  // the first-step fill assumes the d <= 3 terms fit below 0xFF
   if (L > 128 && L % 8 != 0) return false;
@@ -811,8 +871,9 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
   // 128), the taller band on a tie.  The sweep takes any height of at least 4
   // that divides the CTA's rows; other heights are used only where none of
   // these four fits.
-  const int max_warps = (CL == 1) ? 32 : 16;
-  const int target = L <= 64 ? 4 : std::min(16, L / 8);
+  if (warp_cap > 0 && CL != 1) return false;
+  const int max_warps = warp_cap > 0 ? std::min(32, warp_cap) : ((CL == 1) ? 32 : 16);
+  const int target = std::min(max_warps, L <= 64 ? 4 : std::min(16, L / 8));
   int best_H = 0, best_d = 1 << 30;
   for (int H : {4, 8, 16, 32}) {
     if (g.rows_local % H) continue;
@@ -856,7 +917,9 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
   while ((1 << lws) < wpr) ++lws;
   g.lws = lws;
   g.nws = L << lws;
-  if ((g.nws + threads - 1) / threads > 4) return false;  // apply_flips handles <= 4 words/thread
+  // the dense feedback pass handles at most this many words per thread
+  if ((g.nws + threads - 1) / threads > (CL == 1 ? kWordsPerThread<1> : kWordsPerThread<2>))
+    return false;
   g.off = 255 - m_max;
   g.cap = L * L < kListCap ? L * L : kListCap;
   g.sparse_max = L * L / sparse_divisor_for(L, CL);
@@ -879,6 +942,102 @@ struct LaunchShape {
 };
 std::mutex g_shape_mu;
 std::vector<LaunchShape> g_shapes;
+
+// ------------------------------------------------ mixed lattice sizes ----
+//
+// One persistent launch for a batch of shots of different sizes.  The items
+// (shots) are queued by group size, then largest L first, so that the long
+// shots start early and the short ones fill the tail, and every group takes
+// the next item from one counter when it has finished its last (work stealing
+// across sizes; every shot retires after its own number of steps).
+//   * pair items (128 < L <= 256) are decoded by the two CTAs of a cluster;
+//   * every other size has a group size of 512, 256, 128 or 64 threads (the
+//     smallest whose band geometry and shared memory fit): a CTA of 512
+//     threads starts as one group and halves whenever the item it holds needs
+//     a smaller group, the first half keeping the item and the second fetching
+//     its own, so that up to eight small lattices are decoded at once per CTA.
+// Each group has its own named barrier and its own slice of shared memory: the
+// 64-thread slice s (threads 64s .. 64s + 63) owns bytes [s, s + 1) * S / 8 of
+// the S-byte block, a group the slices of its threads.
+// Rank 0 of a cluster fetches pair items and shares the index over DSMEM; the
+// first other index it sees ends the pair phase for both CTAs (rank 0 keeps
+// that item).
+constexpr int kMixThreads = 512;
+constexpr int kMixMaxClasses = 8;
+
+struct MixArgs {
+  DecodeArgs a;                   // outputs, offsets, rules; shot_list = item -> shot
+  const uint8_t* item_class;      // item -> class
+  int64_t n_pair, n_items;
+  size_t slice_bytes;             // shared memory of a 64-thread slice (S / 8)
+  int group_threads[kMixMaxClasses];  // 0 for pair classes
+  FastGeom geom[kMixMaxClasses];
+};
+
+// named barrier of the group of `gsz` threads starting at thread `gofs`:
+// 0 for the whole CTA, then 1-2 (256), 3-6 (128), 7-14 (64)
+__device__ __forceinline__ int mix_barrier(int gsz, int gofs) {
+  if (gsz >= kMixThreads) return 0;
+  if (gsz == 256) return 1 + gofs / 256;
+  if (gsz == 128) return 3 + gofs / 128;
+  return 7 + gofs / 64;
+}
+
+__global__ void __launch_bounds__(kMixThreads, 1) mixed_kernel(MixArgs m) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ long long s_item[16];
+  const int tid = threadIdx.x;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int csize = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  long long k = -1;
+  // ---- pair items: both CTAs of the cluster on one shot
+  if (m.n_pair > 0 && csize == 2) {
+    const Grp whole{tid, kMixThreads, 0};
+    for (;;) {
+      if (rank == 0 && tid == 0) s_item[15] = (long long)atomicAdd(m.a.queue, 1u);
+      cluster.sync();
+      const long long kk = *cluster.map_shared_rank(&s_item[15], 0);
+      // rank 0 must not overwrite the index before its partner has read it
+      cluster.sync();
+      if (kk >= m.n_pair) {
+        k = (rank == 0) ? kk : -1;
+        break;
+      }
+      decode_shot<2, 2>(m.a, m.geom[m.item_class[kk]], smem, m.a.shot_list[kk], whole);
+    }
+  }
+  // ---- every other item: groups of 512, 256, 128 or 64 threads
+  int gsz = kMixThreads, gofs = 0;
+  for (;;) {
+    const int bar = mix_barrier(gsz, gofs);
+    const Grp G{tid - gofs, gsz, bar};
+    if (k < 0) {
+      if (G.tid == 0) s_item[bar] = (long long)atomicAdd(m.a.queue, 1u);
+      G.sync();
+      k = s_item[bar];
+      G.sync();
+    }
+    if (k >= m.n_items) break;
+    const int c = m.item_class[k];
+    if (m.group_threads[c] < gsz) {
+      // the item needs a smaller group: halve; the first half keeps it
+      gsz >>= 1;
+      if (tid - gofs >= gsz) {
+        gofs += gsz;
+        k = -1;
+      }
+      continue;
+    }
+    decode_shot<1, 1>(m.a, m.geom[c], smem + (size_t)(gofs / 64) * m.slice_bytes,
+                      m.a.shot_list[k], G);
+    k = -1;
+  }
+  __syncthreads();
+  // a partner's pair-phase accesses to this CTA's shared memory are over, but
+  // keep the exit ordered as in the one-size kernel
+  if (csize == 2) cluster.sync();
+}
 
 template <int CL, int KW>
 int launch_t(const DecodeArgs& a, const FastGeom& g, int threads, size_t smem,
@@ -966,6 +1125,108 @@ int launch_fast(const DecodeArgs& a, cudaStream_t stream) {
   if (CL == 2 && KW == 2) return launch_t<2, 2>(a, g, threads, smem, stream);
   set_error("no on-chip kernel variant for L=%d", a.L);
   return QCA_ERR_UNSUPPORTED;
+}
+
+// Host side of the mixed-size kernel.  Shared memory available to one CTA.
+constexpr size_t kMixSmemLimit = 227 * 1024;
+
+// Group size of each size in the mixed kernel: 0 for a pair item (two-CTA
+// cluster), else 512, 256, 128 or 64 threads, the smallest whose band geometry
+// fits its warps and whose shared memory times the groups of a CTA fits the
+// limit; -1 if the on-chip sweep does not take the size.
+int mixed_group_threads(int L, int m_max) {
+  int CL, KW, th;
+  FastGeom g;
+  size_t sm;
+  if (!make_geom(L, m_max, CL, KW, g, th, sm)) return -1;
+  if (CL == 2) return sm <= kMixSmemLimit ? 0 : -1;
+  for (int gs = 64; gs <= kMixThreads; gs *= 2) {
+    if (!make_geom(L, m_max, CL, KW, g, th, sm, gs / 32)) continue;
+    const size_t per = (sm + 127) & ~(size_t)127;
+    if (per * (kMixThreads / gs) <= kMixSmemLimit) return gs;
+  }
+  return -1;
+}
+
+int launch_mixed(const DecodeArgs& a, const uint8_t* item_class, const int* sizes,
+                 const int* group_threads, int nclass, int64_t n_pair, int64_t n_items,
+                 cudaStream_t stream) {
+  if (nclass > kMixMaxClasses) {
+    set_error("mixed-size decode: more than %d sizes", kMixMaxClasses);
+    return QCA_ERR_UNSUPPORTED;
+  }
+  MixArgs m;
+  memset(&m, 0, sizeof(m));
+  m.a = a;
+  m.item_class = item_class;
+  m.n_pair = n_pair;
+  m.n_items = n_items;
+  // S: the largest of the pair classes' shared memory and, per other class,
+  // its shared memory times the groups of its size in a CTA
+  size_t S = 0;
+  size_t cls_smem[kMixMaxClasses] = {};
+  for (int c = 0; c < nclass; ++c) {
+    int CL, KW, th;
+    const int gs = group_threads[c];
+    m.group_threads[c] = gs;
+    if (gs < 0) continue;
+    if (!make_geom(sizes[c], a.m_max, CL, KW, m.geom[c], th, cls_smem[c], gs > 0 ? gs / 32 : 0) ||
+        (gs == 0) != (CL == 2)) {
+      set_error("mixed-size decode: no geometry for L = %d", sizes[c]);
+      return QCA_ERR_UNSUPPORTED;
+    }
+    cls_smem[c] = (cls_smem[c] + 127) & ~(size_t)127;
+    S = std::max(S, gs == 0 ? cls_smem[c] : cls_smem[c] * (kMixThreads / gs));
+  }
+  S = (S + 1023) & ~(size_t)1023;  // eight slices, each a multiple of 128 bytes
+  if (S > kMixSmemLimit) {
+    set_error("mixed-size decode: %zu bytes of shared memory needed", S);
+    return QCA_ERR_UNSUPPORTED;
+  }
+  m.slice_bytes = S / 8;
+  const int CL = n_pair > 0 ? 2 : 1;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(kMixThreads);
+  cfg.dynamicSmemBytes = S;
+  cfg.stream = stream;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int units = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    for (const LaunchShape& sh : g_shapes)
+      if (sh.dev == dev && sh.cl == CL && sh.kw == -1 && sh.threads == kMixThreads && sh.smem == S)
+        units = sh.units;
+  }
+  e = cudaFuncSetAttribute(mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S);
+  if (e != cudaSuccess) return cuda_fail(e, "mixed kernel smem attribute");
+  if (units < 0) {
+    cfg.gridDim = dim3((unsigned)(CL * sms));
+    e = cudaOccupancyMaxActiveClusters(&units, mixed_kernel, &cfg);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed kernel occupancy query");
+    if (units < 1) {
+      set_error("mixed-size kernel does not fit on an SM");
+      return QCA_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_shapes.push_back({dev, CL, -1, kMixThreads, S, units});
+  }
+  int64_t grid = units;
+  // no more clusters than items (each takes at least one)
+  const int64_t need = (n_items + CL - 1) / CL;
+  if (grid > need) grid = need > 0 ? need : 1;
+  cfg.gridDim = dim3((unsigned)(grid * CL));
+  e = cudaLaunchKernelEx(&cfg, mixed_kernel, m);
+  return cuda_fail(e, "mixed kernel launch");
 }
 
 }  // namespace qca

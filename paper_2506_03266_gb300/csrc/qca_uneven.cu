@@ -2,16 +2,20 @@
 //
 // A plan groups the shots by L once (host side) and keeps on the device the
 // shot lists, the byte offsets of every shot's [2][L][L] block in the packed
-// input, and one work counter per size.  A decode then launches, for every
-// size present, a persistent kernel whose CTAs take shots from that size's
-// counter (work stealing, each shot retiring on its own step count); the
-// launches run concurrently on side streams forked from and joined back to the
-// caller's stream, so the whole decode can be captured in one CUDA graph.
+// input, and the work counters.  A decode then makes one persistent launch of
+// the mixed-size on-chip kernel over every shot whose size it takes (a single
+// queue, largest L first, work stealing across sizes, each shot retiring on
+// its own step count).  Shots of other sizes (or packed off a 4-byte boundary)
+// go to per-size persistent launches of their own kernel on side streams
+// forked from and joined back to the caller's stream, and that per-size form
+// can also be chosen for every size (qca_uneven_plan_set_mode).  Either way
+// the decode can be captured in one CUDA graph.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
+#include <utility>
 #include <mutex>
 #include <vector>
 
@@ -60,6 +64,17 @@ __global__ void __launch_bounds__(256) sample_uneven_kernel(const int32_t* Ls, c
 using namespace qca;
 
 struct qca_uneven_plan_s {
+  int mode = 0;                  // 0: one mixed-size launch; 1: one launch per size
+  // mixed-size queue: the shots of the sizes the on-chip sweep takes (and whose
+  // blocks are 4-byte aligned), pairs first, then by group size, then largest
+  // L first
+  std::vector<int> msizes;       // its sizes in queue order
+  std::vector<int> mgroup;       // group size of each (0 = pair), as planned
+  std::vector<int64_t> mcount;   // shots of each
+  std::vector<int> in_mixed;     // per size of `sizes`: 1 if it is in the queue
+  int64_t m_items = 0;
+  int32_t* d_mitems = nullptr;   // item -> shot
+  uint8_t* d_mclass = nullptr;   // item -> index into msizes
   int64_t shots = 0;
   int64_t total_bytes = 0;
   int device = 0;
@@ -142,16 +157,58 @@ int qca_uneven_plan_create(const int32_t* L_host, int64_t shots, int64_t* offset
   std::vector<int32_t> list(shots);
   std::vector<int64_t> fill = p->start;
   for (int64_t s = 0; s < shots; ++s) list[fill[cls(L_host[s])]++] = (int32_t)s;
+  // the mixed-size queue: sizes the on-chip sweep takes with the default
+  // options, aligned blocks only, at most kMixClasses sizes (the largest),
+  // ordered by group size (pairs first, then 512 .. 64 threads) and then by
+  // decreasing L
+  constexpr int kMixClasses = 8;
+  p->in_mixed.assign(distinct.size(), 0);
+  std::vector<std::pair<int, int>> order;  // (group rank, size index)
+  for (int i = (int)distinct.size() - 1; i >= 0; --i) {
+    if (p->bytewise[i] || (int)order.size() >= kMixClasses) continue;
+    const int gs = qca::mixed_group_threads(distinct[i], 255);
+    if (gs < 0) continue;
+    order.push_back({gs == 0 ? 1 << 20 : gs, i});
+  }
+  std::stable_sort(order.begin(), order.end(),
+                   [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+                     return a.first > b.first;
+                   });
+  std::vector<int32_t> mitems;
+  std::vector<uint8_t> mclass;
+  for (const auto& o : order) {
+    const int i = o.second;
+    p->in_mixed[i] = 1;
+    const uint8_t c = (uint8_t)p->msizes.size();
+    p->msizes.push_back(distinct[i]);
+    p->mgroup.push_back(o.first == (1 << 20) ? 0 : o.first);
+    p->mcount.push_back(cnt[i]);
+    for (int64_t j = 0; j < cnt[i]; ++j) {
+      mitems.push_back(list[p->start[i] + j]);
+      mclass.push_back(c);
+    }
+  }
+  p->m_items = (int64_t)mitems.size();
   cudaError_t e = cudaSuccess;
   const size_t nc = distinct.size();
   if (shots > 0) {
     e = cudaMalloc(&p->d_list, sizeof(int32_t) * shots);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_offsets, sizeof(int64_t) * shots);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_counters, sizeof(unsigned) * (nc ? nc : 1));
+    // one counter per size, and the mixed queue's after them
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_counters, sizeof(unsigned) * (nc + 1));
     if (e == cudaSuccess)
       e = cudaMemcpy(p->d_list, list.data(), sizeof(int32_t) * shots, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
       e = cudaMemcpy(p->d_offsets, offs.data(), sizeof(int64_t) * shots, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess && p->m_items > 0) {
+    e = cudaMalloc(&p->d_mitems, sizeof(int32_t) * p->m_items);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_mclass, p->m_items);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_mitems, mitems.data(), sizeof(int32_t) * p->m_items,
+                     cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_mclass, mclass.data(), p->m_items, cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
   for (size_t i = 0; i < nc && e == cudaSuccess; ++i) {
@@ -175,12 +232,23 @@ int qca_uneven_plan_create(const int32_t* L_host, int64_t shots, int64_t* offset
 int qca_uneven_plan_destroy(qca_uneven_plan_t p) {
   if (!p) return QCA_OK;
   cudaFree(p->d_list);
+  cudaFree(p->d_mitems);
+  cudaFree(p->d_mclass);
   cudaFree(p->d_offsets);
   cudaFree(p->d_counters);
   for (auto s : p->side) cudaStreamDestroy(s);
   for (auto e : p->join) cudaEventDestroy(e);
   if (p->fork) cudaEventDestroy(p->fork);
   delete p;
+  return QCA_OK;
+}
+
+int qca_uneven_plan_set_mode(qca_uneven_plan_t p, int mode) {
+  if (!p || (mode != 0 && mode != 1)) {
+    set_error("qca_uneven_plan_set_mode: bad arguments");
+    return QCA_ERR_ARG;
+  }
+  p->mode = mode;
   return QCA_OK;
 }
 
@@ -233,10 +301,35 @@ int qca_decode_uneven_async(qca_uneven_plan_t p, const uint8_t* errors, int max_
   qca_default_config(&c);
   if (cfg) c = *cfg;
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMemsetAsync(p->d_counters, 0, sizeof(unsigned) * p->sizes.size(), st);
-  if (e == cudaSuccess) e = cudaEventRecord(p->fork, st);
+  // the mixed-size launch takes the queued sizes unless the per-size form is
+  // chosen, or the options leave the on-chip sweep (v != 3, m_max < 3) or
+  // change a planned group size (tuning overrides)
+  bool mixed = p->mode == 0 && p->m_items > 0 && c.v == 3;
+  for (size_t i = 0; mixed && i < p->msizes.size(); ++i)
+    mixed = mixed_group_threads(p->msizes[i], c.m_max) == p->mgroup[i];
+  cudaError_t e = cudaMemsetAsync(p->d_counters, 0, sizeof(unsigned) * (p->sizes.size() + 1), st);
+  if (e != cudaSuccess) return cuda_fail(e, "uneven decode counters");
+  if (mixed) {
+    DecodeArgs a;
+    int rc = fill_decode_args(a, errors, p->msizes[0], p->m_items, max_steps, rng_seed, &c);
+    if (rc) return rc;
+    a.out_C = out_correction;
+    a.out_steps = out_steps;
+    a.out_flag = out_logical_fail;
+    a.shot_list = p->d_mitems;
+    a.offsets = p->d_offsets;
+    a.queue = p->d_counters + p->sizes.size();
+    int64_t n_pair = 0;
+    for (size_t i = 0; i < p->mgroup.size(); ++i)
+      if (p->mgroup[i] == 0) n_pair += p->mcount[i];
+    rc = launch_mixed(a, p->d_mclass, p->msizes.data(), p->mgroup.data(), (int)p->msizes.size(),
+                      n_pair, p->m_items, st);
+    if (rc) return rc;
+  }
+  e = cudaEventRecord(p->fork, st);
   if (e != cudaSuccess) return cuda_fail(e, "uneven decode fork");
   for (size_t i = 0; i < p->sizes.size(); ++i) {
+    if (mixed && p->in_mixed[i]) continue;
     e = cudaStreamWaitEvent(p->side[i], p->fork, 0);
     if (e != cudaSuccess) return cuda_fail(e, "uneven decode fork wait");
     DecodeArgs a;

@@ -110,3 +110,38 @@ def test_uneven_decode_in_cuda_graph(built):
         torch.cuda.synchronize()
         assert torch.equal(out[1], s0) and torch.equal(out[2], f0) and torch.equal(out[0], C0)
     plan.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("tie_order,balance_rule", [(0, 0), (1, 1)])
+def test_mixed_launch_matches_per_size_launches(built, tie_order, balance_rule):
+    """The single mixed-size launch (pairs of CTAs for L > 128, whole CTAs for
+    64 < L <= 128, four groups per CTA for L <= 64) against one launch per
+    size, bit for bit, on nine on-chip sizes (the ninth and smallest runs in a
+    launch of its own: the queue takes eight) and two odd sizes packed last
+    (byte-access sweep); the small sizes also against the oracle."""
+    _cuda()
+    rng = np.random.default_rng(11)
+    even = [256, 192, 136, 128, 80, 64, 40, 24, 12]
+    L = np.array(rng.permutation(np.repeat(even, [3, 4, 4, 6, 8, 10, 12, 14, 16])).tolist()
+                 + [33, 33, 21, 21], dtype=np.int32)
+    thr = np.full(len(L), oracle.prob_threshold(0.06), dtype=np.uint64)
+    plan = qca.UnevenPlan(L)
+    N = plan.sample(thr, seed=9)
+    kw = dict(max_steps=400, rng_seed=13, tie_order=tie_order, balance_rule=balance_rule)
+    mixed = [t.cpu().numpy() for t in plan.decode(N, **kw)]
+    plan.set_mode("per_size")
+    per = [t.cpu().numpy() for t in plan.decode(N, **kw)]
+    plan.set_mode("mixed")
+    for a, b in zip(mixed, per):
+        np.testing.assert_array_equal(a, b)
+    Nh = N.cpu().numpy()
+    for s in [i for i in range(len(L)) if L[i] <= 40][:30]:
+        n = 2 * int(L[s]) ** 2
+        blk = Nh[plan.offsets[s]:plan.offsets[s] + n].reshape(2, L[s], L[s])
+        Co, so, fo = oracle.decode_shot(blk, max_steps=400, tie_order=tie_order,
+                                        balance_rule=balance_rule, seed=13, shot=s)
+        assert mixed[1][s] == so and mixed[2][s] == fo, s
+        np.testing.assert_array_equal(
+            mixed[0][plan.offsets[s]:plan.offsets[s] + n].reshape(Co.shape), Co)
+    plan.close()
