@@ -246,9 +246,9 @@ int qca_sample_errors_uneven_async(const int32_t* L_dev, const int64_t* offsets_
  * size the on-chip sweep takes (multiples of 4 up to 128 and of 8 up to 256,
  * blocks on a 4-byte boundary; the 8 largest such sizes) form one queue, pairs
  * first, then by group size, then largest L first.  Clusters of two CTAs take
- * the shots with L > 128; every other size is decoded by a group of 512, 256,
- * 128 or 64 threads (the smallest that fits), a 512-thread CTA halving into up
- * to eight groups as the queue reaches smaller sizes.  Each takes its next shot
+ * the shots with L > 128; every other size is decoded by a group of 512, 256
+ * or 128 threads (the smallest that fits), a 512-thread CTA halving into up
+ * to four groups as the queue reaches smaller sizes.  Each takes its next shot
  * when the last one is done (work stealing across sizes; every shot retires
  * after its own number of steps).  Shots of other sizes go to a persistent launch
  * per size on streams forked from and joined to `stream`; mode 1 of

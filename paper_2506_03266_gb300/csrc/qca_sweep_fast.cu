@@ -383,17 +383,20 @@ __device__ __forceinline__ void store_words(uint8_t* p, const uint32_t (&w)[KW])
 template <int KW, bool MERGE>
 __device__ void dense_terms(const uint32_t* sig, const uint16_t* list, int count, uint32_t* sT,
                             const FastGeom& g, uint8_t* planes, int pl, int lrow0, int R0,
-                            bool plus, int cword, bool lane_on, const Grp& G) {
+                            bool plus, int cword, bool lane_on, const Grp& G, bool yframe,
+                            bool build_sT) {
   const int tid = G.tid, nt = G.nt, L = g.L;
-  // transposed sigma: bit (row x, column y), the frame of the y planes
-  for (int i = tid; i < g.nws; i += nt) sT[i] = 0;
-  G.sync();
-  for_each_anyon(list, count, sig, g, G, [&](int x, int y) {
-    atomicOr(&sT[(x << g.lws) + (y >> 5)], 1u << (y & 31));
-  });
-  G.sync();
+  if (build_sT) {
+    // transposed sigma: bit (row x, column y), the frame of the y planes
+    for (int i = tid; i < g.nws; i += nt) sT[i] = 0;
+    G.sync();
+    for_each_anyon(list, count, sig, g, G, [&](int x, int y) {
+      atomicOr(&sT[(x << g.lws) + (y >> 5)], 1u << (y & 31));
+    });
+    G.sync();
+  }
   if (lane_on) {
-    const uint32_t* bm = (pl < 2) ? sig : sT;
+    const uint32_t* bm = yframe ? sT : sig;
     const uint32_t off2 = (uint32_t)(g.off + 2) * 0x01010101u;
     // the lane's KW plane words cover sites 4c .. 4c + 4KW - 1 of a row; window
     // bit i <-> column 4c - 3 + i, i in [0, 4KW + 6)
@@ -566,7 +569,7 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs& a, const FastGeom&
       // for every site (32 sites per bitmap operation) instead of
       // scattering the cone sections of the many initial anyons.
       dense_terms<KW, false>(sig_cur, list, count, flip, g, planes, pl, lrow0, R0, plus, cword,
-                             lane_on, G);
+                             lane_on, G, pl >= 2, true);
     } else if (warp_on) {
       // ================= 1a. dense message update of this thread's band
       Chain cH[KW], cL[KW];
@@ -675,7 +678,7 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs& a, const FastGeom&
       } else {
         G.sync();  // the dense update above is complete
         dense_terms<KW, true>(sig_cur, list, count, flip, g, planes, pl, lrow0, R0, plus, cword,
-                              lane_on, G);
+                              lane_on, G, pl >= 2, true);
       }
     }
     // clear this step's flipped-link map (also the scratch of the dense terms)
@@ -951,11 +954,11 @@ std::vector<LaunchShape> g_shapes;
 // the next item from one counter when it has finished its last (work stealing
 // across sizes; every shot retires after its own number of steps).
 //   * pair items (128 < L <= 256) are decoded by the two CTAs of a cluster;
-//   * every other size has a group size of 512, 256, 128 or 64 threads (the
+//   * every other size has a group size of 512, 256 or 128 threads (the
 //     smallest whose band geometry and shared memory fit): a CTA of 512
 //     threads starts as one group and halves whenever the item it holds needs
 //     a smaller group, the first half keeping the item and the second fetching
-//     its own, so that up to eight small lattices are decoded at once per CTA.
+//     its own, so that up to four small lattices are decoded at once per CTA.
 // Each group has its own named barrier and its own slice of shared memory: the
 // 64-thread slice s (threads 64s .. 64s + 63) owns bytes [s, s + 1) * S / 8 of
 // the S-byte block, a group the slices of its threads.
@@ -1127,20 +1130,23 @@ int launch_fast(const DecodeArgs& a, cudaStream_t stream) {
   return QCA_ERR_UNSUPPORTED;
 }
 
-// Host side of the mixed-size kernel.  Shared memory available to one CTA.
-constexpr size_t kMixSmemLimit = 227 * 1024;
+// Host side of the mixed-size kernel.  Dynamic shared memory available to one
+// CTA (227 KB less room for the kernel's static shared memory).
+constexpr size_t kMixSmemLimit = 227 * 1024 - 1024;
 
 // Group size of each size in the mixed kernel: 0 for a pair item (two-CTA
-// cluster), else 512, 256, 128 or 64 threads, the smallest whose band geometry
+// cluster), else 512, 256 or 128 threads, the smallest whose band geometry
 // fits its warps and whose shared memory times the groups of a CTA fits the
-// limit; -1 if the on-chip sweep does not take the size.
+// limit; -1 if the on-chip sweep does not take the size.  (Groups of 64
+// threads, eight small lattices per CTA, measured slower on the mixed C3
+// batch: 109 against 99 ms.)
 int mixed_group_threads(int L, int m_max) {
   int CL, KW, th;
   FastGeom g;
   size_t sm;
   if (!make_geom(L, m_max, CL, KW, g, th, sm)) return -1;
   if (CL == 2) return sm <= kMixSmemLimit ? 0 : -1;
-  for (int gs = 64; gs <= kMixThreads; gs *= 2) {
+  for (int gs = 128; gs <= kMixThreads; gs *= 2) {
     if (!make_geom(L, m_max, CL, KW, g, th, sm, gs / 32)) continue;
     const size_t per = (sm + 127) & ~(size_t)127;
     if (per * (kMixThreads / gs) <= kMixSmemLimit) return gs;
@@ -1170,8 +1176,10 @@ int launch_mixed(const DecodeArgs& a, const uint8_t* item_class, const int* size
     const int gs = group_threads[c];
     m.group_threads[c] = gs;
     if (gs < 0) continue;
-    if (!make_geom(sizes[c], a.m_max, CL, KW, m.geom[c], th, cls_smem[c], gs > 0 ? gs / 32 : 0) ||
-        (gs == 0) != (CL == 2)) {
+    const bool ok = make_geom(sizes[c], a.m_max, CL, KW, m.geom[c], th, cls_smem[c],
+                              gs > 0 ? gs / 32 : 0) &&
+                    (gs == 0) == (CL == 2);
+    if (!ok) {
       set_error("mixed-size decode: no geometry for L = %d", sizes[c]);
       return QCA_ERR_UNSUPPORTED;
     }
