@@ -80,6 +80,7 @@ def lib():
             "qca_decode_batch_noalloc": ([vp, i32, i64, i32, u64, vp, vp, vp, cfgp, vp], i32),
             "qca_uneven_draw": ([i64, u64, vp, vp], i32),
             "qca_set_tuning": ([i32, i32, i32], i32),
+            "qca_set_cluster_ctas": ([i32, i32], i32),
             "qca_get_tuning": ([i32, vp, vp, vp], i32),
             "qca_autotune": ([i32, i64, ctypes.c_double, u64, i32, vp, vp, vp], i32),
             "qca_uneven_plan_create": ([vp, i64, vp, vp, ctypes.POINTER(vp)], i32),
@@ -383,6 +384,11 @@ def decode_batch_noalloc(errors, out, max_steps: int = 4096, rng_seed: int = 0, 
 
 def set_tuning(L: int, band_height: int = 0, sparse_divisor: int = 0):
     _check(lib().qca_set_tuning(L, band_height, sparse_divisor))
+
+
+def set_cluster_ctas(L: int, ctas: int):
+    """CTAs per cluster (2 or 4) of the on-chip sweep for 128 < L <= 256."""
+    _check(lib().qca_set_cluster_ctas(L, ctas))
 
 
 def get_tuning(L: int):

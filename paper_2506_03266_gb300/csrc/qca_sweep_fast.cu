@@ -182,7 +182,7 @@ __device__ __forceinline__ int wrapi(int i, int L) { return i < 0 ? i + L : (i >
 template <int CL>
 __device__ __forceinline__ uint8_t* plane_ptr(uint8_t* planes, const FastGeom& g, int p, int R,
                                               int c) {
-  const int owner = (CL == 1) ? 0 : (R >= g.rows_local ? 1 : 0);
+  const int owner = (CL == 1) ? 0 : (CL == 2 ? (R >= g.rows_local ? 1 : 0) : R / g.rows_local);
   const int lr = R - owner * g.rows_local;
   return Cluster<CL>::at(planes, owner) + ((size_t)(p * g.rows_local + lr)) * g.ls + c;
 }
@@ -266,8 +266,10 @@ __device__ __forceinline__ int apply_flips(uint32_t* sig, const uint32_t* flip, 
     snew[k] = s;
     n += __popc(s);
     if (y >= row_lo && y < row_hi) {
-      Cb[w] ^= fx;
-      Cb[g.nws + w] ^= fy;
+      // the correction of this CTA's rows: [x-links, y-links][local row][word]
+      const int lw = ((y - row_lo) << g.lws) + j;
+      Cb[lw] ^= fx;
+      Cb[(g.rows_local << g.lws) + lw] ^= fy;
     }
   }
   // new anyon list (same layout as build_list)
@@ -451,7 +453,7 @@ __device__ void dense_terms(const uint32_t* sig, const uint16_t* list, int count
 // Most bitmap words a thread handles in the dense feedback pass: geometries
 // are accepted only within it (make_geom).
 template <int CL>
-constexpr int kWordsPerThread = CL == 1 ? 2 : 4;
+constexpr int kWordsPerThread = CL == 1 ? 2 : (CL == 2 ? 4 : 8);
 
 // Decodes one shot with the group G (the whole CTA or a slice of it, CL = 1;
 // or the CTAs of a 2-CTA cluster, each with its whole block, CL = 2) on the
@@ -467,8 +469,9 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs& a, const FastGeom&
   uint32_t* const bits_base = reinterpret_cast<uint32_t*>(smem + g.plane_bytes);
   uint32_t* const sig_cur = bits_base;            // sigma (the full lattice in every CTA)
   uint32_t* const flipb = bits_base + g.nws;      // [step parity][x-links, y-links][nws]
-  uint32_t* const Cb = flipb + 4 * g.nws;         // [2][nws]: correction, this CTA's rows
-  uint16_t* list = reinterpret_cast<uint16_t*>(Cb + 2 * g.nws);
+  uint32_t* const Cb = flipb + 4 * g.nws;         // [2][rows_local][words]: this CTA's rows
+  const int cbk = g.rows_local << g.lws;          // words of one link kind of Cb
+  uint16_t* list = reinterpret_cast<uint16_t*>(Cb + 2 * cbk);
   int* misc = reinterpret_cast<int*>(list + ((g.cap + 7) & ~7));
 
   const int tid = G.tid, nt = G.nt;
@@ -519,7 +522,7 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs& a, const FastGeom&
   // ---- init: bitmaps cleared, sigma measured (every CTA of the cluster holds
   //      the full sigma); the planes are written whole by the first step
   {
-    for (int i = tid; i < 6 * g.nws; i += nt) flipb[i] = 0;  // flip maps and Cb
+    for (int i = tid; i < 4 * g.nws + 2 * cbk; i += nt) flipb[i] = 0;  // flip maps and Cb
     if (tid == 0) misc[0] = 0;
   }
   // sigma, 32 sites per thread and word; Def. synch_ccqs: parity of the four
@@ -759,27 +762,24 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs& a, const FastGeom&
   const int gpr = L / 4;  // 4-site groups per row
   for (int ax = 0; ax < 2; ++ax) {
     for (int i = tid; i < g.rows_local * gpr; i += nt) {
-      const int y = row_lo + i / gpr, x = (i - (i / gpr) * gpr) * 4;
-      const int w = (y << g.lws) + (x >> 5);
-      const uint32_t bits = Cb[ax * g.nws + w];
+      const int yl = i / gpr, y = row_lo + yl, x = (i - yl * gpr) * 4;
+      const uint32_t bits = Cb[ax * cbk + (yl << g.lws) + (x >> 5)];
       const uint32_t nib = (bits >> (x & 31)) & 0xFu;
       *reinterpret_cast<uint32_t*>(outC + (size_t)ax * LL + (size_t)y * L + x) =
           (nib * 0x00204081u) & 0x01010101u;
     }
   }
   if (tid == 0) misc[1] = misc[2] = 0;
-  G.sync();
+  // every CTA's last correction update is done before rank 0 reads the
+  // partners' shares below
+  csync();
   if (rank == 0) {
     int wx = 0, wy = 0;
     for (int i = tid; i < L; i += nt) {
-      // e_x((0, i)) and e_y((i, 0))
-      uint32_t bx = 0, by = 0;
-#pragma unroll
-      for (int r = 0; r < CL; ++r) {
-        const uint32_t* c = Cluster<CL>::at(Cb, r);
-        bx ^= c[i << g.lws];
-        by ^= c[g.nws + (i >> 5)] >> (i & 31);
-      }
+      // e_x((0, i)): row i, held by CTA i / rows_local; e_y((i, 0)): row 0, CTA 0
+      const int owner = (CL == 1) ? 0 : i / g.rows_local;
+      const uint32_t bx = Cluster<CL>::at(Cb, owner)[(i - owner * g.rows_local) << g.lws];
+      const uint32_t by = Cb[cbk + (i >> 5)] >> (i & 31);
       wx ^= (int)(bx & 1);
       wy ^= (int)(by & 1);
       if (!a.from_sigma) {
@@ -806,12 +806,14 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs& a, const FastGeom&
 }
 
 template <int CL, int KW>
-__global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArgs a, FastGeom g) {
+__global__ void __launch_bounds__(CL == 1 ? 1024 : (CL == 2 ? 512 : 256), CL == 4 ? 2 : 1)
+    fast_kernel(DecodeArgs a, FastGeom g) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int rank = Cluster<CL>::rank();
   const int tid = threadIdx.x;
   const Grp G{tid, (int)blockDim.x, 0};
-  int* misc = reinterpret_cast<int*>(smem + g.plane_bytes + (size_t)7 * g.nws * 4 +
+  int* misc = reinterpret_cast<int*>(smem + g.plane_bytes +
+                                     (size_t)(5 * g.nws + 2 * (g.rows_local << g.lws)) * 4 +
                                      (size_t)((g.cap + 7) & ~7) * 2);
   const int nclusters = gridDim.x / CL;
   const int cid = blockIdx.x / CL;
@@ -842,6 +844,9 @@ __global__ void __launch_bounds__(CL == 1 ? 1024 : 512, 1) fast_kernel(DecodeArg
 // are scattered per anyon, as a divisor of L^2 (0 = 64).
 int g_tune_H[QCA_MAX_L + 1];
 int g_tune_div[QCA_MAX_L + 1];
+// Sizes above 128 decoded by a cluster of four CTAs (64 rows each, two clusters
+// sharing each SM pair) instead of two.
+int g_cluster4[QCA_MAX_L + 1];
 
 // Anyon count (as a divisor of L^2) below which a step writes the anyon terms
 // per anyon: measured best 64 for the one-CTA kernel and 256 for the two-CTA
@@ -849,7 +854,7 @@ int g_tune_div[QCA_MAX_L + 1];
 // scatters every anyon.
 int sparse_divisor_for(int L, int CL) {
   if (g_tune_div[L] > 0) return g_tune_div[L];
-  return CL == 2 ? 256 : 64;
+  return CL >= 2 ? 256 : 64;
 }
 
 // Geometry of the on-chip sweep for L: CL (1 or 2 CTAs per shot), KW (words per
@@ -861,7 +866,7 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
   if (L % 4 != 0 || L < 8 || L > 256) return false;
   if (m_max < 3) return false;  // the first-step fill assumes the d <= 3 terms fit below 0xFF
   if (L > 128 && L % 8 != 0) return false;
-  CL = (L > 128) ? 2 : 1;
+  CL = (L > 128) ? (g_cluster4[L] ? 4 : 2) : 1;
   KW = (L / 4 > 32) ? 2 : 1;
   g.L = L;
   g.rows_local = L / CL;
@@ -875,7 +880,7 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
   // that divides the CTA's rows; other heights are used only where none of
   // these four fits.
   if (warp_cap > 0 && CL != 1) return false;
-  const int max_warps = warp_cap > 0 ? std::min(32, warp_cap) : ((CL == 1) ? 32 : 16);
+  const int max_warps = warp_cap > 0 ? std::min(32, warp_cap) : (CL == 1 ? 32 : (CL == 2 ? 16 : 8));
   const int target = std::min(max_warps, L <= 64 ? 4 : std::min(16, L / 8));
   int best_H = 0, best_d = 1 << 30;
   for (int H : {4, 8, 16, 32}) {
@@ -925,13 +930,17 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
     return false;
   g.off = 255 - m_max;
   g.cap = L * L < kListCap ? L * L : kListCap;
+  if (CL == 4) g.cap = std::min(g.cap, 1024);  // two CTAs of a cluster of four share an SM
   g.sparse_max = L * L / sparse_divisor_for(L, CL);
   // row pitch: L + 4 bytes (one extra bank per row); L + 8 keeps the 8-byte
   // alignment of the 64-bit accesses used with two words per lane
   g.ls = L + (KW == 2 ? 8 : 4);
   g.plane_bytes = (size_t)4 * g.rows_local * g.ls;
   // sigma, two flipped-link maps (x and y each), correction (x and y), list
-  smem = g.plane_bytes + (size_t)7 * g.nws * 4 + (size_t)((g.cap + 7) & ~7) * 2 + 64;
+  // sigma, two flipped-link maps (x and y each), the correction of the CTA's
+  // rows (x and y), list
+  smem = g.plane_bytes + (size_t)(5 * g.nws + 2 * (g.rows_local << lws)) * 4 +
+         (size_t)((g.cap + 7) & ~7) * 2 + 64;
   return true;
 }
 
@@ -1113,7 +1122,7 @@ int fast_path_for(int L, int v, int m_max) {
   FastGeom g;
   size_t smem;
   if (!make_geom(L, m_max, CL, KW, g, threads, smem)) return 0;
-  return CL;
+  return CL > 2 ? 2 : CL;
 }
 
 int launch_fast(const DecodeArgs& a, cudaStream_t stream) {
@@ -1126,6 +1135,7 @@ int launch_fast(const DecodeArgs& a, cudaStream_t stream) {
   }
   if (CL == 1 && KW == 1) return launch_t<1, 1>(a, g, threads, smem, stream);
   if (CL == 2 && KW == 2) return launch_t<2, 2>(a, g, threads, smem, stream);
+  if (CL == 4 && KW == 2) return launch_t<4, 2>(a, g, threads, smem, stream);
   set_error("no on-chip kernel variant for L=%d", a.L);
   return QCA_ERR_UNSUPPORTED;
 }
@@ -1250,6 +1260,15 @@ int qca_set_tuning(int L, int band_height, int sparse_divisor) {
   }
   g_tune_H[L] = band_height;
   g_tune_div[L] = sparse_divisor;
+  return QCA_OK;
+}
+
+int qca_set_cluster_ctas(int L, int ctas) {
+  if (L <= 128 || L > 256 || L % 8 != 0 || (ctas != 2 && ctas != 4)) {
+    set_error("qca_set_cluster_ctas: L must be a multiple of 8 in (128, 256], ctas 2 or 4");
+    return QCA_ERR_ARG;
+  }
+  g_cluster4[L] = ctas == 4 ? 1 : 0;
   return QCA_OK;
 }
 

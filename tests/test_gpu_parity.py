@@ -93,6 +93,25 @@ def test_parity_large_lattices_sampled(L):
     assert_same(gpu_decode(N, 300), oracle.decode_batch(N, max_steps=300), f"L{L}")
 
 
+@pytest.mark.parametrize("L", [136, 160, 192, 200, 248, 256])
+def test_four_cta_clusters_bit_exact(L):
+    """Clusters of four CTAs (a quarter of the rows each, two clusters per SM
+    pair) against two-CTA clusters and the oracle, with the rule options on."""
+    shots = 16
+    N = oracle.sample_errors(L, shots, 0.07, seed=L + 5)
+    kw = dict(tie_order=1, balance_rule=1, rng_seed=3)
+    two = gpu_decode(N, 300, **kw)
+    qca.set_cluster_ctas(L, 4)
+    try:
+        four = gpu_decode(N, 300, **kw)
+    finally:
+        qca.set_cluster_ctas(L, 2)
+    assert_same(four, two, f"L{L}")
+    import oracle_pool
+    cpu = oracle_pool.decode_many(N[:6], max_steps=300, tie_order=1, balance_rule=1, seed=3)
+    assert_same((four[0][:6], four[1][:6], four[2][:6]), cpu, f"L{L} oracle")
+
+
 @pytest.mark.parametrize("p", [0.08, 0.09])
 def test_cluster_path_near_and_above_threshold(p):
     """The two-CTA cluster (L = 256) against the oracle where decoding is hard:
