@@ -272,10 +272,11 @@ int qca_decode_uneven_async(qca_uneven_plan_t plan, const uint8_t* errors, int m
  * An override that does not fit a size is ignored. */
 int qca_set_tuning(int L, int band_height, int sparse_divisor);
 /* CTAs per cluster of the on-chip sweep for 128 < L <= 256 (L % 8 == 0): 2 (each
- * CTA holds half the rows of every plane, one CTA per SM) or 4 (a quarter of
- * the rows, 256 threads; two clusters' CTAs share an SM, so one shot's
- * latency-bound phases overlap another's message update).  Process-wide;
- * QCA_ERR_ARG outside that range. */
+ * CTA holds half the rows of every plane, one CTA per SM; the default) or 4 (a
+ * quarter of the rows, 256 threads; two clusters' CTAs share an SM, so one
+ * shot's latency-bound phases overlap another's message update; measured
+ * slower on GB300 at L = 192 and 256).  Same results either way.
+ * Process-wide; QCA_ERR_ARG outside that range. */
 int qca_set_cluster_ctas(int L, int ctas);
 /* Current effective values and the resulting threads per CTA (QCA_ERR_UNSUPPORTED
  * if L has no on-chip kernel). */

@@ -926,8 +926,9 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
   g.lws = lws;
   g.nws = L << lws;
   // the dense feedback pass handles at most this many words per thread
-  if ((g.nws + threads - 1) / threads > (CL == 1 ? kWordsPerThread<1> : kWordsPerThread<2>))
-    return false;
+  const int max_per =
+      CL == 1 ? kWordsPerThread<1> : (CL == 2 ? kWordsPerThread<2> : kWordsPerThread<4>);
+  if ((g.nws + threads - 1) / threads > max_per) return false;
   g.off = 255 - m_max;
   g.cap = L * L < kListCap ? L * L : kListCap;
   if (CL == 4) g.cap = std::min(g.cap, 1024);  // two CTAs of a cluster of four share an SM

@@ -103,6 +103,7 @@ def test_four_cta_clusters_bit_exact(L):
     two = gpu_decode(N, 300, **kw)
     qca.set_cluster_ctas(L, 4)
     try:
+        assert qca.get_tuning(L)[2] == 256  # the four-CTA form, not a fallback
         four = gpu_decode(N, 300, **kw)
     finally:
         qca.set_cluster_ctas(L, 2)
