@@ -58,12 +58,9 @@ CAP_REACH_STEPS = (255 + 2) // 3
 # DRAM traffic of the dominant kernel per decoded shot at L = 256, p = 0.05
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 4000 shots,
 # profiles/fast_kernel_L256_p005_full.md), valid only for the kernel source
-# whose SHA-256 prefixes are recorded with it; reported as null otherwise.  The
-# second prefix differs from the profiled source in host code only (the band
-# height chosen for sizes where no 4-, 8-, 16- or 32-row band fits); the L = 256
-# launch and the device code are the same.
-TRAFFIC_PER_SHOT = {"sha256_prefixes": ("5df71a97652cf0dd", "72bd69cc3d200392"), "L": 256,
-                    "p": 0.05, "bytes_per_shot": (526.072320e6 + 479.626240e6) / 4000}
+# whose SHA-256 prefix is recorded with it; reported as null otherwise.
+TRAFFIC_PER_SHOT = {"sha256_prefixes": ("d5bd4e62f8bf3461",), "L": 256,
+                    "p": 0.05, "bytes_per_shot": (524.815616e6 + 479.569408e6) / 4000}
 
 
 def traffic_per_launch(L, p, shots):
