@@ -59,7 +59,28 @@ namespace qca {
 
 namespace {
 
-constexpr int kListCap = 16384;  // anyon-list entries (the whole lattice for L <= 128)
+constexpr int kListCap = 16384;  // anyon-list entries (at most)
+
+// Periodic-orbit fast-forward.  With the deterministic rules (no random moves,
+// a balanced axis stays) the step is a function of sigma and the planes, and
+// the planes after a step's message update are a function of the last
+// kOrbitWindow syndromes alone: a message grows by 3 per step from at most
+// off + 2 and is gone (0xFF) after ceil(255 / 3) = 85 steps.  So if the anyon
+// set of the last kOrbitWindow + 1 steps repeats that of the steps P earlier,
+// the whole state repeats with period P, the shot never ends, and the budget's
+// outcome is known: sigma and the planes at max_steps equal those P-periodic
+// images, and the correction, which gains the same flips every period, repeats
+// with period 2P.  A shot in such an orbit stops at the first step congruent
+// to max_steps modulo 2P and reports max_steps and flag 2 with that
+// correction, as if it had run to the budget.  The anyon sets of the steps of
+// the current run of steps with at most kOrbitAnyons anyons are kept as sorted
+// 16-bit sites in a ring of 64-bit entries; steps with more anyons cost nothing.
+constexpr int kOrbitWindow = 88;
+constexpr int kOrbitAnyons = 4;
+// ring entries: periods up to kOrbitRing - 1 - kOrbitWindow = 935 steps are
+// found (the orbits seen at L = 24 to 192 repeat after 1 step, or L to 15 L
+// steps for pairs chasing around the torus)
+constexpr int kOrbitRing = 1024;
 
 struct FastGeom {
   int L;
@@ -455,6 +476,60 @@ __device__ void dense_terms(const uint32_t* sig, const uint16_t* list, int count
 template <int CL>
 constexpr int kWordsPerThread = CL == 1 ? 2 : (CL == 2 ? 4 : 8);
 
+// One step of the orbit watch, run by the 32 lanes of one warp at the start of
+// a step t with at most kOrbitAnyons anyons (sigma and the list are those of
+// step t; every step since `from` had that few): records the step's anyon set
+// in the ring and looks for the smallest period P whose last kOrbitWindow + 1
+// anyon sets, all since `from`, repeat.  Returns the step at which the shot can
+// stop with the budget's outcome, or -1.
+__device__ __forceinline__ int orbit_watch(uint64_t* ring, const uint16_t* list, int count, int t,
+                                           int from, int max_steps, int lane) {
+  constexpr int ring_mask = kOrbitRing - 1;
+  uint64_t e;
+  {
+    uint32_t q[kOrbitAnyons];
+#pragma unroll
+    for (int k = 0; k < kOrbitAnyons; ++k) q[k] = k < count ? list[k] : 0xFFFFu;
+    // sorting network for four keys
+    auto cs = [](uint32_t& u, uint32_t& v) {
+      const uint32_t lo = min(u, v), hi = max(u, v);
+      u = lo;
+      v = hi;
+    };
+    cs(q[0], q[1]);
+    cs(q[2], q[3]);
+    cs(q[0], q[2]);
+    cs(q[1], q[3]);
+    cs(q[1], q[2]);
+    e = (uint64_t)q[0] | ((uint64_t)q[1] << 16) | ((uint64_t)q[2] << 32) | ((uint64_t)q[3] << 48);
+  }
+  if (lane == 0) ring[t & ring_mask] = e;
+  // P <= t - kOrbitWindow - from keeps every compared step in the run;
+  // P + kOrbitWindow <= ring_mask keeps them in the ring and off this step's
+  // entry
+  const int pmax = min(t - kOrbitWindow - from, ring_mask - kOrbitWindow);
+  if (pmax < 1) return -1;
+  int best = 0x7fffffff;
+  for (int P = 1 + lane; P <= pmax; P += 32) {
+    if (ring[(t - P) & ring_mask] != e) continue;
+    bool ok = true;
+    for (int j = 1; j <= kOrbitWindow && ok; ++j)
+      ok = ring[(t - j) & ring_mask] == ring[(t - P - j) & ring_mask];
+    if (ok) {
+      best = P;
+      break;  // this lane's candidates increase
+    }
+  }
+  best = __reduce_min_sync(0xffffffffu, best);
+  if (best == 0x7fffffff) return -1;
+  // the remaining R = max_steps - t steps are n whole periods and r steps;
+  // the correction repeats with period 2P
+  const int R = max_steps - t, n = R / best, r = R - n * best;
+  int stop = t + r + ((n & 1) ? best : 0);
+  if (stop == t) stop = t + 2 * best;  // R = n P with n even and >= 2
+  return stop;
+}
+
 // Decodes one shot with the group G (the whole CTA or a slice of it, CL = 1;
 // or the CTAs of a 2-CTA cluster, each with its whole block, CL = 2) on the
 // shared-memory state at `smem` laid out for geometry g.  Every thread of the
@@ -473,6 +548,7 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs& a, const FastGeom&
   const int cbk = g.rows_local << g.lws;          // words of one link kind of Cb
   uint16_t* list = reinterpret_cast<uint16_t*>(Cb + 2 * cbk);
   int* misc = reinterpret_cast<int*>(list + ((g.cap + 7) & ~7));
+  uint64_t* const ring = reinterpret_cast<uint64_t*>(misc + 16);  // orbit watch
 
   const int tid = G.tid, nt = G.nt;
   const int warp = tid >> 5, lane = tid & 31;
@@ -523,7 +599,11 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs& a, const FastGeom&
   //      the full sigma); the planes are written whole by the first step
   {
     for (int i = tid; i < 4 * g.nws + 2 * cbk; i += nt) flipb[i] = 0;  // flip maps and Cb
-    if (tid == 0) misc[0] = 0;
+    if (tid == 0) {
+      misc[0] = 0;
+      misc[5] = -1;  // orbit stop step
+      misc[6] = 0;   // start of the run of steps with few anyons
+    }
   }
   // sigma, 32 sites per thread and word; Def. synch_ccqs: parity of the four
   // links incident to r (or the given anyon indicator)
@@ -558,10 +638,26 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs& a, const FastGeom&
   int count = misc[0];
 
   int t = 0, flag = 0;
+  // orbit watch: t_stop is -1 while watching, -2 when the rules draw random
+  // numbers (the step is then not a function of the state alone), else the
+  // step at which the shot stops
+  int t_stop = (a.move_thr == 0 && a.balance_rule == QCA_BALANCE_STAY) ? -1 : -2;
   while (any) {
-    if (t >= a.max_steps) {
+    if (t >= a.max_steps || t == t_stop) {
+      // the budget ran out, or the shot is in a periodic orbit and its state
+      // is that of the budget's last step
       flag = 2;
+      t = a.max_steps;
       break;
+    }
+    if (t_stop == -1 && warp == 0) {
+      // misc[6]: first step of the current run of steps with few anyons
+      if (count > kOrbitAnyons) {
+        if (lane == 0) misc[6] = t + 1;
+      } else {
+        const int stop = orbit_watch(ring, list, count, t, misc[6], a.max_steps, lane);
+        if (stop >= 0 && lane == 0) misc[5] = stop;  // read by all after the step's barriers
+      }
     }
     // flipped-link maps alternate by step parity: a partner CTA may still read
     // the previous step's map while this step writes the other one
@@ -754,6 +850,7 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs& a, const FastGeom&
     any = apply_flips<kWordsPerThread<CL>>(sig_cur, flip, Cb, g, list, &misc[0], row_lo, row_hi,
                                             G);
     count = misc[0];
+    if (t_stop == -1) t_stop = misc[5];
     ++t;
   }
   // ================= outputs: correction bytes, homology, steps, flag
@@ -930,18 +1027,19 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
       CL == 1 ? kWordsPerThread<1> : (CL == 2 ? kWordsPerThread<2> : kWordsPerThread<4>);
   if ((g.nws + threads - 1) / threads > max_per) return false;
   g.off = 255 - m_max;
-  g.cap = L * L < kListCap ? L * L : kListCap;
+  // up to half the lattice in the list (more anyons than that are iterated
+  // from the bitmap; a noise rate below 0.5 rarely comes near it)
+  g.cap = std::min(L * L / 2, kListCap);
   if (CL == 4) g.cap = std::min(g.cap, 1024);  // two CTAs of a cluster of four share an SM
   g.sparse_max = L * L / sparse_divisor_for(L, CL);
   // row pitch: L + 4 bytes (one extra bank per row); L + 8 keeps the 8-byte
   // alignment of the 64-bit accesses used with two words per lane
   g.ls = L + (KW == 2 ? 8 : 4);
   g.plane_bytes = (size_t)4 * g.rows_local * g.ls;
-  // sigma, two flipped-link maps (x and y each), correction (x and y), list
   // sigma, two flipped-link maps (x and y each), the correction of the CTA's
-  // rows (x and y), list
+  // rows (x and y), list, 64 bytes of counters, orbit ring
   smem = g.plane_bytes + (size_t)(5 * g.nws + 2 * (g.rows_local << lws)) * 4 +
-         (size_t)((g.cap + 7) & ~7) * 2 + 64;
+         (size_t)((g.cap + 7) & ~7) * 2 + 64 + (size_t)kOrbitRing * 8;
   return true;
 }
 

@@ -36,6 +36,19 @@ def decode_many(N_np, shot0=0, **kw):
             np.array([o[2] for o in out], np.uint8))
 
 
+def _run_one(args):
+    import oracle
+    fn, n, kw = args
+    return getattr(oracle, fn)(n, **kw)
+
+
+def run_many(fn, jobs):
+    """oracle.<fn>(n, **kw) for each (n, kw) of jobs, in parallel; shots of
+    different sizes and options may be mixed."""
+    return _pool().map(_run_one, [(fn, np.ascontiguousarray(n), kw) for n, kw in jobs],
+                       chunksize=1)
+
+
 def close():
     global _POOL
     if _POOL is not None:
