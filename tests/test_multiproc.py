@@ -64,3 +64,12 @@ def test_shard_ranges_tile_the_job():
         seen.extend(range(s0, s0 + n))
     assert seen == list(range(100))
     assert bench.reduce_time_max(3.5) == 3.5
+
+
+def test_executed_site_updates_leave_out_exhausted_shots():
+    # shots that ran out of the budget report it as their step count but may
+    # have been stopped early in a periodic orbit: their steps are not counted
+    steps = np.array([10, 4096, 7, 4096])
+    flags = np.array([0, 2, 1, 2])
+    assert bench.executed_site_updates(steps, flags, 8) == (10 + 7) * 64
+    assert bench.executed_site_updates(steps, flags, np.array([8, 16, 4, 32])) == 10 * 64 + 7 * 16

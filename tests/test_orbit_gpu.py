@@ -98,6 +98,7 @@ def test_orbit_shots_in_the_mixed_size_launch(noise):
     shots = [(s, L) for s, L, _ in ORBITS]
     Ls = np.array([L for _, L in shots], dtype=np.int32)
     plan = qca.UnevenPlan(Ls)
+    plan.set_mode("mixed")
     flat = np.zeros(max(int(plan.offsets[i]) + 2 * L * L for i, (_, L) in enumerate(shots)),
                     dtype=np.uint8)
     for i, (s, L) in enumerate(shots):

@@ -90,11 +90,13 @@ def test_uneven_sampler_and_decoder_against_oracle(built):
 
 
 @pytest.mark.gpu
-def test_uneven_decode_in_cuda_graph(built):
+@pytest.mark.parametrize("mode", ["per_size", "mixed"])
+def test_uneven_decode_in_cuda_graph(built, mode):
     _cuda()
     shots = 600
     L, thr = qca.uneven_draw(shots, 5)
     plan = qca.UnevenPlan(L)
+    plan.set_mode(mode)
     N = plan.sample(thr, seed=5)
     C0, s0, f0 = plan.decode(N, max_steps=800)  # uncaptured call sizes the workspaces
     torch.cuda.synchronize()
@@ -129,10 +131,10 @@ def test_mixed_launch_matches_per_size_launches(built, tie_order, balance_rule):
     plan = qca.UnevenPlan(L)
     N = plan.sample(thr, seed=9)
     kw = dict(max_steps=400, rng_seed=13, tie_order=tie_order, balance_rule=balance_rule)
+    plan.set_mode("mixed")
     mixed = [t.cpu().numpy() for t in plan.decode(N, **kw)]
     plan.set_mode("per_size")
     per = [t.cpu().numpy() for t in plan.decode(N, **kw)]
-    plan.set_mode("mixed")
     for a, b in zip(mixed, per):
         np.testing.assert_array_equal(a, b)
     Nh = N.cpu().numpy()
