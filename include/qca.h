@@ -229,8 +229,8 @@ typedef struct qca_uneven_plan_s* qca_uneven_plan_t;
 int qca_uneven_plan_create(const int32_t* L_host, int64_t shots, int64_t* offsets_host,
                            int64_t* total_bytes, qca_uneven_plan_t* out_plan);
 int qca_uneven_plan_destroy(qca_uneven_plan_t plan);
-/* Launch form of qca_decode_uneven_async for this plan: 0 one mixed-size
- * persistent launch, 1 (default) one persistent launch per size. */
+/* Launch form of qca_decode_uneven_async for this plan: 0 (default) one
+ * mixed-size persistent launch, 1 one persistent launch per size. */
 int qca_uneven_plan_set_mode(qca_uneven_plan_t plan, int mode);
 /* Device array of the plan's block offsets (int64 [shots]), owned by the plan. */
 int qca_uneven_plan_offsets_device(qca_uneven_plan_t plan, const int64_t** offsets_device);
@@ -242,18 +242,19 @@ int qca_sample_errors_uneven_async(const int32_t* L_dev, const int64_t* offsets_
                                    const uint64_t* thr_dev, int64_t shots, uint64_t seed,
                                    uint8_t* out_errors, void* stream);
 
-/* Decode a packed uneven batch.  Default (mode 1 of qca_uneven_plan_set_mode):
- * one persistent launch per size, each on a stream forked from and joined to
- * `stream`, so that the sizes run side by side.  Mode 0: one persistent launch
- * for the shots of every size the on-chip sweep takes (multiples of 4 up to
- * 128 and of 8 up to 256, blocks on a 4-byte boundary; the 8 largest such
- * sizes), queued pairs first, then by group size, then largest L first.
+/* Decode a packed uneven batch.  Default (mode 0 of qca_uneven_plan_set_mode):
+ * one persistent launch for the shots of every size the on-chip sweep takes
+ * (multiples of 4 up to 128 and of 8 up to 256, blocks on a 4-byte boundary;
+ * the 8 largest such sizes), queued pairs first, then by group size, then
+ * largest L first.
  * Clusters of two CTAs take the shots with L > 128; every other size is
  * decoded by a group of 512, 256 or 128 threads (the smallest that fits), a
  * 512-thread CTA halving into up to four groups as the queue reaches smaller
  * sizes; each takes its next shot when the last one is done (work stealing
  * across sizes; every shot retires after its own number of steps); shots of
- * other sizes still go to per-size launches.  Only kernel launches, memset and
+ * other sizes go to per-size launches.  Mode 1: one persistent launch per
+ * size, each on a stream forked from and joined to `stream`, so that the sizes
+ * run side by side.  Only kernel launches, memset and
  * event operations are enqueued, so the call can be captured in a CUDA graph
  * once one uncaptured call has sized the library's workspaces.  Outputs are
  * bit-identical to decoding each shot with qca_decode_batch in either mode. */

@@ -437,8 +437,8 @@ class UnevenPlan:
         self.total_bytes = total.value
 
     def set_mode(self, mode: str):
-        """"per_size" (default): one persistent launch per size; "mixed": one
-        persistent launch over every size the on-chip sweep takes."""
+        """"mixed" (default): one persistent launch over every size the on-chip
+        sweep takes; "per_size": one persistent launch per size."""
         _check(lib().qca_uneven_plan_set_mode(self.handle, {"mixed": 0, "per_size": 1}[mode]))
 
     def close(self):

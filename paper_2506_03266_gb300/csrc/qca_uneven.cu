@@ -2,17 +2,14 @@
 //
 // A plan groups the shots by L once (host side) and keeps on the device the
 // shot lists, the byte offsets of every shot's [2][L][L] block in the packed
-// input, and the work counters.  A decode makes one persistent launch per size
-// on side streams forked from and joined back to the caller's stream (the
-// default), or, with qca_uneven_plan_set_mode(plan, 0), one persistent launch
-// of the mixed-size on-chip kernel over every shot whose size it takes (a
-// single queue, largest L first, work stealing across sizes, each shot
-// retiring on its own step count) with per-size launches for the rest (sizes
-// it does not take, blocks packed off a 4-byte boundary).  The per-size form is
-// the faster on GB300: its one-size kernels run the small sizes at 64
-// registers and up to 32 warps per SM, where the mixed kernel, which also
-// holds the two-CTA form, is held to 16.  Either way the decode can be captured
-// in one CUDA graph.
+// input, and the work counters.  A decode makes one persistent launch of the
+// mixed-size on-chip kernel over every shot whose size it takes (a single
+// queue, largest L first, work stealing across sizes, each shot retiring on
+// its own step count).  Shots of other sizes (or packed off a 4-byte boundary)
+// go to per-size persistent launches of their own kernel on side streams
+// forked from and joined back to the caller's stream, and that per-size form
+// can also be chosen for every size (qca_uneven_plan_set_mode).  Either way
+// the decode can be captured in one CUDA graph.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -67,7 +64,7 @@ __global__ void __launch_bounds__(256) sample_uneven_kernel(const int32_t* Ls, c
 using namespace qca;
 
 struct qca_uneven_plan_s {
-  int mode = 1;                  // 0: one mixed-size launch; 1 (default): one launch per size
+  int mode = 0;                  // 0 (default): one mixed-size launch; 1: one launch per size
   // mixed-size queue: the shots of the sizes the on-chip sweep takes (and whose
   // blocks are 4-byte aligned), pairs first, then by group size, then largest
   // L first
