@@ -54,7 +54,7 @@ struct TiledGeom {
   // slot layout (byte offsets)
   size_t o_sig, o_flip, o_C, slot;
   // shared memory layout (byte offsets)
-  size_t s_band, s_sband, s_M, s_D, s_bar, s_misc, smem;
+  size_t s_band, s_sband, s_D, s_bar, s_misc, smem;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -156,7 +156,6 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
 
   uint8_t* band = smem + g.s_band;                                         // [2][kTRows][L]
   uint32_t* sband = reinterpret_cast<uint32_t*>(smem + g.s_sband);         // [2][kTRows][W]
-  uint32_t* M = reinterpret_cast<uint32_t*>(smem + g.s_M);                 // [kTB][cols]
   uint32_t* D = reinterpret_cast<uint32_t*>(smem + g.s_D);                 // [3][kTB][W]
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + g.s_bar);             // [2]
   int* misc = reinterpret_cast<int*>(smem + g.s_misc);
@@ -329,93 +328,99 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
           D[(size_t)(kTB + r) * W + w] = d2;
           D[(size_t)(2 * kTB + r) * W + w] = d3;
         }
-        // transverse window min over 7 rows, rolling down the band: with pair
-        // mins q(j) = min(row j, row j + 1), min(rows r .. r + 6) =
-        // min(q(r), q(r + 2), q(r + 4), row r + 6)  (4 mins per half-word)
+        __syncthreads();  // the dilated rows are complete
+        // fused message update of the band, one 4-site column word per thread:
+        // every staged row is shifted by 3 sites along the byte axis as it is
+        // loaded (funnel shift with the neighbouring column word, wrapping at
+        // the row end).  The shift commutes with the bytewise min over rows and
+        // with the saturating add, so the transverse min over 7 rows (rolling
+        // down the band, 3 mins per half-word and row), the +3 and the anyon
+        // terms then give the output word directly.
+        const bool plus = (p % 2) == 0;  // m^{+a} reads from r - 3 a^
+        uint32_t* out = reinterpret_cast<uint32_t*>(plane(dst, p)) + (size_t)R0 * cols;
+        const uint32_t v1 = (uint32_t)(g.off) * 0x01010101u;
         for (int kc = tid; kc < cols; kc += nt) {
           const uint32_t* col = reinterpret_cast<const uint32_t*>(Bk) + kc;
-          uint32_t qh[5], ql[5], rh, rl;
-          {
-            uint32_t h[6], l[6];
+          const int kn = plus ? (kc == 0 ? cols - 1 : kc - 1) : (kc + 1 == cols ? 0 : kc + 1);
+          const uint32_t* nbc = reinterpret_cast<const uint32_t*>(Bk) + kn;
+          auto shifted = [&](int j) -> uint32_t {
+            const uint32_t w = col[(size_t)j * cols], nb = nbc[(size_t)j * cols];
+            return plus ? __funnelshift_r(nb, w, 8) : __funnelshift_r(w, nb, 24);
+          };
+          // the d <= 3 cones of the word's four sites read positions
+          // 4 kc - 3 .. 4 kc + 2 (m^+) or 4 kc + 1 .. 4 kc + 6 (m^-) of the
+          // dilated rows; bit positions of the six-bit test and of each d
+          const int pos6 = twrap(4 * kc + (plus ? -3 : 1), L);
+          int posd[3];
 #pragma unroll
-            for (int j = 0; j < 6; ++j) {
-              const uint32_t w = col[(size_t)j * cols];
-              h[j] = w & 0xFF00FF00u;
-              l[j] = w & 0x00FF00FFu;
-            }
+          for (int d = 1; d <= 3; ++d) posd[d - 1] = twrap(4 * kc + (plus ? -d : d), L);
+          // rolling window over staged rows a(j): pair mins q, quad mins u,
+          // out(r) = min(u(r), u(r + 3)) = min of staged rows r .. r + 6
+          uint32_t ah[7], al[7];
 #pragma unroll
-            for (int j = 0; j < 5; ++j) {
-              qh[j] = __vminu2(h[j], h[j + 1]);
-              ql[j] = __vminu2(l[j], l[j + 1]);
-            }
-            rh = h[5];
-            rl = l[5];
+          for (int j = 0; j < 6; ++j) {
+            const uint32_t w = shifted(j);
+            ah[j] = w & 0xFF00FF00u;
+            al[j] = w & 0x00FF00FFu;
           }
-#pragma unroll 4
+          uint32_t qh[6], ql[6], uh[3], ul[3];
+#pragma unroll
+          for (int j = 0; j < 5; ++j) {
+            qh[j] = __vminu2(ah[j], ah[j + 1]);
+            ql[j] = __vminu2(al[j], al[j + 1]);
+          }
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            uh[j] = __vminu2(qh[j], qh[j + 2]);
+            ul[j] = __vminu2(ql[j], ql[j + 2]);
+          }
+          uint32_t lasth = ah[5], lastl = al[5];
+#pragma unroll
           for (int r = 0; r < kTB; ++r) {
-            const uint32_t w = col[(size_t)(r + 6) * cols];
+            // consume staged row r + 6: q(r + 5), u(r + 3), out(r)
+            const uint32_t w = shifted(r + 6);
             const uint32_t h6 = w & 0xFF00FF00u, l6 = w & 0x00FF00FFu;
-            const uint32_t mh = __vminu2(__vminu2(qh[0], qh[2]), __vminu2(qh[4], h6));
-            const uint32_t ml = __vminu2(__vminu2(ql[0], ql[2]), __vminu2(ql[4], l6));
+            const uint32_t q5h = __vminu2(lasth, h6), q5l = __vminu2(lastl, l6);
+            const uint32_t u3h = __vminu2(qh[3], q5h), u3l = __vminu2(ql[3], q5l);
+            const uint32_t mh = __vminu2(uh[0], u3h), ml = __vminu2(ul[0], u3l);
             // +3 saturating at 0xFF while each byte sits alone in a 16-bit lane:
             // clamp at 0xFC, then add (no carry leaves the lane)
-            M[(size_t)r * cols + kc] = (__vminu2(mh, 0xFC00FC00u) + 0x03000300u) |
-                                       (__vminu2(ml, 0x00FC00FCu) + 0x00030003u);
+            uint32_t v = (__vminu2(mh, 0xFC00FC00u) + 0x03000300u) |
+                         (__vminu2(ml, 0x00FC00FCu) + 0x00030003u);
+            // roll: q(r + 1 ..) and u(r + 1 ..)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               qh[j] = qh[j + 1];
               ql[j] = ql[j + 1];
             }
-            qh[4] = __vminu2(rh, h6);
-            ql[4] = __vminu2(rl, l6);
-            rh = h6;
-            rl = l6;
-          }
-        }
-        __syncthreads();
-        // shift by 3 sites along the byte axis, anyon terms
-        const bool plus = (p % 2) == 0;  // m^{+a} reads from r - 3 a^
-        uint32_t* out = reinterpret_cast<uint32_t*>(plane(dst, p)) + (size_t)R0 * cols;
-        const uint32_t v1 = (uint32_t)(g.off) * 0x01010101u;
-        // items idx = r * cols + kc (r < kTB), stepped by nt without division
-        int r = tid / cols, kc = tid - r * cols;
-        while (r < kTB) {
-          const uint32_t* Mr = M + (size_t)r * cols;
-          uint32_t s;
-          if (plus) {
-            const int km = kc == 0 ? cols - 1 : kc - 1;
-            s = __funnelshift_r(Mr[km], Mr[kc], 8);
-          } else {
-            const int kp = kc + 1 == cols ? 0 : kc + 1;
-            s = __funnelshift_r(Mr[kc], Mr[kp], 24);
-          }
-          uint32_t v = s;
-          // terms: the smallest d wins (d = 3 first, overwritten by smaller d),
-          // and every term lies below every propagated value, so it replaces it.
-          // The d <= 3 cones of the word's four sites read positions
-          // 4 kc - 3 .. 4 kc + 2 (m^+) or 4 kc + 1 .. 4 kc + 6 (m^-) of the
-          // dilated rows, and D_3 contains D_2 and D_1: if those six bits of
-          // D_3 are clear there is no term.
-          const uint32_t* D3 = D + (size_t)(2 * kTB + r) * W;
-          if (bits6(D3, W, twrap(4 * kc + (plus ? -3 : 1), L))) {
-            uint32_t T = 0u, any = 0u;
+            qh[4] = q5h;
+            ql[4] = q5l;
+            uh[0] = uh[1];
+            ul[0] = ul[1];
+            uh[1] = uh[2];
+            ul[1] = ul[2];
+            uh[2] = u3h;
+            ul[2] = u3l;
+            lasth = h6;
+            lastl = l6;
+            // terms: the smallest d wins (d = 3 first, overwritten by smaller
+            // d), and every term lies below every propagated value, so it
+            // replaces it; D_3 contains D_2 and D_1, so if the six bits of D_3
+            // are clear there is no term
+            if (bits6(D + (size_t)(2 * kTB + r) * W, W, pos6)) {
+              uint32_t T = 0u, any = 0u;
 #pragma unroll
-            for (int d = 3; d >= 1; --d) {
-              const int pos = twrap(4 * kc + (plus ? -d : d), L);
-              const uint32_t m = nib_mask(bits4(D + (size_t)((d - 1) * kTB + r) * W, W, pos));
-              T = (T & ~m) | ((v1 + (uint32_t)(d - 1) * 0x01010101u) & m);
-              any |= m;
+              for (int d = 3; d >= 1; --d) {
+                const uint32_t m = nib_mask(bits4(D + (size_t)((d - 1) * kTB + r) * W, W, posd[d - 1]));
+                T = (T & ~m) | ((v1 + (uint32_t)(d - 1) * 0x01010101u) & m);
+                any |= m;
+              }
+              v = (v & ~any) | (T & any);
             }
-            v = (v & ~any) | (T & any);
-          }
-          out[(size_t)r * cols + kc] = v;
-          kc += nt;
-          while (kc >= cols) {
-            kc -= cols;
-            ++r;
+            out[(size_t)r * cols + kc] = v;
           }
         }
-        __syncthreads();  // M, D and the band buffer are free again
+        __syncthreads();  // D and the band buffer are free again
       }
       fence_proxy_async_global();
       if (aborted && tid == 0) atomicOr(rank_ptr(&misc[5], 0), 1);
@@ -613,8 +618,6 @@ bool tiled_geom(int L, int m_max, TiledGeom& g) {
   o += 2 * (size_t)kTRows * L;
   g.s_sband = o;
   o += 2 * (size_t)kTRows * g.W * 4;
-  g.s_M = o;
-  o += (size_t)kTB * g.cols * 4;
   g.s_D = o;
   o += 3 * (size_t)kTB * g.W * 4;
   o = (o + 15) & ~(size_t)15;
