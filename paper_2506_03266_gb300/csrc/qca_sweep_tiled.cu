@@ -40,8 +40,9 @@ namespace {
 
 constexpr int kTCL = 8;        // CTAs per cluster: one shot
 constexpr int kTThreads = 256;
-constexpr int kTB = 16;        // plane rows per staged band
-constexpr int kTRows = kTB + 6;  // staged rows: 3 halo rows on either side
+// plane rows per staged band (a template parameter of the kernel): 32 where
+// it divides the CTA's rows (L a multiple of 256), else 16; a band is staged
+// with 3 halo rows on either side
 constexpr long long kWaitCycles = 4000000000LL;  // watchdog on a copy (about 2 s)
 
 struct TiledGeom {
@@ -50,6 +51,7 @@ struct TiledGeom {
   int RL;     // rows per CTA in either frame (L / 8)
   int cols;   // 32-bit words per plane row (L / 4)
   int off;    // 255 - m_max
+  int TB;     // plane rows per staged band (16 or 32)
   size_t LL;
   // slot layout (byte offsets)
   size_t o_sig, o_flip, o_C, slot;
@@ -141,8 +143,10 @@ __device__ __forceinline__ T* rank_ptr(T* p, int r) {
   return cg::this_cluster().map_shared_rank(p, (unsigned)r);
 }
 
+template <int kTB>
 __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, TiledGeom g,
                                                              uint8_t* ws) {
+  constexpr int kTRows = kTB + 6;  // staged rows
   extern __shared__ __align__(128) uint8_t smem[];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -607,6 +611,8 @@ bool tiled_geom(int L, int m_max, TiledGeom& g) {
   g.RL = L / kTCL;
   g.cols = L / 4;
   g.off = 255 - m_max;
+  g.TB = (g.RL % 32 == 0) ? 32 : 16;
+  const int TR = g.TB + 6;
   g.LL = (size_t)L * L;
   const size_t bm = (size_t)L * g.W * 4;  // one bitmap, bytes
   g.o_sig = 8 * g.LL;
@@ -615,11 +621,11 @@ bool tiled_geom(int L, int m_max, TiledGeom& g) {
   g.slot = ((g.o_C + 2 * bm) + 255) & ~(size_t)255;
   size_t o = 0;
   g.s_band = o;
-  o += 2 * (size_t)kTRows * L;
+  o += 2 * (size_t)TR * L;
   g.s_sband = o;
-  o += 2 * (size_t)kTRows * g.W * 4;
+  o += 2 * (size_t)TR * g.W * 4;
   g.s_D = o;
-  o += 3 * (size_t)kTB * g.W * 4;
+  o += 3 * (size_t)g.TB * g.W * 4;
   o = (o + 15) & ~(size_t)15;
   g.s_bar = o;
   o += 16;
@@ -638,7 +644,7 @@ std::mutex g_tws_mu;
 TiledWorkspace g_tws[64];
 
 struct TiledShape {
-  int dev;
+  int dev, tb;
   size_t smem;
   int clusters;
 };
@@ -688,27 +694,28 @@ int launch_tiled(const DecodeArgs& a, cudaStream_t stream) {
   cfg.blockDim = dim3(kTThreads);
   cfg.dynamicSmemBytes = g.smem;
   cfg.stream = stream;
+  auto kern = g.TB == 32 ? tiled_kernel<32> : tiled_kernel<16>;
   int clusters = -1;
   {
     std::lock_guard<std::mutex> lk(g_tshape_mu);
     for (const TiledShape& s : g_tshapes)
-      if (s.dev == dev && s.smem == g.smem) clusters = s.clusters;
+      if (s.dev == dev && s.tb == g.TB && s.smem == g.smem) clusters = s.clusters;
   }
-  e = cudaFuncSetAttribute(tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)g.smem);
   if (e != cudaSuccess) return cuda_fail(e, "tiled sweep smem attribute");
   if (clusters < 0) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cfg.gridDim = dim3((unsigned)(kTCL * sms));
-    e = cudaOccupancyMaxActiveClusters(&clusters, tiled_kernel, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
     if (e != cudaSuccess) return cuda_fail(e, "tiled cluster occupancy query");
     if (clusters < 1) {
       set_error("tiled sweep cluster does not fit (L=%d)", a.L);
       return QCA_ERR_UNSUPPORTED;
     }
     std::lock_guard<std::mutex> lk(g_tshape_mu);
-    g_tshapes.push_back({dev, g.smem, clusters});
+    g_tshapes.push_back({dev, g.TB, g.smem, clusters});
   }
   int64_t grid = clusters;
   if (grid > a.shots) grid = a.shots;
@@ -736,7 +743,7 @@ int launch_tiled(const DecodeArgs& a, cudaStream_t stream) {
   e = cudaStreamWaitEvent(stream, w.done, 0);
   if (e != cudaSuccess) return cuda_fail(e, "stream wait");
   cfg.gridDim = dim3((unsigned)(grid * kTCL));
-  e = cudaLaunchKernelEx(&cfg, tiled_kernel, a, g, w.ptr);
+  e = cudaLaunchKernelEx(&cfg, kern, a, g, w.ptr);
   if (e != cudaSuccess) return cuda_fail(e, "tiled sweep launch");
   return cuda_fail(cudaEventRecord(w.done, stream), "event record");
 }
