@@ -44,6 +44,7 @@ constexpr int kTThreads = 256;
 // it divides the CTA's rows (L a multiple of 256), else 16; a band is staged
 // with 3 halo rows on either side
 constexpr long long kWaitCycles = 4000000000LL;  // watchdog on a copy (about 2 s)
+constexpr int kRowBatch = 4;   // bitmap rows whose global loads are issued together
 
 struct TiledGeom {
   int L;
@@ -440,10 +441,19 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
         uint64_t kstep = 0, kbal = 0;
         if (a.move_thr) kstep = move_step_key(a.move_key, a.shot_offset + shot, t);
         if (a.balance_rule) kbal = move_step_key(a.balance_key, a.shot_offset + shot, t);
-        for (int rr = warp; rr < RL; rr += nw) {
-          const int y = r0 + rr, wq = lane;
-          if (wq >= W) continue;
-          uint32_t bits = Sx[(size_t)y * W + wq];
+        // the sigma words of kRowBatch rows are loaded before the first is
+        // used (one global latency per batch instead of one per row)
+        for (int rb = warp; rb < RL; rb += nw * kRowBatch) {
+          uint32_t words[kRowBatch];
+#pragma unroll
+          for (int u = 0; u < kRowBatch; ++u) {
+            const int rr = rb + u * nw;
+            words[u] = (rr < RL && lane < W) ? Sx[(size_t)(r0 + rr) * W + lane] : 0u;
+          }
+#pragma unroll
+          for (int u = 0; u < kRowBatch; ++u) {
+          const int y = r0 + rb + u * nw, wq = lane;
+          uint32_t bits = words[u];
           while (bits) {
             // up to four anyons of the word at a time: all sixteen field loads
             // are issued before the first one is used
@@ -485,6 +495,7 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
               atomicOr(flip(par, 1, kind) + (size_t)lx * W + (ly >> 5), 1u << (ly & 31));
             }
           }
+          }
         }
       }
       cluster.sync();  // flipped-link maps complete
@@ -497,21 +508,41 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
           const uint32_t* Fa = flip(par, fr, fr == 0 ? 0 : 1);  // links along the row
           const uint32_t* Fc = flip(par, fr, fr == 0 ? 1 : 0);  // links across rows
           uint32_t* S = sigf(fr);
-          for (int rr = warp; rr < RL; rr += nw) {
-            const int R = r0 + rr, wq = lane;
-            if (wq >= W) continue;
-            const int Rm = twrap(R - 1, L), wm = wq == 0 ? W - 1 : wq - 1;
-            const uint32_t fa = Fa[(size_t)R * W + wq];
-            const uint32_t fa_prev = Fa[(size_t)R * W + wm];
-            const uint32_t along = fa ^ ((fa << 1) | (fa_prev >> 31));
-            const uint32_t fc = Fc[(size_t)R * W + wq];
-            const uint32_t across = fc ^ Fc[(size_t)Rm * W + wq];
-            const uint32_t s = S[(size_t)R * W + wq] ^ along ^ across;
-            S[(size_t)R * W + wq] = s;
-            if (fr == 0) {
-              cnt += __popc(s);
-              Cb[(size_t)R * W + wq] ^= fa;                       // x links
-              Cb[(size_t)L * W + (size_t)R * W + wq] ^= fc;       // y links
+          // kRowBatch rows at a time: every load of the batch is issued
+          // before the first store
+          for (int rb = warp; rb < RL; rb += nw * kRowBatch) {
+            uint32_t fa[kRowBatch], fc[kRowBatch], fcu[kRowBatch], sv[kRowBatch];
+            uint32_t cx[kRowBatch], cy[kRowBatch];
+#pragma unroll
+            for (int u = 0; u < kRowBatch; ++u) {
+              const int rr = rb + u * nw;
+              const bool on = rr < RL && lane < W;
+              const int R = r0 + (rr < RL ? rr : 0), Rm = twrap(R - 1, L);
+              fa[u] = on ? Fa[(size_t)R * W + lane] : 0u;
+              fc[u] = on ? Fc[(size_t)R * W + lane] : 0u;
+              fcu[u] = on ? Fc[(size_t)Rm * W + lane] : 0u;
+              sv[u] = on ? S[(size_t)R * W + lane] : 0u;
+              cx[u] = (on && fr == 0) ? Cb[(size_t)R * W + lane] : 0u;
+              cy[u] = (on && fr == 0) ? Cb[(size_t)L * W + (size_t)R * W + lane] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kRowBatch; ++u) {
+              const int rr = rb + u * nw;
+              const bool on = rr < RL && lane < W;
+              const int R = r0 + (rr < RL ? rr : 0);
+              // e_a of the previous word of the row (wrapping at the row end)
+              const uint32_t fa_prev = __shfl_sync(0xFFFFFFFFu, fa[u], lane == 0 ? W - 1 : lane - 1);
+              const uint32_t along = fa[u] ^ ((fa[u] << 1) | (fa_prev >> 31));
+              const uint32_t across = fc[u] ^ fcu[u];
+              const uint32_t sn = sv[u] ^ along ^ across;
+              if (on) {
+                S[(size_t)R * W + lane] = sn;
+                if (fr == 0) {
+                  cnt += __popc(sn);
+                  Cb[(size_t)R * W + lane] = cx[u] ^ fa[u];                 // x links
+                  Cb[(size_t)L * W + (size_t)R * W + lane] = cy[u] ^ fc[u];  // y links
+                }
+              }
             }
           }
         }
