@@ -192,6 +192,8 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
   const uint32_t task_bytes = (uint32_t)(kTRows * L + kTRows * W * 4);
 
   // issue the copies of task i (plane p, band b) of a step reading buffer `src`
+  // called by the 32 lanes of warp 0: lane 0 posts the expected bytes, then
+  // every lane issues the copies of its rows
   auto issue = [&](int i, int src) {
     const int p = i / nbands, b = i - p * nbands;
     const int buf = i & 1;
@@ -199,9 +201,12 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
     const uint8_t* P = plane(src, p);
     const uint32_t* S = sigf(p < 2 ? 0 : 1);
     fence_proxy_async_global();
-    inflight[buf] = true;
-    mbar_expect_tx(&bar[buf], task_bytes);
-    for (int j = 0; j < kTRows; ++j) {
+    if (lane == 0) {
+      inflight[buf] = true;
+      mbar_expect_tx(&bar[buf], task_bytes);
+    }
+    __syncwarp();
+    for (int j = lane; j < kTRows; j += 32) {
       const int R = twrap(R0 - 3 + j, L);
       bulk_g2s(band + ((size_t)buf * kTRows + j) * L, P + (size_t)R * L, (uint32_t)L, &bar[buf]);
       bulk_g2s(sband + ((size_t)buf * kTRows + j) * W, S + (size_t)R * W, (uint32_t)(W * 4),
@@ -304,9 +309,9 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
       }
       const int src = t & 1, dst = src ^ 1;
       // ================= 1. messages: bands staged by bulk copies
-      if (tid == 0) issue(0, src);
+      if (warp == 0) issue(0, src);
       for (int i = 0; i < ntasks; ++i) {
-        if (tid == 0 && i + 1 < ntasks && !aborted) issue(i + 1, src);
+        if (warp == 0 && i + 1 < ntasks && !aborted) issue(i + 1, src);
         const int buf = i & 1;
         const bool ok = mbar_wait_bounded(&bar[buf], phase[buf]);
         if (ok) {
