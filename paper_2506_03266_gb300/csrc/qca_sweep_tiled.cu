@@ -139,6 +139,14 @@ __device__ __forceinline__ uint32_t nib_mask(uint32_t nib) {
 }
 __device__ __forceinline__ uint32_t nibble_of_bytes(uint32_t w) { return (w * 0x01020408u) >> 24; }
 
+// n words (a multiple of 4, 16-byte aligned: every row range of the slot's
+// planes and bitmaps is) set to v by the threads of the CTA, 16 bytes a store.
+__device__ __forceinline__ void fill_words(uint32_t* p, int n, uint32_t v, int tid, int nt) {
+  uint4* q = reinterpret_cast<uint4*>(p);
+  const uint4 vv = make_uint4(v, v, v, v);
+  for (int i = tid; i < (n >> 2); i += nt) q[i] = vv;
+}
+
 template <class T>
 __device__ __forceinline__ T* rank_ptr(T* p, int r) {
   return cg::this_cluster().map_shared_rank(p, (unsigned)r);
@@ -232,17 +240,17 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
     {
       for (int p = 0; p < 4; ++p) {
         uint32_t* P = reinterpret_cast<uint32_t*>(plane(0, p)) + (size_t)r0 * cols;
-        for (int i = tid; i < RL * cols; i += nt) P[i] = 0xFFFFFFFFu;
+        fill_words(P, RL * cols, 0xFFFFFFFFu, tid, nt);
       }
       for (int par = 0; par < 2; ++par)
         for (int fr = 0; fr < 2; ++fr)
           for (int kd = 0; kd < 2; ++kd) {
             uint32_t* F = flip(par, fr, kd) + (size_t)r0 * W;
-            for (int i = tid; i < RL * W; i += nt) F[i] = 0;
+            fill_words(F, RL * W, 0u, tid, nt);
           }
       for (int kd = 0; kd < 2; ++kd) {
         uint32_t* C = Cb + (size_t)kd * L * W + (size_t)r0 * W;
-        for (int i = tid; i < RL * W; i += nt) C[i] = 0;
+        fill_words(C, RL * W, 0u, tid, nt);
       }
       // sigma (Def. synch_ccqs: parity of the four links incident to r)
       uint32_t* Sx = sigf(0);
@@ -555,7 +563,7 @@ __global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, Tiled
         for (int fr = 0; fr < 2; ++fr)
           for (int kd = 0; kd < 2; ++kd) {
             uint32_t* F = flip(par ^ 1, fr, kd) + (size_t)r0 * W;
-            for (int i = tid; i < RL * W; i += nt) F[i] = 0;
+            fill_words(F, RL * W, 0u, tid, nt);
           }
       }
       for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
