@@ -40,9 +40,12 @@ namespace {
 
 constexpr int kTCL = 8;        // CTAs per cluster: one shot
 constexpr int kTThreads = 256;
-// plane rows per staged band (a template parameter of the kernel): 32 where
-// it divides the CTA's rows (L a multiple of 256), else 16; a band is staged
-// with 3 halo rows on either side
+// Plane rows per staged band, staged with 3 halo rows on either side.  16-row
+// bands keep a CTA at 57 KB of shared memory and 64 registers, four CTAs per
+// SM; 32-row bands (100 KB, two CTAs per SM) measured slower.
+constexpr int kTB = 16;
+constexpr int kTRows = kTB + 6;
+constexpr int kTCtasPerSm = 4;
 constexpr long long kWaitCycles = 4000000000LL;  // watchdog on a copy (about 2 s)
 constexpr int kRowBatch = 4;   // bitmap rows whose global loads are issued together
 
@@ -52,7 +55,6 @@ struct TiledGeom {
   int RL;     // rows per CTA in either frame (L / 8)
   int cols;   // 32-bit words per plane row (L / 4)
   int off;    // 255 - m_max
-  int TB;     // plane rows per staged band (16 or 32)
   size_t LL;
   // slot layout (byte offsets)
   size_t o_sig, o_flip, o_C, slot;
@@ -152,10 +154,8 @@ __device__ __forceinline__ T* rank_ptr(T* p, int r) {
   return cg::this_cluster().map_shared_rank(p, (unsigned)r);
 }
 
-template <int kTB>
-__global__ void __launch_bounds__(kTThreads, 2) tiled_kernel(DecodeArgs a, TiledGeom g,
+__global__ void __launch_bounds__(kTThreads, kTCtasPerSm) tiled_kernel(DecodeArgs a, TiledGeom g,
                                                              uint8_t* ws) {
-  constexpr int kTRows = kTB + 6;  // staged rows
   extern __shared__ __align__(128) uint8_t smem[];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -655,8 +655,7 @@ bool tiled_geom(int L, int m_max, TiledGeom& g) {
   g.RL = L / kTCL;
   g.cols = L / 4;
   g.off = 255 - m_max;
-  g.TB = (g.RL % 32 == 0) ? 32 : 16;
-  const int TR = g.TB + 6;
+  const int TR = kTRows;
   g.LL = (size_t)L * L;
   const size_t bm = (size_t)L * g.W * 4;  // one bitmap, bytes
   g.o_sig = 8 * g.LL;
@@ -669,7 +668,7 @@ bool tiled_geom(int L, int m_max, TiledGeom& g) {
   g.s_sband = o;
   o += 2 * (size_t)TR * g.W * 4;
   g.s_D = o;
-  o += 3 * (size_t)g.TB * g.W * 4;
+  o += 3 * (size_t)kTB * g.W * 4;
   o = (o + 15) & ~(size_t)15;
   g.s_bar = o;
   o += 16;
@@ -688,7 +687,7 @@ std::mutex g_tws_mu;
 TiledWorkspace g_tws[64];
 
 struct TiledShape {
-  int dev, tb;
+  int dev;
   size_t smem;
   int clusters;
 };
@@ -738,12 +737,12 @@ int launch_tiled(const DecodeArgs& a, cudaStream_t stream) {
   cfg.blockDim = dim3(kTThreads);
   cfg.dynamicSmemBytes = g.smem;
   cfg.stream = stream;
-  auto kern = g.TB == 32 ? tiled_kernel<32> : tiled_kernel<16>;
+  auto kern = tiled_kernel;
   int clusters = -1;
   {
     std::lock_guard<std::mutex> lk(g_tshape_mu);
     for (const TiledShape& s : g_tshapes)
-      if (s.dev == dev && s.tb == g.TB && s.smem == g.smem) clusters = s.clusters;
+      if (s.dev == dev && s.smem == g.smem) clusters = s.clusters;
   }
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)g.smem);
@@ -759,7 +758,7 @@ int launch_tiled(const DecodeArgs& a, cudaStream_t stream) {
       return QCA_ERR_UNSUPPORTED;
     }
     std::lock_guard<std::mutex> lk(g_tshape_mu);
-    g_tshapes.push_back({dev, g.TB, g.smem, clusters});
+    g_tshapes.push_back({dev, g.smem, clusters});
   }
   int64_t grid = clusters;
   if (grid > a.shots) grid = a.shots;
