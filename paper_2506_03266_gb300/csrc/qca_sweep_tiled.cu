@@ -47,7 +47,9 @@ constexpr int kTB = 16;
 constexpr int kTRows = kTB + 6;
 constexpr int kTCtasPerSm = 4;
 constexpr long long kWaitCycles = 4000000000LL;  // watchdog on a copy (about 2 s)
-constexpr int kRowBatch = 4;   // bitmap rows whose global loads are issued together
+// bitmap rows whose global loads are issued together (move phase, sigma update)
+constexpr int kMoveBatch = 2;
+constexpr int kSigBatch = 2;
 
 struct TiledGeom {
   int L;
@@ -454,17 +456,17 @@ __global__ void __launch_bounds__(kTThreads, kTCtasPerSm) tiled_kernel(DecodeArg
         uint64_t kstep = 0, kbal = 0;
         if (a.move_thr) kstep = move_step_key(a.move_key, a.shot_offset + shot, t);
         if (a.balance_rule) kbal = move_step_key(a.balance_key, a.shot_offset + shot, t);
-        // the sigma words of kRowBatch rows are loaded before the first is
+        // the sigma words of kMoveBatch rows are loaded before the first is
         // used (one global latency per batch instead of one per row)
-        for (int rb = warp; rb < RL; rb += nw * kRowBatch) {
-          uint32_t words[kRowBatch];
+        for (int rb = warp; rb < RL; rb += nw * kMoveBatch) {
+          uint32_t words[kMoveBatch];
 #pragma unroll
-          for (int u = 0; u < kRowBatch; ++u) {
+          for (int u = 0; u < kMoveBatch; ++u) {
             const int rr = rb + u * nw;
             words[u] = (rr < RL && lane < W) ? Sx[(size_t)(r0 + rr) * W + lane] : 0u;
           }
 #pragma unroll
-          for (int u = 0; u < kRowBatch; ++u) {
+          for (int u = 0; u < kMoveBatch; ++u) {
           const int y = r0 + rb + u * nw, wq = lane;
           uint32_t bits = words[u];
           while (bits) {
@@ -521,13 +523,13 @@ __global__ void __launch_bounds__(kTThreads, kTCtasPerSm) tiled_kernel(DecodeArg
           const uint32_t* Fa = flip(par, fr, fr == 0 ? 0 : 1);  // links along the row
           const uint32_t* Fc = flip(par, fr, fr == 0 ? 1 : 0);  // links across rows
           uint32_t* S = sigf(fr);
-          // kRowBatch rows at a time: every load of the batch is issued
+          // kSigBatch rows at a time: every load of the batch is issued
           // before the first store
-          for (int rb = warp; rb < RL; rb += nw * kRowBatch) {
-            uint32_t fa[kRowBatch], fc[kRowBatch], fcu[kRowBatch], sv[kRowBatch];
-            uint32_t cx[kRowBatch], cy[kRowBatch];
+          for (int rb = warp; rb < RL; rb += nw * kSigBatch) {
+            uint32_t fa[kSigBatch], fc[kSigBatch], fcu[kSigBatch], sv[kSigBatch];
+            uint32_t cx[kSigBatch], cy[kSigBatch];
 #pragma unroll
-            for (int u = 0; u < kRowBatch; ++u) {
+            for (int u = 0; u < kSigBatch; ++u) {
               const int rr = rb + u * nw;
               const bool on = rr < RL && lane < W;
               const int R = r0 + (rr < RL ? rr : 0), Rm = twrap(R - 1, L);
@@ -539,7 +541,7 @@ __global__ void __launch_bounds__(kTThreads, kTCtasPerSm) tiled_kernel(DecodeArg
               cy[u] = (on && fr == 0) ? Cb[(size_t)L * W + (size_t)R * W + lane] : 0u;
             }
 #pragma unroll
-            for (int u = 0; u < kRowBatch; ++u) {
+            for (int u = 0; u < kSigBatch; ++u) {
               const int rr = rb + u * nw;
               const bool on = rr < RL && lane < W;
               const int R = r0 + (rr < RL ? rr : 0);
