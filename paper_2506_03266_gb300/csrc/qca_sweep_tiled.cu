@@ -8,7 +8,7 @@
 //      exactly as in the on-chip kernel): every CTA streams bands of 16 rows of
 //      each plane plus 3 halo rows on either side, and the matching rows of the
 //      syndrome bitmap, from the previous step's buffer into shared memory with
-//      bulk asynchronous copies (TMA, completion on an mbarrier, the next band
+//      bulk asynchronous copies (completion on an mbarrier, the next band
 //      prefetched while this one is computed); computes
 //        w3(r) = min( off + d - 1 for the smallest d <= 3 with an anyon on
 //                     {r - s d a^ + j b^, |j| <= d},
@@ -41,8 +41,8 @@ namespace {
 constexpr int kTCL = 8;        // CTAs per cluster: one shot
 constexpr int kTThreads = 256;
 // Plane rows per staged band, staged with 3 halo rows on either side.  16-row
-// bands keep a CTA at 57 KB of shared memory and 64 registers, four CTAs per
-// SM; 32-row bands (100 KB, two CTAs per SM) measured slower.
+// bands keep a CTA at 51 KB of shared memory and 64 registers, four CTAs per
+// SM; 32-row bands (two CTAs per SM) measured slower.
 constexpr int kTB = 16;
 constexpr int kTRows = kTB + 6;
 constexpr int kTCtasPerSm = 4;
@@ -61,7 +61,7 @@ struct TiledGeom {
   // slot layout (byte offsets)
   size_t o_sig, o_flip, o_C, slot;
   // shared memory layout (byte offsets)
-  size_t s_band, s_sband, s_D, s_bar, s_misc, smem;
+  size_t s_band, s_sband, s_bar, s_misc, smem;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -121,22 +121,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 __device__ __forceinline__ int twrap(int i, int L) { return i < 0 ? i + L : (i >= L ? i - L : i); }
 
-// Four bits of a bitmap row starting at bit position pos (wrapping at the row end).
-__device__ __forceinline__ uint32_t bits4(const uint32_t* row, int W, int pos) {
-  const int q = pos >> 5, sh = pos & 31;
-  const int q1 = (q + 1 == W) ? 0 : q + 1;
-  const uint64_t two = ((uint64_t)row[q1] << 32) | row[q];
-  return (uint32_t)(two >> sh) & 0xFu;
-}
-
-// Six bits of a bitmap row starting at bit position pos (wrapping at the row end).
-__device__ __forceinline__ uint32_t bits6(const uint32_t* row, int W, int pos) {
-  const int q = pos >> 5, sh = pos & 31;
-  const int q1 = (q + 1 == W) ? 0 : q + 1;
-  const uint64_t two = ((uint64_t)row[q1] << 32) | row[q];
-  return (uint32_t)(two >> sh) & 0x3Fu;
-}
-
 // 4 bits -> 4 bytes of 0xFF / 0x00 (bit k -> byte k).
 __device__ __forceinline__ uint32_t nib_mask(uint32_t nib) {
   return ((nib * 0x00204081u) & 0x01010101u) * 0xFFu;
@@ -171,7 +155,6 @@ __global__ void __launch_bounds__(kTThreads, kTCtasPerSm) tiled_kernel(DecodeArg
 
   uint8_t* band = smem + g.s_band;                                         // [2][kTRows][L]
   uint32_t* sband = reinterpret_cast<uint32_t*>(smem + g.s_sband);         // [2][kTRows][W]
-  uint32_t* D = reinterpret_cast<uint32_t*>(smem + g.s_D);                 // [3][kTB][W]
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + g.s_bar);             // [2]
   int* misc = reinterpret_cast<int*>(smem + g.s_misc);
   // misc: [0..1] anyon counts by step parity (rank 0), [2] wx, [3] wy (rank 0),
@@ -336,19 +319,6 @@ __global__ void __launch_bounds__(kTThreads, kTCtasPerSm) tiled_kernel(DecodeArg
         const int R0 = r0 + b * kTB;
         const uint8_t* Bk = band + (size_t)buf * kTRows * L;
         const uint32_t* Sb = sband + (size_t)buf * kTRows * W;
-        // dilated syndrome rows D_d(R) = OR_{|j| <= d} sigma(R + j), d = 1, 2, 3
-        for (int r = warp; r < kTB; r += nw) {
-          const int w = lane;
-          if (w >= W) continue;
-          const uint32_t* c = Sb + (size_t)(r + 3) * W + w;
-          const uint32_t d1 = c[-W] | c[0] | c[W];
-          const uint32_t d2 = d1 | c[-2 * W] | c[2 * W];
-          const uint32_t d3 = d2 | c[-3 * W] | c[3 * W];
-          D[(size_t)r * W + w] = d1;
-          D[(size_t)(kTB + r) * W + w] = d2;
-          D[(size_t)(2 * kTB + r) * W + w] = d3;
-        }
-        __syncthreads();  // the dilated rows are complete
         // fused message update of the band, one 4-site column word per thread:
         // every staged row is shifted by 3 sites along the byte axis as it is
         // loaded (funnel shift with the neighbouring column word, wrapping at
@@ -369,11 +339,20 @@ __global__ void __launch_bounds__(kTThreads, kTCtasPerSm) tiled_kernel(DecodeArg
           };
           // the d <= 3 cones of the word's four sites read positions
           // 4 kc - 3 .. 4 kc + 2 (m^+) or 4 kc + 1 .. 4 kc + 6 (m^-) of the
-          // dilated rows; bit positions of the six-bit test and of each d
+          // dilated syndrome rows
           const int pos6 = twrap(4 * kc + (plus ? -3 : 1), L);
-          int posd[3];
+          const int q6 = pos6 >> 5, sh6 = pos6 & 31, q6n = (q6 + 1 == W) ? 0 : q6 + 1;
+          // six syndrome bits pos6 .. pos6 + 5 of staged row j
+          auto sig6 = [&](int j) -> uint32_t {
+            const uint32_t* row = Sb + (size_t)j * W;
+            return __funnelshift_r(row[q6], row[q6n], sh6) & 0x3Fu;
+          };
+          // dilated rows D_d of band row r = OR of staged syndrome rows
+          // r + 3 - d .. r + 3 + d, rolled down the band with the planes; the
+          // four bits of D_d for the word sit at offset 3 - d (m^+) or d - 1 (m^-)
+          uint32_t sg[7];
 #pragma unroll
-          for (int d = 1; d <= 3; ++d) posd[d - 1] = twrap(4 * kc + (plus ? -d : d), L);
+          for (int j = 0; j < 6; ++j) sg[j] = sig6(j);
           // rolling window over staged rows a(j): pair mins q, quad mins u,
           // out(r) = min(u(r), u(r + 3)) = min of staged rows r .. r + 6
           uint32_t ah[7], al[7];
@@ -427,11 +406,19 @@ __global__ void __launch_bounds__(kTThreads, kTCtasPerSm) tiled_kernel(DecodeArg
             // d), and every term lies below every propagated value, so it
             // replaces it; D_3 contains D_2 and D_1, so if the six bits of D_3
             // are clear there is no term
-            if (bits6(D + (size_t)(2 * kTB + r) * W, W, pos6)) {
+            sg[6] = sig6(r + 6);
+            const uint32_t d1 = sg[2] | sg[3] | sg[4];
+            const uint32_t d2 = d1 | sg[1] | sg[5];
+            const uint32_t d3 = d2 | sg[0] | sg[6];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) sg[j] = sg[j + 1];
+            if (d3) {
+              const uint32_t dd[3] = {d1, d2, d3};
               uint32_t T = 0u, any = 0u;
 #pragma unroll
               for (int d = 3; d >= 1; --d) {
-                const uint32_t m = nib_mask(bits4(D + (size_t)((d - 1) * kTB + r) * W, W, posd[d - 1]));
+                const int off = plus ? 3 - d : d - 1;
+                const uint32_t m = nib_mask((dd[d - 1] >> off) & 0xFu);
                 T = (T & ~m) | ((v1 + (uint32_t)(d - 1) * 0x01010101u) & m);
                 any |= m;
               }
@@ -669,8 +656,6 @@ bool tiled_geom(int L, int m_max, TiledGeom& g) {
   o += 2 * (size_t)TR * L;
   g.s_sband = o;
   o += 2 * (size_t)TR * g.W * 4;
-  g.s_D = o;
-  o += 3 * (size_t)kTB * g.W * 4;
   o = (o + 15) & ~(size_t)15;
   g.s_bar = o;
   o += 16;
