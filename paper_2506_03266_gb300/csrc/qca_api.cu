@@ -327,29 +327,42 @@ int qca_decode_batch_host(const uint8_t* syndrome, int L, int64_t shots, int max
       cudaError_t e = cudaStreamCreateWithFlags(&st.streams[i], cudaStreamNonBlocking);
       if (e != cudaSuccess) return cuda_fail(e, "stream creation");
     }
-  int64_t k = 0;
-  for (int64_t s0 = 0; s0 < shots; s0 += chunk, ++k) {
-    const int64_t n = (shots - s0 < chunk) ? shots - s0 : chunk;
-    const int set = concurrent ? (int)(k & 1) : 0;
-    cudaStream_t sm = st.streams[set];
-    uint8_t* dN = st.buf + set * per_set;
+  // Chunk k uses buffer set k % 2 on stream k % 2.  The input copy of chunk
+  // k + 1 is enqueued before the output copies of chunk k: where the driver
+  // serves both directions from one copy queue, an input copy queued behind an
+  // output copy would wait for that chunk's decode, and the next decode with it.
+  const int64_t nchunks = (shots + chunk - 1) / chunk;
+  auto set_of = [&](int64_t k) { return concurrent ? (int)(k & 1) : 0; };
+  auto dN_of = [&](int64_t k) { return st.buf + set_of(k) * per_set; };
+  auto input_copy = [&](int64_t k) -> int {
+    const int64_t s0 = k * chunk, n = (shots - s0 < chunk) ? shots - s0 : chunk;
+    cudaError_t e = cudaMemcpyAsync(dN_of(k), syndrome + s0 * E, n * E, cudaMemcpyHostToDevice,
+                                    st.streams[set_of(k)]);
+    return e == cudaSuccess ? QCA_OK : cuda_fail(e, "host-to-device copy");
+  };
+  if ((rc = input_copy(0))) return rc;
+  for (int64_t k = 0; k < nchunks; ++k) {
+    const int64_t s0 = k * chunk, n = (shots - s0 < chunk) ? shots - s0 : chunk;
+    cudaStream_t sm = st.streams[set_of(k)];
+    uint8_t* dN = dN_of(k);
     uint8_t* dC = dN + ((chunk * E + 255) & ~(size_t)255);
     uint8_t* dF = dC + ((chunk * E + 255) & ~(size_t)255);
     int32_t* dS = (int32_t*)(dF + ((chunk + 15) & ~(int64_t)15));
-    cudaError_t e = cudaMemcpyAsync(dN, syndrome + s0 * E, n * E, cudaMemcpyHostToDevice, sm);
-    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
     qca_config cc = c;
     cc.shot_offset = c.shot_offset + s0;
     rc = qca_decode_batch_async(dN, L, n, max_steps, rng_seed, dC, dS, dF, &cc, sm);
     if (rc) return rc;
-    if (out_correction) {
+    // one buffer set without concurrency: the next input waits for this chunk
+    if (concurrent && k + 1 < nchunks && (rc = input_copy(k + 1))) return rc;
+    cudaError_t e = cudaSuccess;
+    if (out_correction)
       e = cudaMemcpyAsync(out_correction + s0 * E, dC, n * E, cudaMemcpyDeviceToHost, sm);
-      if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
-    }
-    e = cudaMemcpyAsync(out_steps + s0, dS, n * sizeof(int32_t), cudaMemcpyDeviceToHost, sm);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out_steps + s0, dS, n * sizeof(int32_t), cudaMemcpyDeviceToHost, sm);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(out_logical_fail + s0, dF, n, cudaMemcpyDeviceToHost, sm);
     if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    if (!concurrent && k + 1 < nchunks && (rc = input_copy(k + 1))) return rc;
   }
   for (int i = 0; i < 2; ++i) {
     cudaError_t e = cudaStreamSynchronize(st.streams[i]);

@@ -166,6 +166,19 @@ def test_host_entry_point_matches_device():
     assert_same((C.numpy(), s.numpy(), f.numpy()), oracle.decode_batch(N, max_steps=500), "host")
 
 
+@pytest.mark.parametrize("L,shots", [(256, 1100), (1024, 70)])
+def test_host_entry_point_in_several_chunks(L, shots):
+    """Batches of three 64 MiB chunks: the host-buffer decode's pipelined copies
+    (two buffer sets on two streams for the on-chip sweep, one set for the
+    large-lattice sweep) give the device entry point's outputs."""
+    N = qca.sample_errors(L, shots, 0.05, seed=4)
+    Cd, sd, fd = qca.decode_batch(N, max_steps=600)
+    torch.cuda.synchronize()
+    C, s, f = qca.decode_batch_host(N.cpu().pin_memory(), max_steps=600)
+    assert torch.equal(s, sd.cpu()) and torch.equal(f, fd.cpu())
+    assert torch.equal(C, Cd.cpu())
+
+
 # -------------------------------------------------------------- edges -----
 
 def test_edge_cases():
