@@ -307,13 +307,13 @@ __global__ void __launch_bounds__(kTThreads, kTCtasPerSm) tiled_kernel(DecodeArg
         if (warp == 0 && i + 1 < ntasks && !aborted) issue(i + 1, src);
         const int buf = i & 1;
         const bool ok = mbar_wait_bounded(&bar[buf], phase[buf]);
+        // every thread waited on the copies itself; a wait that gave up is
+        // agreed on at the band's closing barrier (the band is then garbage,
+        // read and written at the same data-independent places, and the shot
+        // ends with flag 3)
         if (ok) {
           phase[buf] ^= 1u;
           inflight[buf] = false;
-        }
-        if (__syncthreads_or(!ok)) {
-          aborted = true;
-          break;
         }
         const int p = i / nbands, b = i - p * nbands;
         const int R0 = r0 + b * kTB;
@@ -427,7 +427,11 @@ __global__ void __launch_bounds__(kTThreads, kTCtasPerSm) tiled_kernel(DecodeArg
             out[(size_t)r * cols + kc] = v;
           }
         }
-        __syncthreads();  // D and the band buffer are free again
+        // the band buffer is free again
+        if (__syncthreads_or(!ok)) {
+          aborted = true;
+          break;
+        }
       }
       fence_proxy_async_global();
       if (aborted && tid == 0) atomicOr(rank_ptr(&misc[5], 0), 1);
