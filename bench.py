@@ -12,7 +12,11 @@ device before timing (inputs resident in HBM; 13.1 GB, larger than L2).
 
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank decodes its
 own batch (weak scaling; no data-path collective) and the time is the max over
-ranks.  --impl reference times the CPU oracle on the host cores instead.
+ranks.  --impl reference times the CPU oracle on the host cores instead.  On
+one GPU the line also carries, under "configs", the lines of the other
+configurations (the L x p grid, the uneven batch, the pre-decoder at L = 128
+and the L = 1024 stress), each measured by --workload in a process of its own
+after the headline (--no-configs skips them).
 """
 from __future__ import annotations
 
@@ -87,6 +91,40 @@ def executed_site_updates(steps, flags, L):
     ended = np.asarray(flags) != 2
     L2 = np.asarray(L, dtype=np.int64) ** 2
     return int((st * L2 * ended).sum())
+
+
+# The other configurations of the benchmark, run after the headline when one
+# GPU runs the default line: (key, workload).
+CONFIG_WORKLOADS = (("C2_grid", "sweep"), ("C3_uneven", "uneven"), ("C4_net", "net"),
+                    ("C5_large", "large"))
+
+
+def run_config_lines(args):
+    """The bench lines of the other configurations (the L x p grid, the uneven
+    batch, the pre-decoder at L = 128 and the L = 1024 stress), each measured by
+    this script in a process of its own after the headline's timed work, with
+    the same steps and warm-up.  A configuration that fails is reported with
+    its error; the headline line is printed either way."""
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("RANK", "LOCAL_RANK", "WORLD_SIZE", "LOCAL_WORLD_SIZE", "MASTER_ADDR",
+                        "MASTER_PORT", "GROUP_RANK", "ROLE_RANK", "TORCHELASTIC_RUN_ID")}
+    out = {}
+    for key, workload in CONFIG_WORKLOADS:
+        t0 = time.perf_counter()
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", workload,
+               "--steps", str(args.steps), "--warmup", str(args.warmup)]
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, env=env,
+                               cwd=ROOT)
+            lines = [x for x in r.stdout.strip().splitlines() if x.startswith("{")]
+            if r.returncode == 0 and lines:
+                out[key] = json.loads(lines[-1])
+            else:
+                out[key] = {"error": f"rc {r.returncode}: {r.stderr.strip()[-300:]}"}
+        except Exception as e:  # a timeout or an unreadable line
+            out[key] = {"error": repr(e)[:300]}
+        out[key]["wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 def shard(rank: int, shots_per_rank: int):
@@ -986,6 +1024,8 @@ def main():
     ap.add_argument("--shots", type=int, default=SHOTS_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="headline only: skip the other configurations' lines (C2-C5)")
     ap.add_argument("--no-net", action="store_true",
                     help="skip the net + automaton comparison of the default workload")
     ap.add_argument("--workload", default="uniform",
@@ -1260,6 +1300,12 @@ def main():
         "cpu_baseline": cpu,
         "net_ca": net_ca,
     }
+    if rank == 0 and world == 1 and not args.no_configs:
+        # the other configurations, untimed here, each timed in its own process
+        out = nout = scratch = None  # release the headline's device buffers
+        del N, C, steps, fail
+        torch.cuda.empty_cache()
+        line["configs"] = run_config_lines(args)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
