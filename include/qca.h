@@ -247,7 +247,7 @@ int qca_sample_errors_uneven_async(const int32_t* L_dev, const int64_t* offsets_
  * (multiples of 4 up to 128 and of 8 up to 256, blocks on a 4-byte boundary;
  * the 8 largest such sizes), queued pairs first, then by group size, then
  * largest L first.
- * Clusters of two CTAs take the shots with L > 128; every other size is
+ * Clusters of two CTAs take the shots with L > 192; every other size is
  * decoded by a group of 512, 256 or 128 threads (the smallest that fits), a
  * 512-thread CTA halving into up to four groups as the queue reaches smaller
  * sizes; each takes its next shot when the last one is done (work stealing

@@ -473,8 +473,8 @@ __device__ void dense_terms(const uint32_t* sig, const uint16_t* list, int count
 
 // Most bitmap words a thread handles in the dense feedback pass: geometries
 // are accepted only within it (make_geom).
-template <int CL>
-constexpr int kWordsPerThread = CL == 1 ? 2 : (CL == 2 ? 4 : 8);
+template <int CL, int KW>
+constexpr int kWordsPerThread = CL == 1 ? (KW == 2 ? 4 : 2) : (CL == 2 ? 4 : 8);
 
 // One step of the orbit watch, run by the 32 lanes of one warp at the start of
 // a step t with at most kOrbitAnyons anyons (sigma and the list are those of
@@ -847,7 +847,7 @@ __device__ __forceinline__ void decode_shot(const DecodeArgs& a, const FastGeom&
     csync();
     // ================= 3. sigma and correction from the flipped links, new
     //                   anyon list, early exit
-    any = apply_flips<kWordsPerThread<CL>>(sig_cur, flip, Cb, g, list, &misc[0], row_lo, row_hi,
+    any = apply_flips<kWordsPerThread<CL, KW>>(sig_cur, flip, Cb, g, list, &misc[0], row_lo, row_hi,
                                             G);
     count = misc[0];
     if (t_stop == -1) t_stop = misc[5];
@@ -955,15 +955,17 @@ int sparse_divisor_for(int L, int CL) {
 }
 
 // Geometry of the on-chip sweep for L: CL (1 or 2 CTAs per shot), KW (words per
-// lane), bands and shared-memory layout.  warp_cap > 0 limits the warps of a
-// one-CTA geometry (the groups of the mixed-size kernel); such a request fails
-// for L > 128.
+// lane), bands and shared-memory layout.  warp_cap > 0 asks for a one-CTA
+// geometry with at most that many warps (the groups of the mixed-size kernel),
+// also above L = 128, where the list is capped so that a lattice up to L = 192
+// fits one CTA; the caller checks the shared memory.
 bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, size_t& smem,
                int warp_cap = 0) {
   if (L % 4 != 0 || L < 8 || L > 256) return false;
   if (m_max < 3) return false;  // the first-step fill assumes the d <= 3 terms fit below 0xFF
   if (L > 128 && L % 8 != 0) return false;
-  CL = (L > 128) ? (g_cluster4[L] ? 4 : 2) : 1;
+  // a group of the mixed-size kernel decodes its shot alone, up to L = 192
+  CL = (L > 128 && warp_cap == 0) ? (g_cluster4[L] ? 4 : 2) : 1;
   KW = (L / 4 > 32) ? 2 : 1;
   g.L = L;
   g.rows_local = L / CL;
@@ -976,7 +978,6 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
   // 128), the taller band on a tie.  The sweep takes any height of at least 4
   // that divides the CTA's rows; other heights are used only where none of
   // these four fits.
-  if (warp_cap > 0 && CL != 1) return false;
   const int max_warps = warp_cap > 0 ? std::min(32, warp_cap) : (CL == 1 ? 32 : (CL == 2 ? 16 : 8));
   const int target = std::min(max_warps, L <= 64 ? 4 : std::min(16, L / 8));
   int best_H = 0, best_d = 1 << 30;
@@ -1023,14 +1024,15 @@ bool make_geom(int L, int m_max, int& CL, int& KW, FastGeom& g, int& threads, si
   g.lws = lws;
   g.nws = L << lws;
   // the dense feedback pass handles at most this many words per thread
-  const int max_per =
-      CL == 1 ? kWordsPerThread<1> : (CL == 2 ? kWordsPerThread<2> : kWordsPerThread<4>);
+  const int max_per = CL == 1 ? (KW == 2 ? kWordsPerThread<1, 2> : kWordsPerThread<1, 1>)
+                               : (CL == 2 ? kWordsPerThread<2, 2> : kWordsPerThread<4, 2>);
   if ((g.nws + threads - 1) / threads > max_per) return false;
   g.off = 255 - m_max;
   // up to half the lattice in the list (more anyons than that are iterated
   // from the bitmap; a noise rate below 0.5 rarely comes near it)
   g.cap = std::min(L * L / 2, kListCap);
   if (CL == 4) g.cap = std::min(g.cap, 1024);  // two CTAs of a cluster of four share an SM
+  if (CL == 1 && L > 128) g.cap = std::min(g.cap, 8192);  // a whole L <= 192 lattice in one CTA
   g.sparse_max = L * L / sparse_divisor_for(L, CL);
   // row pitch: L + 4 bytes (one extra bank per row); L + 8 keeps the 8-byte
   // alignment of the 64-bit accesses used with two words per lane
@@ -1061,9 +1063,11 @@ std::vector<LaunchShape> g_shapes;
 // shots start early and the short ones fill the tail, and every group takes
 // the next item from one counter when it has finished its last (work stealing
 // across sizes; every shot retires after its own number of steps).
-//   * pair items (128 < L <= 256) are decoded by the two CTAs of a cluster;
+//   * pair items, sizes that no CTA holds alone (above L = 192), are decoded
+//     by the two CTAs of a cluster;
 //   * every other size has a group size of 512, 256 or 128 threads (the
-//     smallest whose band geometry and shared memory fit): a CTA of 512
+//     smallest whose band geometry and shared memory fit; 512 with two plane
+//     words per lane for 128 < L <= 192): a CTA of 512
 //     threads starts as one group and halves whenever the item it holds needs
 //     a smaller group, the first half keeping the item and the second fetching
 //     its own, so that up to four small lattices are decoded at once per CTA.
@@ -1140,8 +1144,12 @@ __global__ void __launch_bounds__(kMixThreads, 1) mixed_kernel(MixArgs m) {
       }
       continue;
     }
-    decode_shot<1, 1>(m.a, m.geom[c], smem + (size_t)(gofs / 64) * m.slice_bytes,
-                      m.a.shot_list[k], G);
+    if (m.geom[c].L > 128)  // two plane words per lane
+      decode_shot<1, 2>(m.a, m.geom[c], smem + (size_t)(gofs / 64) * m.slice_bytes,
+                        m.a.shot_list[k], G);
+    else
+      decode_shot<1, 1>(m.a, m.geom[c], smem + (size_t)(gofs / 64) * m.slice_bytes,
+                        m.a.shot_list[k], G);
     k = -1;
   }
   __syncthreads();
@@ -1243,24 +1251,27 @@ int launch_fast(const DecodeArgs& a, cudaStream_t stream) {
 // CTA (227 KB less room for the kernel's static shared memory).
 constexpr size_t kMixSmemLimit = 227 * 1024 - 1024;
 
-// Group size of each size in the mixed kernel: 0 for a pair item (two-CTA
-// cluster), else 512, 256 or 128 threads, the smallest whose band geometry
-// fits its warps and whose shared memory times the groups of a CTA fits the
-// limit; -1 if the on-chip sweep does not take the size.  (Groups of 64
-// threads, eight small lattices per CTA, measured slower on the mixed C3
-// batch: 109 against 99 ms.)
+// Group size of each size in the mixed kernel: 512, 256 or 128 threads, the
+// smallest whose one-CTA band geometry fits its warps and whose shared memory
+// times the groups of a CTA fits the limit; else 0 for a pair item (two-CTA
+// cluster; sizes above 192); -1 if the on-chip sweep does not take the size.
+// (One CTA per L = 192 shot instead of a pair took the C3 batch from 67.7 to
+// 58.8 ms; groups of 64 threads, eight small lattices per CTA, measured
+// slower: 109 against 99 ms.)
 int mixed_group_threads(int L, int m_max) {
   int CL, KW, th;
   FastGeom g;
   size_t sm;
   if (!make_geom(L, m_max, CL, KW, g, th, sm)) return -1;
-  if (CL == 2) return sm <= kMixSmemLimit ? 0 : -1;
+  const bool pair_ok = CL == 2 && sm <= kMixSmemLimit;
   for (int gs = 128; gs <= kMixThreads; gs *= 2) {
-    if (!make_geom(L, m_max, CL, KW, g, th, sm, gs / 32)) continue;
-    const size_t per = (sm + 127) & ~(size_t)127;
+    int cl, kw, t2;
+    size_t s2;
+    if (!make_geom(L, m_max, cl, kw, g, t2, s2, gs / 32)) continue;
+    const size_t per = (s2 + 127) & ~(size_t)127;
     if (per * (kMixThreads / gs) <= kMixSmemLimit) return gs;
   }
-  return -1;
+  return pair_ok ? 0 : -1;
 }
 
 int launch_mixed(const DecodeArgs& a, const uint8_t* item_class, const int* sizes,
