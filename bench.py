@@ -63,8 +63,8 @@ CAP_REACH_STEPS = (255 + 2) // 3
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 4000 shots,
 # profiles/fast_kernel_L256_p005_full.md), valid only for the kernel source
 # whose SHA-256 prefix is recorded with it; reported as null otherwise.
-TRAFFIC_PER_SHOT = {"sha256_prefixes": ("289ec4bbeb84b6cf",), "L": 256,
-                    "p": 0.05, "bytes_per_shot": (527.332864e6 + 480.011264e6) / 4000}
+TRAFFIC_PER_SHOT = {"sha256_prefixes": ("5e1dbd7f441ad48a",), "L": 256,
+                    "p": 0.05, "bytes_per_shot": (525.402112e6 + 479.698944e6) / 4000}
 
 
 def traffic_per_launch(L, p, shots):
