@@ -161,7 +161,8 @@ int qca_decode_syndrome_batch(const uint8_t* sigma, int L, int shots, int max_st
  * and flags back, overlapping transfers with decoding.  Host buffers should be
  * page-locked for full speed.  out_correction may be NULL (not copied back).
  * Uses a device staging workspace cached by the library (qca_free_workspace
- * releases it).  Synchronises. */
+ * releases it).  Synchronises; on an error it still waits for the copies it
+ * had enqueued, so none touches the caller's buffers after it returns. */
 int qca_decode_batch_host(const uint8_t* syndrome, int L, int64_t shots, int max_steps,
                           uint64_t rng_seed, uint8_t* out_correction, int32_t* out_steps,
                           uint8_t* out_logical_fail, const qca_config* cfg);

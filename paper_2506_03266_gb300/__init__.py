@@ -168,6 +168,24 @@ def _dev_u8(torch, t, shape, name):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
 
 
+def _check_out(torch, out, specs, device):
+    """Raise ValueError unless `out` holds one contiguous tensor per spec
+    (dtype, shape, name), each on `device`: the kernels write those extents."""
+    if not isinstance(out, (tuple, list)) or len(out) != len(specs):
+        raise ValueError(f"out must be a tuple of {len(specs)} tensors")
+    for t, (dtype, shape, name) in zip(out, specs):
+        if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_contiguous() \
+                or t.device != device:
+            raise ValueError(f"{name} must be a contiguous {dtype} tensor on {device}")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+def _decode_specs(torch, shots, L):
+    return [(torch.uint8, (shots, 2, L, L), "correction"), (torch.int32, (shots,), "steps"),
+            (torch.uint8, (shots,), "logical_fail")]
+
+
 def kernel_path(L: int, v: int = 3) -> int:
     rc = lib().qca_kernel_path(L, ctypes.byref(make_config(v=v)))
     if rc < 0:
@@ -197,6 +215,9 @@ def decode_1d_batch(errors, max_steps: int = 4096, rng_seed: int = 0, *, v: int 
         out = (torch.empty_like(errors), torch.empty(shots, dtype=torch.int32, device=errors.device),
                torch.empty(shots, dtype=torch.uint8, device=errors.device),
                torch.empty(shots, dtype=torch.uint8, device=errors.device))
+    _check_out(torch, out, [(torch.uint8, (shots, L), "correction"),
+                            (torch.int32, (shots,), "steps"), (torch.uint8, (shots,), "flag"),
+                            (torch.uint8, (shots,), "majority_flag")], errors.device)
     C, steps, flag, maj = out
     cfg = make_config(v, m_max, p_move, shot_offset)
     _check(lib().qca_decode_1d_batch_async(
@@ -209,10 +230,11 @@ def decode_1d_batch(errors, max_steps: int = 4096, rng_seed: int = 0, *, v: int 
 
 def _variant_out(errors, out):
     torch = _torch()
-    shots = errors.shape[0]
+    shots, L = errors.shape[0], errors.shape[-1]
     if out is None:
         out = (torch.empty_like(errors), torch.empty(shots, dtype=torch.int32, device=errors.device),
                torch.empty(shots, dtype=torch.uint8, device=errors.device))
+    _check_out(torch, out, _decode_specs(torch, shots, L), errors.device)
     return out
 
 
@@ -282,6 +304,7 @@ def decode_batch(errors, max_steps: int = 4096, rng_seed: int = 0, *, v: int = 3
         steps = torch.empty(shots, dtype=torch.int32, device=errors.device)
         fail = torch.empty(shots, dtype=torch.uint8, device=errors.device)
     else:
+        _check_out(torch, out, _decode_specs(torch, shots, L), errors.device)
         C, steps, fail = out
     cfg = make_config(v, m_max, p_move, shot_offset, tie_order, balance_rule)
     _check(lib().qca_decode_batch_async(
@@ -343,12 +366,19 @@ def decode_batch_host(errors, max_steps: int = 4096, rng_seed: int = 0, *, v: in
     if errors.is_cuda or errors.dtype != torch.uint8 or not errors.is_contiguous():
         raise ValueError("errors must be a contiguous host uint8 tensor")
     shots, L = errors.shape[0], errors.shape[-1]
+    if tuple(errors.shape) != (shots, 2, L, L):
+        raise ValueError(f"errors has shape {tuple(errors.shape)}, expected (shots, 2, L, L)")
     if out is None:
         pin = errors.is_pinned()
         C = torch.empty_like(errors, pin_memory=pin) if correction else None
         steps = torch.empty(shots, dtype=torch.int32, pin_memory=pin)
         fail = torch.empty(shots, dtype=torch.uint8, pin_memory=pin)
     else:
+        specs = _decode_specs(torch, shots, L)
+        if isinstance(out, (tuple, list)) and len(out) == 3 and out[0] is None:
+            _check_out(torch, out[1:], specs[1:], errors.device)  # correction not copied back
+        else:
+            _check_out(torch, out, specs, errors.device)
         C, steps, fail = out
     cfg = make_config(v, m_max, p_move, 0, tie_order, balance_rule)
     _check(lib().qca_decode_batch_host(
@@ -373,6 +403,7 @@ def decode_batch_noalloc(errors, out, max_steps: int = 4096, rng_seed: int = 0, 
     torch = _torch()
     shots, L = errors.shape[0], errors.shape[-1]
     _dev_u8(torch, errors, (shots, 2, L, L), "errors")
+    _check_out(torch, out, _decode_specs(torch, shots, L), errors.device)
     C, steps, fail = out
     cfg = make_config(v, m_max, p_move, shot_offset, tie_order, balance_rule)
     _check(lib().qca_decode_batch_noalloc(
@@ -463,6 +494,7 @@ class UnevenPlan:
         import numpy as np
         if out is None:
             out = torch.empty(self.total_bytes, dtype=torch.uint8, device="cuda")
+        _dev_u8(torch, out, (self.total_bytes,), "out")
         Ld = torch.from_numpy(self.L).cuda()
         td = torch.from_numpy(np.ascontiguousarray(thr_host, dtype=np.uint64).view(np.int64)).cuda()
         _check(lib().qca_sample_errors_uneven_async(
@@ -477,11 +509,15 @@ class UnevenPlan:
                balance_rule: int = BALANCE_STAY):
         """Decode packed noise; returns (correction packed uint8, steps, logical_fail)."""
         torch = _torch()
+        _dev_u8(torch, errors, (self.total_bytes,), "errors")
         if out is None:
             C = torch.empty_like(errors)
             steps = torch.empty(self.shots, dtype=torch.int32, device=errors.device)
             fail = torch.empty(self.shots, dtype=torch.uint8, device=errors.device)
         else:
+            _check_out(torch, out, [(torch.uint8, (self.total_bytes,), "correction"),
+                                    (torch.int32, (self.shots,), "steps"),
+                                    (torch.uint8, (self.shots,), "logical_fail")], errors.device)
             C, steps, fail = out
         cfg = make_config(v, m_max, p_move, 0, tie_order, balance_rule)
         _check(lib().qca_decode_uneven_async(
@@ -659,9 +695,11 @@ class Net:
             steps = torch.empty(shots, dtype=torch.int32, device=errors.device)
             fail = torch.empty(shots, dtype=torch.uint8, device=errors.device)
         else:
+            _check_out(torch, out, _decode_specs(torch, shots, L), errors.device)
             C, steps, fail = out
         if scratch is None:
             scratch = torch.empty_like(errors)
+        _dev_u8(torch, scratch, (shots, 2, L, L), "scratch")
         cfg = make_config(v, m_max, p_move, shot_offset, tie_order, balance_rule)
         _check(lib().qca_net_decode_batch_async(
             self.handle, ctypes.c_void_p(errors.data_ptr()), L, shots, max_steps,

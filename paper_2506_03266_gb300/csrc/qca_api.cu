@@ -340,7 +340,13 @@ int qca_decode_batch_host(const uint8_t* syndrome, int L, int64_t shots, int max
                                     st.streams[set_of(k)]);
     return e == cudaSuccess ? QCA_OK : cuda_fail(e, "host-to-device copy");
   };
-  if ((rc = input_copy(0))) return rc;
+  // on an error, wait for what was already enqueued before returning, so that
+  // no copy touches the caller's buffers afterwards
+  auto drain = [&](int err) {
+    for (int i = 0; i < 2; ++i) cudaStreamSynchronize(st.streams[i]);
+    return err;
+  };
+  if ((rc = input_copy(0))) return drain(rc);
   for (int64_t k = 0; k < nchunks; ++k) {
     const int64_t s0 = k * chunk, n = (shots - s0 < chunk) ? shots - s0 : chunk;
     cudaStream_t sm = st.streams[set_of(k)];
@@ -351,9 +357,9 @@ int qca_decode_batch_host(const uint8_t* syndrome, int L, int64_t shots, int max
     qca_config cc = c;
     cc.shot_offset = c.shot_offset + s0;
     rc = qca_decode_batch_async(dN, L, n, max_steps, rng_seed, dC, dS, dF, &cc, sm);
-    if (rc) return rc;
+    if (rc) return drain(rc);
     // one buffer set without concurrency: the next input waits for this chunk
-    if (concurrent && k + 1 < nchunks && (rc = input_copy(k + 1))) return rc;
+    if (concurrent && k + 1 < nchunks && (rc = input_copy(k + 1))) return drain(rc);
     cudaError_t e = cudaSuccess;
     if (out_correction)
       e = cudaMemcpyAsync(out_correction + s0 * E, dC, n * E, cudaMemcpyDeviceToHost, sm);
@@ -361,12 +367,12 @@ int qca_decode_batch_host(const uint8_t* syndrome, int L, int64_t shots, int max
       e = cudaMemcpyAsync(out_steps + s0, dS, n * sizeof(int32_t), cudaMemcpyDeviceToHost, sm);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(out_logical_fail + s0, dF, n, cudaMemcpyDeviceToHost, sm);
-    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
-    if (!concurrent && k + 1 < nchunks && (rc = input_copy(k + 1))) return rc;
+    if (e != cudaSuccess) return drain(cuda_fail(e, "device-to-host copy"));
+    if (!concurrent && k + 1 < nchunks && (rc = input_copy(k + 1))) return drain(rc);
   }
   for (int i = 0; i < 2; ++i) {
     cudaError_t e = cudaStreamSynchronize(st.streams[i]);
-    if (e != cudaSuccess) return cuda_fail(e, "qca_decode_batch_host");
+    if (e != cudaSuccess) return drain(cuda_fail(e, "qca_decode_batch_host"));
   }
   return QCA_OK;
 }

@@ -7,7 +7,8 @@
 // queue, largest L first, work stealing across sizes, each shot retiring on
 // its own step count).  Shots of other sizes (or packed off a 4-byte boundary)
 // go to per-size persistent launches of their own kernel on side streams
-// forked from and joined back to the caller's stream, and that per-size form
+// forked from and joined back to the caller's stream (beside the mixed-size
+// launch, which has no dependence on them), and that per-size form
 // can also be chosen for every size (qca_uneven_plan_set_mode).  Either way
 // the decode can be captured in one CUDA graph.
 #include <math.h>
@@ -309,6 +310,10 @@ int qca_decode_uneven_async(qca_uneven_plan_t p, const uint8_t* errors, int max_
     mixed = mixed_group_threads(p->msizes[i], c.m_max) == p->mgroup[i];
   cudaError_t e = cudaMemsetAsync(p->d_counters, 0, sizeof(unsigned) * (p->sizes.size() + 1), st);
   if (e != cudaSuccess) return cuda_fail(e, "uneven decode counters");
+  // the side streams fork before the mixed-size launch, so that the sizes
+  // outside its queue take SMs as its CTAs retire
+  e = cudaEventRecord(p->fork, st);
+  if (e != cudaSuccess) return cuda_fail(e, "uneven decode fork");
   if (mixed) {
     DecodeArgs a;
     int rc = fill_decode_args(a, errors, p->msizes[0], p->m_items, max_steps, rng_seed, &c);
@@ -326,8 +331,6 @@ int qca_decode_uneven_async(qca_uneven_plan_t p, const uint8_t* errors, int max_
                       n_pair, p->m_items, st);
     if (rc) return rc;
   }
-  e = cudaEventRecord(p->fork, st);
-  if (e != cudaSuccess) return cuda_fail(e, "uneven decode fork");
   for (size_t i = 0; i < p->sizes.size(); ++i) {
     if (mixed && p->in_mixed[i]) continue;
     e = cudaStreamWaitEvent(p->side[i], p->fork, 0);

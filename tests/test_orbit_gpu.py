@@ -94,7 +94,8 @@ def test_orbit_shots_from_their_syndromes(noise):
 
 def test_orbit_shots_in_the_mixed_size_launch(noise):
     """The orbit shots of sizes up to 192 in one uneven batch (one mixed-size
-    launch: pairs, 256- and 128-thread groups) against the oracle."""
+    launch: a 512-thread CTA per L = 192 shot, smaller groups below) against
+    the oracle."""
     shots = [(s, L) for s, L, _ in ORBITS]
     Ls = np.array([L for _, L in shots], dtype=np.int32)
     plan = qca.UnevenPlan(Ls)

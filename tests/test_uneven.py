@@ -117,8 +117,8 @@ def test_uneven_decode_in_cuda_graph(built, mode):
 @pytest.mark.gpu
 @pytest.mark.parametrize("tie_order,balance_rule", [(0, 0), (1, 1)])
 def test_mixed_launch_matches_per_size_launches(built, tie_order, balance_rule):
-    """The single mixed-size launch (pairs of CTAs for L > 128, whole CTAs for
-    64 < L <= 128, four groups per CTA for L <= 64) against one launch per
+    """The single mixed-size launch (pairs of CTAs for L > 192, one CTA per shot
+    for 64 < L <= 192, several groups per CTA below) against one launch per
     size, bit for bit, on nine on-chip sizes (the ninth and smallest runs in a
     launch of its own: the queue takes eight) and two odd sizes packed last
     (byte-access sweep); the small sizes also against the oracle."""
