@@ -123,6 +123,49 @@ def test_band_geometry_covers_every_supported_size(lib):
         assert qca.get_tuning(L)[0] == H, L
 
 
+def _band_height_rule(L):
+    """The band-height rule of the on-chip sweep restated: among 4-, 8-, 16-
+    and 32-row bands that divide the CTA's rows within its warp limit, the one
+    whose warp count is nearest the target, the taller on a tie; if none fits,
+    any other divisor of at least 5 rows by the same distance, the shorter on
+    a tie.  Returns (height, whether a tie decided it)."""
+    cl = 2 if L > 128 else 1
+    kw = 2 if L // 4 > 32 else 1
+    rows = L // cl
+    spw = 32 // (L // 4 // kw)  # band segments per warp
+    max_warps = 32 if cl == 1 else 16
+    target = min(max_warps, 4 if L <= 64 else min(16, L // 8))
+
+    def dist(H):
+        return abs(-(-4 * (rows // H) // spw) - target)
+
+    def fits(H):
+        return rows % H == 0 and -(-4 * (rows // H) // spw) <= max_warps
+
+    cand = [H for H in (4, 8, 16, 32) if fits(H)]
+    if cand:
+        best = min(cand, key=lambda H: (dist(H), -H))
+    else:
+        cand = [H for H in range(5, rows + 1) if fits(H)]
+        best = min(cand, key=lambda H: (dist(H), H))
+    return best, sum(dist(H) == dist(best) for H in cand) > 1
+
+
+def test_band_height_follows_its_rule_at_every_size_ties_included(lib):
+    ties = {}
+    for L in range(8, 257, 4):
+        if L > 128 and L % 8:
+            continue
+        qca.set_tuning(L, 0, 0)
+        H, tie = _band_height_rule(L)
+        assert qca.get_tuning(L)[0] == H, L
+        if tie:
+            ties[L] = H
+    # taller among the power-of-two bands (8: 4 or 8 rows; 24: 4 or 8), shorter
+    # among the others (84: 28 or 42 rows; 100: 25 or 50)
+    assert ties == {8: 8, 24: 8, 84: 28, 100: 25}, ties
+
+
 def test_large_lattice_path_selection(lib):
     # above 256: the large-lattice sweep for multiples of 128, else the generic one
     for L in range(257, 1025):
