@@ -253,7 +253,8 @@ int qca_sample_errors_uneven_async(const int32_t* L_dev, const int64_t* offsets_
  * 512-thread CTA halving into up to four groups as the queue reaches smaller
  * sizes; each takes its next shot when the last one is done (work stealing
  * across sizes; every shot retires after its own number of steps); shots of
- * other sizes go to per-size launches.  Mode 1: one persistent launch per
+ * other sizes go to per-size launches on streams forked from `stream` before
+ * it, which run beside it.  Mode 1: one persistent launch per
  * size, each on a stream forked from and joined to `stream`, so that the sizes
  * run side by side.  Only kernel launches, memset and
  * event operations are enqueued, so the call can be captured in a CUDA graph
